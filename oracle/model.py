@@ -1,0 +1,243 @@
+"""Pointwise constitutive law of the phase-field model (oracle; test infrastructure only).
+
+All functions are vectorised over numpy arrays and work in float64.  Strains are given
+by their in-plane tensor components (exx, eyy, exy) -- exy is the tensor shear, half
+the engineering shear.  The out-of-plane strain is zero (plane strain, Sec. 4 intro:
+one element thick, thickness-direction motion suppressed).
+
+Invariants.  With ``cdim`` the deviatoric factor (1/3 for plane strain, where the 3D
+deviator of a tensor with ezz = 0 is used; 1/2 for the 2D-invariant plane-stress
+variant) and ``tr = exx + eyy``::
+
+    e.e = exx^2 + eyy^2 + 2 exy^2 - cdim * tr^2      (eps_dev : eps_dev)
+
+Energy split (Sec. 2, volumetric/deviatoric split; the paper prints the symbol Psi^+
+twice, the second one is the inactive part Psi^-)::
+
+    Psi+ = mu e.e + (K/2) <tr>_+^2 ,   Psi- = (K/2) <tr>_-^2
+
+Degraded stress (Sec. 2, constitutive equation for sigma)::
+
+    sigma = g(d) [2 mu eps_dev + K <tr>_+ I] + K <tr>_- I
+
+AT2 model (Table 1): g(d) = (1-d)^2 + eta, w(d) = d^2, c_w = 2.
+"""
+import numpy as np
+
+PLANE_STRAIN = 0
+PLANE_STRESS = 1
+
+C_W_AT2 = 2.0  # Table 1, AT2 row
+
+
+class Material:
+    """Material constants in the paper's notation.
+
+    ``mu`` shear modulus, ``K`` bulk modulus (the paper's k, Sec. 2), ``Gc`` critical
+    energy release rate, ``l`` length scale, ``eta`` residual stiffness in g(d)
+    (Table 1), ``cdim`` deviatoric factor (see module docstring).
+    """
+
+    def __init__(self, mu, K, Gc, l, eta, cdim):
+        self.mu = float(mu)
+        self.K = float(K)
+        self.Gc = float(Gc)
+        self.l = float(l)
+        self.eta = float(eta)
+        self.cdim = float(cdim)
+
+    @property
+    def psi_crit(self):
+        """Psi_crit = G_c / (c_w l), Sec. 3.5 (activation condition), AT2 c_w = 2."""
+        return self.Gc / (C_W_AT2 * self.l)
+
+
+def material_from_E_nu(E, nu, Gc, l, eta, plane=PLANE_STRAIN):
+    """Lame constants from (E, nu); bulk modulus K per plane mode.
+
+    Plane strain keeps the 3D bulk modulus K = lambda + 2 mu / 3.  Plane stress uses
+    2D invariants with K = E / (2 (1 - nu)), which reproduces the plane-stress Hooke
+    law for an undamaged solid (2 mu eps + (K - mu) tr I).
+    """
+    mu = E / (2.0 * (1.0 + nu))
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    if plane == PLANE_STRAIN:
+        return Material(mu, lam + 2.0 * mu / 3.0, Gc, l, eta, 1.0 / 3.0)
+    return Material(mu, E / (2.0 * (1.0 - nu)), Gc, l, eta, 0.5)
+
+
+def E_nu_from_lame(lam, mu):
+    """Inverse of the Lame relations: E = mu (3 lam + 2 mu)/(lam + mu), nu = lam/(2(lam+mu))."""
+    return mu * (3.0 * lam + 2.0 * mu) / (lam + mu), lam / (2.0 * (lam + mu))
+
+
+def g(d, eta):
+    """Degradation function g(d) = (1-d)^2 + eta (Table 1)."""
+    return (1.0 - d) ** 2 + eta
+
+
+def dg(d):
+    """dg/dd = -2 (1-d)."""
+    return -2.0 * (1.0 - d)
+
+
+def pos(x):
+    """<x>_+ = (x + |x|)/2 (Sec. 2)."""
+    return 0.5 * (x + np.abs(x))
+
+
+def neg(x):
+    """<x>_- = (x - |x|)/2 (Sec. 2)."""
+    return 0.5 * (x - np.abs(x))
+
+
+def invariants(exx, eyy, exy, cdim):
+    """Return (tr eps, eps_dev : eps_dev)."""
+    tr = exx + eyy
+    ee = exx * exx + eyy * eyy + 2.0 * exy * exy - cdim * tr * tr
+    return tr, ee
+
+
+def psi_plus(exx, eyy, exy, m):
+    """Active strain energy Psi+ = mu e.e + K/2 <tr>_+^2 (Sec. 2)."""
+    tr, ee = invariants(exx, eyy, exy, m.cdim)
+    return m.mu * ee + 0.5 * m.K * pos(tr) ** 2
+
+
+def psi_minus(exx, eyy, exy, m):
+    """Inactive strain energy Psi- = K/2 <tr>_-^2 (Sec. 2)."""
+    tr, _ = invariants(exx, eyy, exy, m.cdim)
+    return 0.5 * m.K * neg(tr) ** 2
+
+
+def stress(exx, eyy, exy, d, m):
+    """In-plane components (sxx, syy, sxy) of the degraded stress (Sec. 2)."""
+    tr = exx + eyy
+    gd = g(d, m.eta)
+    vol = gd * m.K * pos(tr) + m.K * neg(tr)
+    sxx = gd * 2.0 * m.mu * (exx - m.cdim * tr) + vol
+    syy = gd * 2.0 * m.mu * (eyy - m.cdim * tr) + vol
+    sxy = gd * 2.0 * m.mu * exy
+    return sxx, syy, sxy
+
+
+def stress_zz(exx, eyy, d, m):
+    """Out-of-plane normal stress of the plane-strain state (ezz = 0), same law (Sec. 2).
+
+    Only meaningful for the 3D-invariant (plane strain) mode; the weak form does not
+    need it, the invariant checks of the fixed-stress relations do.
+    """
+    tr = exx + eyy
+    gd = g(d, m.eta)
+    return gd * 2.0 * m.mu * (-m.cdim * tr) + gd * m.K * pos(tr) + m.K * neg(tr)
+
+
+def tension(exx, eyy):
+    """Sign indicator I_+ of Sec. 3.3: 1 where tr eps > 0 strictly, else 0."""
+    return (exx + eyy) > 0.0
+
+
+def tangent_voigt(d, ip, m):
+    """Consistent tangent of the stress in Voigt form (xx, yy, engineering xy).
+
+    For a frozen sign indicator ``ip`` the stress is linear in the strain; this is the
+    bracket of the stress-increment equation in Sec. 3.3 (the part multiplying
+    Delta eps).  Returns an array of shape d.shape + (3, 3).
+    """
+    gd = g(d, m.eta)
+    kv = np.where(ip, gd * m.K, m.K)
+    D = np.zeros(np.shape(d) + (3, 3))
+    c = m.cdim
+    two_mu_g = 2.0 * m.mu * gd
+    D[..., 0, 0] = two_mu_g * (1.0 - c) + kv
+    D[..., 1, 1] = two_mu_g * (1.0 - c) + kv
+    D[..., 0, 1] = -two_mu_g * c + kv
+    D[..., 1, 0] = -two_mu_g * c + kv
+    D[..., 2, 2] = m.mu * gd  # sxy = g 2 mu exy = g mu gamma
+    return D
+
+
+# --------------------------------------------------------------------------------------
+# Fixed-stress schemes (Sec. 3.3-3.5)
+# --------------------------------------------------------------------------------------
+ST, S1, S2, S3 = 0, 1, 2, 3
+
+
+def fixed_stress_Q(tr, ee, scheme, m):
+    """Bracket of the extra stiffness K~^S (Sec. 3.4, three forms after Table 2).
+
+    S1: K <tr>_+^2 ;  S2: 2 mu e.e ;  S3: 2 mu e.e + K <tr>_+^2 ;  ST: 0.
+    """
+    tp2 = m.K * pos(tr) ** 2
+    dev = 2.0 * m.mu * ee
+    if scheme == S1:
+        return tp2
+    if scheme == S2:
+        return dev
+    if scheme == S3:
+        return dev + tp2
+    return np.zeros_like(tr)
+
+
+def activation(psi, H_prev, d_q, m, psi_crit=None):
+    """Softening-region test of Sec. 3.5.
+
+    Active where Psi+ > Psi_crit, Psi+ > Psi_max and phi < 0.95, all strict.  Psi_max
+    is read as the quadrature point's history maximum from the last converged load
+    step, and phi as the phase field interpolated to the point.
+    """
+    pc = m.psi_crit if psi_crit is None else psi_crit
+    return (psi > pc) & (psi > H_prev) & (d_q < 0.95)
+
+
+def extra_stiffness(tr, ee, d_q, scheme, m):
+    """Per-point value of K~^S without the shape functions (Sec. 3.4).
+
+    K~ = -4 (1-d)^2 / g(d) * Q_S, Q_S from ``fixed_stress_Q``.
+    """
+    return -4.0 * (1.0 - d_q) ** 2 / g(d_q, m.eta) * fixed_stress_Q(tr, ee, scheme, m)
+
+
+def trace_increment(tr, d_q, dd_q, m):
+    """tr Delta eps = 2(1-d)/g(d) <tr>_+ Delta d for Delta d > 0, else 0.
+
+    First fixed-invariant relation (Sec. 3.3, from Delta sigma . I = 0) with the
+    Delta d > 0 rule of Sec. 3.5.
+    """
+    a = 2.0 * (1.0 - d_q) / g(d_q, m.eta)
+    return np.where(dd_q > 0.0, a * pos(tr) * dd_q, 0.0)
+
+
+def dev_increment(ee, d_q, dd_q, m):
+    """eps_dev . Delta eps = 2(1-d)/g(d) (eps_dev . eps_dev) Delta d for Delta d > 0, else 0.
+
+    Second fixed-invariant relation (Sec. 3.3, from Delta sigma . eps_dev = 0) with the
+    Delta d > 0 rule of Sec. 3.5.
+    """
+    a = 2.0 * (1.0 - d_q) / g(d_q, m.eta)
+    return np.where(dd_q > 0.0, a * ee * dd_q, 0.0)
+
+
+def predict_psi(tr, ee, d_q, dd_q, scheme, m):
+    """Predicted active energy Psi+^{k+1/2} (Sec. 3.3) with the Delta d > 0 rule (Sec. 3.5).
+
+    The increments from the fixed-invariant relations are
+        tr Delta eps        = a <tr>_+ Delta d        (first relation, used by S1, S3)
+        eps_dev . Delta eps = a (e.e) Delta d        (second relation, used by S2, S3)
+    with a = 2(1-d)/g(d), both set to zero unless Delta d > 0.  The updated invariants
+    are  <tr>_+^{k+1/2} = <tr>_+ (1 + a Delta d)  and
+        e.e^{k+1/2} = e.e + 4 e.e [ (1-d)/g Delta d + (1-d)^2/g^2 Delta d^2 ],
+    i.e. e.e times (1 + a Delta d)^2.  The scheme picks which invariant is updated.
+    """
+    tp = pos(tr)
+    if scheme in (S1, S3):
+        tp_new = tp + trace_increment(tr, d_q, dd_q, m)
+    else:
+        tp_new = tp
+    if scheme in (S2, S3):
+        r = (1.0 - d_q) / g(d_q, m.eta)
+        ddp = np.where(dd_q > 0.0, dd_q, 0.0)
+        ee_new = ee + 4.0 * ee * (r * ddp + r * r * ddp * ddp)
+    else:
+        ee_new = ee
+    return m.mu * ee_new + 0.5 * m.K * tp_new ** 2

@@ -1,0 +1,177 @@
+"""Synthetic specimens and seeded inputs (input generation only, no method arithmetic).
+
+Builds the structured-grid specimens of the paper's benchmark family -- tensile and
+shear notched squares (Sec. 4.1-4.2), an L-shaped panel (Sec. 4.3) -- plus small
+analytic specimens used for checks, and seeded random fields.  Everything here is data:
+node flag bytes, element masks, load schedules and material constants.  The solver
+(CUDA library) and the independent checker both take these arrays as inputs.
+
+Node flag bits (one byte per node): FIX_X=1, FIX_Y=2, LOAD_X=4, LOAD_Y=8, D_FIX1=16
+(phase field held at 1), D_FIX0=32 (phase field held at 0).  Node (i, j) has id
+j (nx+1) + i; element (i, j) has id j nx + i.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+FIX_X, FIX_Y, LOAD_X, LOAD_Y, D_FIX1, D_FIX0 = 1, 2, 4, 8, 16, 32
+PLANE_STRAIN, PLANE_STRESS = 0, 1
+
+# Tensile/shear material of the notched-square benchmarks in kN and mm
+# (lambda = 121.15 kN/mm^2, mu = 80.77 kN/mm^2, G_c = 2.7e-3 kN/mm).
+MIEHE_LAMBDA = 121.15
+MIEHE_MU = 80.77
+MIEHE_GC = 2.7e-3
+
+
+def lame_to_E_nu(lam, mu):
+    """(lambda, mu) -> (E, nu); the library's create call takes E and nu."""
+    return mu * (3.0 * lam + 2.0 * mu) / (lam + mu), lam / (2.0 * (lam + mu))
+
+
+@dataclass
+class Specimen:
+    name: str
+    nx: int
+    ny: int
+    Lx: float
+    Ly: float
+    node_flags: np.ndarray
+    elem_active: np.ndarray
+    reaction_dir: int
+    plane: int
+    E: float
+    nu: float
+    Gc: float
+    l: float
+    eta: float
+    increments: np.ndarray = field(default_factory=lambda: np.zeros(0))
+
+    @property
+    def nn(self):
+        return (self.nx + 1) * (self.ny + 1)
+
+    @property
+    def ne(self):
+        return self.nx * self.ny
+
+
+def _node_ij(nx, ny):
+    j, i = np.divmod(np.arange((nx + 1) * (ny + 1)), nx + 1)
+    return i, j
+
+
+def _slit(flags, nx, ny):
+    """Horizontal slit from the left edge to the centre: d = 1 on nodes y = Ly/2, x <= Lx/2."""
+    if ny % 2 or nx % 2:
+        raise ValueError("slit specimens need even nx and ny")
+    i, j = _node_ij(nx, ny)
+    flags[(j == ny // 2) & (i <= nx // 2)] |= D_FIX1
+
+
+def tensile(n, l=None, steps=20, u_max=6e-3, eta=1e-9):
+    """Tensile notched unit square: bottom fixed, top pulled up (u_x = 0 on top)."""
+    nx = ny = int(n)
+    i, j = _node_ij(nx, ny)
+    flags = np.zeros((nx + 1) * (ny + 1), np.uint8)
+    flags[j == 0] |= FIX_X | FIX_Y
+    flags[j == ny] |= FIX_X | LOAD_Y
+    _slit(flags, nx, ny)
+    E, nu = lame_to_E_nu(MIEHE_LAMBDA, MIEHE_MU)
+    return Specimen("tensile", nx, ny, 1.0, 1.0, flags, np.ones(nx * ny, np.uint8), 1,
+                    PLANE_STRAIN, E, nu, MIEHE_GC, 0.03 if l is None else l, eta,
+                    np.full(steps, u_max / steps))
+
+
+def shear(n, l=None, steps=150, u_max=1.5e-2, eta=1e-9):
+    """Shear notched unit square: bottom fixed, top moved in x (u_y = 0), rollers on sides."""
+    nx = ny = int(n)
+    i, j = _node_ij(nx, ny)
+    flags = np.zeros((nx + 1) * (ny + 1), np.uint8)
+    side = ((i == 0) | (i == nx)) & (j > 0) & (j < ny)
+    flags[side] |= FIX_Y
+    flags[j == 0] |= FIX_X | FIX_Y
+    flags[j == ny] |= LOAD_X | FIX_Y
+    _slit(flags, nx, ny)
+    E, nu = lame_to_E_nu(MIEHE_LAMBDA, MIEHE_MU)
+    return Specimen("shear", nx, ny, 1.0, 1.0, flags, np.ones(nx * ny, np.uint8), 0,
+                    PLANE_STRAIN, E, nu, MIEHE_GC, 0.03 if l is None else l, eta,
+                    np.full(steps, u_max / steps))
+
+
+def l_shape(n, steps=200, u_max=1.0, l=2.5, eta=1e-9, patch=30.0):
+    """L-shaped panel: 500 x 500 mm with the top-right quadrant masked out, plane stress.
+
+    The bottom edge under the upright part (x <= 250 mm) is clamped; the lower arm
+    (x > 250 mm) is a cantilever lifted on a ``patch``-wide strip of its bottom edge at
+    the free end, where the phase field is held at zero.
+    """
+    nx = ny = int(n)
+    if n % 2:
+        raise ValueError("l_shape needs an even grid")
+    L = 500.0
+    h = L / n
+    ej, ei = np.divmod(np.arange(nx * ny), nx)
+    active = ~((ei >= nx // 2) & (ej >= ny // 2))
+    i, j = _node_ij(nx, ny)
+    x = i * h
+    flags = np.zeros((nx + 1) * (ny + 1), np.uint8)
+    flags[(j == 0) & (x <= 0.5 * L + 1e-9)] |= FIX_X | FIX_Y
+    load = (j == 0) & (x >= L - patch - 1e-9)
+    flags[load] |= LOAD_Y
+    flags[(j <= max(1, int(round(patch / h)))) & (x >= L - patch - 1e-9)] |= D_FIX0
+    return Specimen("l_shape", nx, ny, L, L, flags, active.astype(np.uint8), 1,
+                    PLANE_STRESS, 25.85, 0.18, 8.9e-5, l, eta,
+                    np.full(steps, u_max / steps))
+
+
+def uniaxial_bar(nx, ny, Lx=1.0, Ly=1.0, lam=MIEHE_LAMBDA, mu=MIEHE_MU, Gc=MIEHE_GC,
+                 l=0.03, eta=1e-9, steps=10, u_max=1e-2):
+    """Homogeneous uniaxial strain: u_x = 0 everywhere on the boundary sides, bottom
+    u_y = 0, top u_y = ubar, no slit.  The exact state is uniform (closed form)."""
+    i, j = _node_ij(nx, ny)
+    flags = np.zeros((nx + 1) * (ny + 1), np.uint8)
+    flags[(i == 0) | (i == nx)] |= FIX_X
+    flags[j == 0] |= FIX_X | FIX_Y
+    flags[j == ny] |= FIX_X | LOAD_Y
+    E, nu = lame_to_E_nu(lam, mu)
+    return Specimen("uniaxial", nx, ny, Lx, Ly, flags, np.ones(nx * ny, np.uint8), 1,
+                    PLANE_STRAIN, E, nu, Gc, l, eta, np.full(steps, u_max / steps))
+
+
+def strip_1d(nx, ny=4, L=1.0, l=0.05):
+    """Phase-field strip [0, L] x [0, L ny / nx] with d = 1 held on x = 0 and no load."""
+    i, j = _node_ij(nx, ny)
+    flags = np.zeros((nx + 1) * (ny + 1), np.uint8)
+    flags[i == 0] |= D_FIX1
+    flags[:] |= 0
+    E, nu = lame_to_E_nu(MIEHE_LAMBDA, MIEHE_MU)
+    return Specimen("strip", nx, ny, L, L * ny / nx, flags, np.ones(nx * ny, np.uint8), 1,
+                    PLANE_STRAIN, E, nu, MIEHE_GC, l, 1e-9)
+
+
+# ---- seeded random inputs ------------------------------------------------------------------
+def rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def random_state(spec, seed, u_scale=1e-3, h_scale=None):
+    """Seeded (u, d, H) of crack-like structure for operator checks.
+
+    u: smooth field plus noise (strain of order u_scale), d in [0, 1) with a damaged
+    band and values up to 1, H >= 0 per quadrature point of the order of Psi_crit.
+    """
+    r = rng(seed)
+    i, j = _node_ij(spec.nx, spec.ny)
+    x = i / spec.nx
+    y = j / spec.ny
+    ux = u_scale * (np.sin(3.1 * x + 0.3) * y + 0.2 * r.standard_normal(spec.nn))
+    uy = u_scale * (np.cos(2.3 * y) * x + y + 0.2 * r.standard_normal(spec.nn))
+    u = np.stack([ux, uy], axis=1).ravel() * spec.Lx
+    band = np.exp(-((y - 0.5) / 0.08) ** 2)
+    d = np.clip(band * (0.7 + 0.3 * r.random(spec.nn)) + 0.05 * r.random(spec.nn), 0.0, 1.0)
+    d[r.random(spec.nn) < 0.02] = 1.0
+    if h_scale is None:
+        h_scale = spec.Gc / spec.l
+    H = h_scale * r.random((spec.ne, 4)) * (1.0 + 3.0 * r.random((spec.ne, 1)))
+    return u, d, H

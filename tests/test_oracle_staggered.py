@@ -1,0 +1,123 @@
+"""Pins of the checker's staggered solvers against closed forms and invariants.
+
+* 1D phase-field profile: with H = 0 and d = 1 held on x = 0 the AT2 evolution equation
+  (Sec. 2) reduces to d - l^2 d'' = 0, solved by cosh((L - x)/l)/cosh(L/l); the FE
+  error must fall at second order.
+* Homogeneous uniaxial strain: u is fixed by the boundary values, H = max_t Psi+, the
+  exact discrete phase field is d = 2H/(G_c/l + 2H) and the top reaction is
+  g(d) M eps Lx (M = lambda + 2 mu).  Every scheme must reach it, across the peak.
+* Irreversibility: H never decreases; d does not decrease on a monotone path.
+* With the softening test switched off, S1/S2/S3 are the standard scheme exactly.
+"""
+import numpy as np
+import pytest
+
+from oracle import model, q1, staggered as stg
+from paper_2209_07969_gb300 import specimens as S
+
+
+def _grid(sp):
+    return q1.Grid(sp.nx, sp.ny, sp.Lx, sp.Ly, sp.node_flags, sp.elem_active)
+
+
+def _mat(sp):
+    return model.material_from_E_nu(sp.E, sp.nu, sp.Gc, sp.l, sp.eta, sp.plane)
+
+
+def test_1d_profile_second_order():
+    L, l = 1.0, 0.1
+    errs = []
+    for nx in (40, 80, 160):
+        sp = S.strip_1d(nx, ny=2, L=L, l=l)
+        g, m = _grid(sp), _mat(sp)
+        d = stg.d_step_standard(g, m, np.zeros((g.ne, 4)))
+        s, _ = q1.gauss_points_unit()
+        ej, ei = np.divmod(np.arange(g.ne), g.nx)
+        xq = (ei[:, None] + s[None]) * g.hx
+        exact = np.cosh((L - xq) / l) / np.cosh(L / l)
+        err = q1.interp_qp(g, d) - exact
+        errs.append(np.sqrt(np.sum(err ** 2) * q1.qp_weight(g) / (g.Lx * g.Ly)))
+    errs = np.array(errs)
+    orders = np.log2(errs[:-1] / errs[1:])
+    assert errs[-1] < 1e-3
+    assert np.all(np.abs(orders - 2.0) < 0.1), orders
+
+
+@pytest.mark.parametrize("scheme", [model.ST, model.S1, model.S2, model.S3])
+def test_uniaxial_bar_closed_form(scheme):
+    lam, mu, Gc, l, eta = 121.15, 80.77, 2.7e-3, 0.03, 1e-9
+    M = lam + 2 * mu
+    eps_c = np.sqrt(Gc / (3 * M * l))          # peak strain of the homogeneous AT2 state
+    sp = S.uniaxial_bar(3, 4, Lx=0.5, Ly=1.0, lam=lam, mu=mu, Gc=Gc, l=l, eta=eta,
+                        steps=8, u_max=2.5 * eps_c)
+    g, m = _grid(sp), _mat(sp)
+    opts = stg.Options(tol_st=1e-9, tol_nr=1e-10, max_stag=200)
+    st = stg.State(g)
+    H = 0.0
+    peak = 0.0
+    for k, du in enumerate(sp.increments):
+        r = stg.load_step(g, m, st, du, scheme, opts, reaction_dir=1)
+        assert r.converged
+        eps = st.ubar / sp.Ly
+        H = max(H, 0.5 * M * eps ** 2)
+        d = 2 * H / (Gc / l + 2 * H)
+        F = ((1 - d) ** 2 + eta) * M * eps * sp.Lx
+        peak = max(peak, F)
+        assert np.allclose(st.d, d, rtol=1e-7, atol=1e-9)
+        assert r.reaction == pytest.approx(F, rel=1e-7)
+        assert np.allclose(st.H, H, rtol=1e-12)
+    # the path crossed the closed-form peak sigma_c = (9/16) sqrt(M Gc / (3 l))
+    sig_c = 9.0 / 16.0 * np.sqrt(M * Gc / (3 * l))
+    assert peak <= sig_c * sp.Lx * (1 + 1e-9)
+    assert peak > 0.9 * sig_c * sp.Lx
+
+
+def test_homogeneous_peak_stress_closed_form():
+    """max_eps (1 - d(eps))^2 M eps with d = M eps^2 / (Gc/l + M eps^2) (eta -> 0)."""
+    M, Gc, l = 342.69, 2.7e-3, 0.03
+    eps = np.linspace(1e-5, 3e-2, 200001)
+    d = M * eps ** 2 / (Gc / l + M * eps ** 2)
+    sig = (1 - d) ** 2 * M * eps
+    assert sig.max() == pytest.approx(9 / 16 * np.sqrt(M * Gc / (3 * l)), rel=1e-8)
+    assert eps[np.argmax(sig)] == pytest.approx(np.sqrt(Gc / (3 * M * l)), rel=1e-4)
+
+
+def _small_tensile(n=16, steps=6, u_max=4.5e-3):
+    sp = S.tensile(n, l=0.1, steps=steps, u_max=u_max)
+    return sp, _grid(sp), _mat(sp)
+
+
+def test_irreversibility_on_monotone_path():
+    sp, g, m = _small_tensile()
+    opts = stg.Options(tol_st=1e-8, tol_nr=1e-9)
+    st = stg.State(g)
+    for du in sp.increments:
+        H0, d0 = st.H.copy(), st.d.copy()
+        r = stg.load_step(g, m, st, du, model.ST, opts)
+        assert r.converged
+        assert np.all(st.H >= H0)
+        assert np.all(st.d >= d0 - 1e-8)
+
+
+@pytest.mark.parametrize("scheme", [model.S1, model.S2, model.S3])
+def test_schemes_equal_standard_without_softening(scheme):
+    sp, g, m = _small_tensile(steps=3)
+    opts_off = stg.Options(tol_st=1e-7, psi_crit=np.inf)
+    a, b = stg.State(g), stg.State(g)
+    for du in sp.increments:
+        ra = stg.load_step(g, m, a, du, model.ST, opts_off)
+        rb = stg.load_step(g, m, b, du, scheme, opts_off)
+        assert ra.stag_iters == rb.stag_iters
+        assert np.array_equal(a.u, b.u) and np.array_equal(a.d, b.d)
+        assert ra.reaction == rb.reaction
+
+
+def test_dirichlet_values_held():
+    sp, g, m = _small_tensile(steps=2)
+    st = stg.State(g)
+    for du in sp.increments:
+        stg.load_step(g, m, st, du, model.S1, stg.Options())
+    cu = g.u_constrained()
+    assert np.array_equal(st.u[cu], g.u_dirichlet_values(st.ubar)[cu])
+    cd = g.d_constrained()
+    assert np.array_equal(st.d[cd], g.d_dirichlet_values()[cd])
