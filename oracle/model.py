@@ -198,6 +198,24 @@ def extra_stiffness(tr, ee, d_q, scheme, m):
     return -4.0 * (1.0 - d_q) ** 2 / g(d_q, m.eta) * fixed_stress_Q(tr, ee, scheme, m)
 
 
+def augmented_coefficient(H_k, k_extra, m, floor=True):
+    """Per-point mass coefficient of the augmented d-tangent K_dd + K~^S (Sec. 3.4).
+
+    The standard AT2 coefficient is G_c/l + 2H.  Adding K~ can make it negative: at an
+    activated point the material is past its peak, the fixed-stress linearisation has
+    no equilibrium and the augmented system turns indefinite and near-singular, so
+    the exact first NR iterate explodes and the staggered iteration stagnates.  The
+    footnote of Sec. 3.3 requires the d-subproblem to stay convex; the reading used
+    here lets K~ cancel at most the history part 2H of the tangent, i.e. the
+    coefficient never drops below the crack-surface term G_c/l.  ``floor=False``
+    gives the unlimited form.
+    """
+    c = m.Gc / m.l + 2.0 * H_k + k_extra
+    if floor:
+        c = np.maximum(c, m.Gc / m.l)
+    return c
+
+
 def trace_increment(tr, d_q, dd_q, m):
     """tr Delta eps = 2(1-d)/g(d) <tr>_+ Delta d for Delta d > 0, else 0.
 

@@ -4,7 +4,8 @@ Follows Sec. 3 of the paper step by step, for the AT2 model with a history field
 (Sec. 2: the history variable replacing Psi+; Sec. 3.1 and 3.3: with AT2 and a history
 field the evolution equation is linear, so one NR iteration solves it).  Every linear
 system is solved exactly with SciPy's sparse LU (SuperLU); the augmented fixed-stress
-system may be indefinite and LU handles that.
+system is SPD under the reading of model.augmented_coefficient (LU also solves the
+unlimited, indefinite form when that reading is switched off).
 
 Per load step n (Sec. 3.1, Fig. 1, d-u order):
   1. ubar_n = ubar_{n-1} + dubar; the Dirichlet values are applied to u.
@@ -25,6 +26,8 @@ Readings where the paper is silent (the same readings are used by the CUDA path)
   * staggered residual: max over free d-DOFs of |R_d_i / (K_dd)_ii| with H from u^{k+1}
   * Psi_max of the activation test = committed history H_{n-1} at the point
   * at least one d-u pass per load step
+  * the augmented per-point coefficient G_c/l + 2H + K~ is kept >= G_c/l (convexity
+    of the d-subproblem, footnote of Sec. 3.3); see model.augmented_coefficient
 """
 import numpy as np
 import scipy.sparse.linalg as spla
@@ -34,13 +37,14 @@ from . import model, q1
 
 class Options:
     def __init__(self, tol_nr=1e-7, tol_st=1e-6, max_newton=50, max_stag=1000,
-                 psi_crit=None, project=False):
+                 psi_crit=None, project=False, kt_floor=True):
         self.tol_nr = tol_nr          # TOL_NR (Sec. 4 intro: 1e-7)
         self.tol_st = tol_st          # TOL_ST (Sec. 4 intro: 1e-6)
         self.max_newton = max_newton
         self.max_stag = max_stag
         self.psi_crit = psi_crit      # override of Psi_crit (None: G_c/(c_w l))
         self.project = project        # clamp d into [d_{n-1}, 1] after each d-solve
+        self.kt_floor = kt_floor      # augmented coefficient >= G_c/l (model.augmented_coefficient)
 
 
 class State:
@@ -139,7 +143,8 @@ def d_step_fixed_stress(grid, m, u_k, d_k, H_prev, scheme, opts, info=None):
     # residual of the evolution equation at (d^k, H^k)
     R = q1.assemble_damage(grid, c_std, kappa) @ d_k - q1.damage_rhs(grid, H_k)
     # first NR iteration with the augmented tangent K_dd + K~^S
-    K_aug = q1.assemble_damage(grid, c_std + k_extra, kappa)
+    K_aug = q1.assemble_damage(grid, model.augmented_coefficient(H_k, k_extra, m, opts.kt_floor),
+                               kappa)
     cd = grid.d_constrained()
     free = ~cd
     dd = np.zeros(grid.nn)

@@ -273,3 +273,22 @@ def test_s3_prediction_scales_plane_strain_energy():
     s = 1 + 2 * (1 - d) / ((1 - d) ** 2 + m.eta) * dd
     got = model.predict_psi(tr, ee, d, dd, model.S3, m)
     assert np.allclose(got, model.psi_plus(s * exx, s * eyy, s * exy, m), rtol=1e-12)
+
+
+def test_augmented_coefficient_floor():
+    """Reading of the footnote of Sec. 3.3: K~ cancels at most the 2H part of the tangent."""
+    m = _mat(eta=1e-9)
+    r = np.random.default_rng(15)
+    exx, eyy, exy = _strains(400, 16, sign=1.0)
+    exx, eyy, exy = exx * 30, eyy * 30, exy * 30
+    d = r.random(400) * 0.9
+    tr, ee = model.invariants(exx, eyy, exy, m.cdim)
+    H = model.psi_plus(exx, eyy, exy, m)
+    for s in (model.S1, model.S2, model.S3):
+        kt = model.extra_stiffness(tr, ee, d, s, m)
+        lit = model.augmented_coefficient(H, kt, m, floor=False)
+        c = model.augmented_coefficient(H, kt, m)
+        assert np.all(c >= m.Gc / m.l)
+        assert np.any(lit < 0)                      # the unlimited form goes indefinite
+        keep = lit >= m.Gc / m.l
+        assert np.array_equal(c[keep], lit[keep])
