@@ -1,0 +1,251 @@
+/*
+ * pf.h -- C ABI of libpf, a GB300 (sm_103a) solver for the staggered phase-field model
+ * of brittle fracture with the fixed-stress schemes of Luo, "Fast staggered schemes for
+ * the phase-field model of brittle fracture based on the fixed-stress concept"
+ * (arXiv 2209.07969).
+ *
+ * The model (Sec. 2): energy split into an active part
+ *     Psi+ = mu eps_dev:eps_dev + K/2 <tr eps>_+^2
+ * and an inactive part K/2 <tr eps>_-^2, degraded stress
+ *     sigma = g(d) [2 mu eps_dev + K <tr eps>_+ I] + K <tr eps>_- I,
+ * AT2 functions g(d) = (1-d)^2 + eta, w(d) = d^2, c_w = 2 (Table 1), and the history
+ * field H = max over time of Psi+ driving the evolution equation
+ *     [G_c/l + 2H] d - G_c l lap d = 2H.
+ * Discretisation: bilinear (Q1) elements on a structured nx-by-ny grid, 2x2 Gauss.
+ * Staggered schemes (Sec. 3.1, Fig. 1; Sec. 3.3-3.5, Table 2): standard (ST, d-u
+ * order) and fixed-stress S1 (first stress invariant held), S2 (deviatoric relation),
+ * S3 (both).
+ *
+ * Layouts (all arrays dense, C order):
+ *   node (i, j), 0 <= i <= nx, 0 <= j <= ny : id j*(nx+1) + i, at (i*Lx/nx, j*Ly/ny)
+ *   element (i, j), 0 <= i < nx, 0 <= j < ny: id j*nx + i, nodes (i,j),(i+1,j),(i,j+1),(i+1,j+1)
+ *   u   : 2*N doubles, interleaved (u_x, u_y) per node, N = (nx+1)*(ny+1)
+ *   d   : N doubles
+ *   H   : 4*nx*ny doubles, element-major, Gauss points (-,-),(+,-),(-,+),(+,+)
+ *
+ * Errors: every call returns a pf_status; PF_OK is 0.  Calls on a context set a
+ * message readable with pf_last_error.  Nothing in the library aborts the process.
+ * Thread safety: one context must not be used from two host threads at once.
+ */
+#ifndef PF_H
+#define PF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PF_API_VERSION 1
+
+typedef enum {
+  PF_OK = 0,
+  PF_EINVAL = 1,     /* bad argument (sizes, flags, NULL pointer, material out of range) */
+  PF_ENOMEM = 2,     /* device or host allocation failed */
+  PF_ENOTCONV = 3,   /* a solver hit its iteration cap; state is kept, see pf_step_result */
+  PF_ECUDA = 4,      /* a CUDA runtime call failed (message has the CUDA error string) */
+  PF_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+  PF_EBUSY = 6       /* resource in use (e.g. server slots full) */
+} pf_status;
+
+/* Staggered schemes of Table 2. */
+typedef enum { PF_ST = 0, PF_S1 = 1, PF_S2 = 2, PF_S3 = 3 } pf_scheme;
+
+/* Node flag bits (one byte per node). */
+enum {
+  PF_FIX_X = 1,   /* u_x held at 0 */
+  PF_FIX_Y = 2,   /* u_y held at 0 */
+  PF_LOAD_X = 4,  /* u_x held at the prescribed displacement ubar */
+  PF_LOAD_Y = 8,  /* u_y held at ubar */
+  PF_D_FIX1 = 16, /* d held at 1 (initial slit) */
+  PF_D_FIX0 = 32  /* d held at 0 (protected region) */
+};
+/* A node with no active element has all its DOFs held at 0. */
+
+enum { PF_PLANE_STRAIN = 0, PF_PLANE_STRESS = 1 };
+enum { PF_FP64 = 0, PF_FP32_IR = 1 };          /* linear-solve precision */
+enum { PF_PRECOND_JACOBI = 0, PF_PRECOND_GMG = 1 };
+enum { PF_F64 = 0, PF_F32 = 1 };                /* element type of operator-level arrays */
+
+/* Structured Q1 mesh; host pointers, copied by pf_create. */
+typedef struct {
+  int nx, ny;                  /* elements per side, >= 1 */
+  double Lx, Ly;               /* side lengths (mm), > 0 */
+  const uint8_t *elem_active;  /* nx*ny bytes (0 = masked out) or NULL = all active */
+  const uint8_t *node_flags;   /* N bytes of PF_* flag bits; must not be NULL */
+  int plane;                   /* PF_PLANE_STRAIN (3D invariants, eps_zz = 0) or
+                                  PF_PLANE_STRESS (2D invariants, K = E/(2(1-nu))) */
+  int precision;               /* PF_FP64 or PF_FP32_IR */
+  int reaction_dir;            /* 0: x, 1: y -- component summed over LOAD nodes */
+  int precond;                 /* PF_PRECOND_JACOBI or PF_PRECOND_GMG */
+} pf_mesh;
+
+/* Solver controls.  pf_default_options fills the defaults given in brackets. */
+typedef struct {
+  double tol_nr;     /* [1e-7] Newton stop: ||R_free|| <= tol_nr*max(||R0_free||, ||F_constr||)
+                        (TOL_NR of Sec. 4) */
+  double tol_lin;    /* [1e-10] relative residual of every FP64 linear solve */
+  double tol_inner;  /* [1e-4] relative residual of one FP32 inner solve (PF_FP32_IR) */
+  int max_newton;    /* [50] Newton iterations per u-solve */
+  int max_stag;      /* [1000] staggered iterations per load step */
+  int max_lin;       /* [200000] Krylov iterations per linear solve */
+  int max_refine;    /* [30] FP64 refinement sweeps per linear solve (PF_FP32_IR) */
+  double psi_crit;   /* [-1] < 0: G_c/(c_w l) of Sec. 3.5; else the given threshold */
+  int project;       /* [0] 1: clamp d into [d_{n-1}, 1] after every d-solve */
+  int check_every;   /* [8] Krylov iterations between convergence reads */
+} pf_options;
+
+typedef struct {
+  double ubar;          /* prescribed displacement after the step */
+  double reaction;      /* sum of the internal force over LOAD nodes (force / thickness) */
+  double stag_residual; /* max_i |R_d,i / K_dd,ii| at the last check (free d DOFs) */
+  int stag_iters;       /* d-u passes of this step */
+  int newton_u;         /* Newton linear solves for u */
+  int lin_u;            /* Krylov iterations in u-solves (inner iterations in FP32_IR) */
+  int lin_d;            /* Krylov iterations in d-solves, incl. the augmented S-solve */
+  int d_solves;         /* d linear solves (ST: 1 per pass, S1/S2/S3: 2 per pass) */
+  int refine_steps;     /* FP64 refinement sweeps (PF_FP32_IR) */
+  int converged;        /* 1 if the staggered residual met tol */
+  double ms;            /* device time of the step (CUDA events), milliseconds */
+} pf_step_result;
+
+typedef struct pf_ctx pf_ctx;
+
+void pf_default_options(pf_options *opt);
+
+/* Create a simulation (Sec. 2 model with E, nu, G_c, l and residual stiffness k_res,
+ * the eta of g(d) = (1-d)^2 + eta).  Allocates all device memory for the mesh; the
+ * state starts at u = 0, H = 0, d = Dirichlet values (1 on PF_D_FIX1 nodes, else 0),
+ * ubar = 0.  Uses the calling thread's current CUDA device and a new stream.
+ * Errors: PF_EINVAL (nx, ny < 1; L <= 0; nu outside (-1, 0.5); E, Gc, l <= 0;
+ * k_res < 0; NULL pointers), PF_ENOMEM, PF_ECUDA.  *out is NULL on error. */
+pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double l,
+                    double k_res, pf_ctx **out);
+pf_status pf_set_options(pf_ctx *ctx, const pf_options *opt);
+pf_status pf_get_options(const pf_ctx *ctx, pf_options *opt);
+
+/* One load step (Sec. 3.1 and 3.3-3.5): ubar += d_ubar, Dirichlet lift, u-solve with
+ * d_{n-1}, then staggered passes {d-step by `scheme`; u-solve; residual check} until
+ * stag_residual <= tol or max_stag passes; H_n = max(H_{n-1}, Psi+(u_n)).
+ * `out` may be NULL.  Returns PF_ENOTCONV (state advanced, out->converged = 0) when a
+ * cap was hit.  Synchronises the context's stream before returning. */
+pf_status pf_load_step(pf_ctx *ctx, double d_ubar, int scheme, double tol,
+                       pf_step_result *out);
+
+/* Copy the committed state to caller-owned host arrays (any may be NULL):
+ * u: 2N doubles, d: N doubles, H: 4*nx*ny doubles. */
+pf_status pf_get_fields(pf_ctx *ctx, double *u, double *d, double *H);
+/* Overwrite the committed state from host arrays (any may be NULL = keep). */
+pf_status pf_set_fields(pf_ctx *ctx, const double *u, const double *d, const double *H,
+                        double ubar);
+
+/* Serialised state (u, d, H, ubar, step count) for checkpoint/resume. */
+size_t pf_state_size(const pf_ctx *ctx);
+pf_status pf_get_state(pf_ctx *ctx, void *buf, size_t size);
+pf_status pf_set_state(pf_ctx *ctx, const void *buf, size_t size);
+
+/* Counts of the mesh: nodes N, elements, quadrature points. */
+pf_status pf_sizes(const pf_ctx *ctx, int64_t *n_nodes, int64_t *n_elems, int64_t *n_qp);
+/* Kernel launches issued by this context since creation (for accounting). */
+int64_t pf_launch_count(const pf_ctx *ctx);
+
+const char *pf_last_error(const pf_ctx *ctx);
+const char *pf_status_string(pf_status s);
+void pf_destroy(pf_ctx *ctx);
+
+/* ------------------------------------------------------------------------------------
+ * Operator level.  Stateless single operations on caller-owned DEVICE arrays, enqueued
+ * on `stream` (a cudaStream_t, NULL = legacy default stream) and not synchronised
+ * unless stated.  These are the building blocks of pf_load_step, exposed for checking
+ * and for callers with their own drivers.
+ * ------------------------------------------------------------------------------------ */
+
+/* Grid descriptor: device pointers may be NULL where stated. */
+typedef struct {
+  int nx, ny;
+  double hx, hy;                /* element sizes Lx/nx, Ly/ny */
+  const uint8_t *elem_active;   /* device, nx*ny bytes, or NULL = all active */
+  const uint8_t *dof_mask;      /* device, N bytes from pf_op_dof_mask, or NULL: no DOF
+                                   constrained (operators return plain K x) */
+} pf_grid;
+
+/* Material in the notation of Sec. 2: shear modulus mu, bulk modulus K, deviatoric
+ * factor cdim (1/3 plane strain, 1/2 plane stress), eta, G_c, l. */
+typedef struct {
+  double mu, K, cdim, eta, Gc, l;
+} pf_material;
+
+pf_status pf_material_make(double E, double nu, double Gc, double l, double k_res,
+                           int plane, pf_material *out);
+
+/* dof_mask[n] bit0: u_x constrained, bit1: u_y constrained, bit2: d constrained,
+ * bit3: node without active element (then all DOFs constrained at 0), from node flags
+ * and the element mask.  node_flags, elem_active (may be NULL), dof_mask: device arrays. */
+pf_status pf_op_dof_mask(int nx, int ny, const uint8_t *node_flags,
+                         const uint8_t *elem_active, uint8_t *dof_mask, void *stream);
+
+/* Internal force of the momentum balance, F = sum_e sum_q w B^T sigma(eps(u), d)
+ * (weak form F_u of Sec. 3.2 without the boundary term), over all 2N DOFs, FP64.
+ * `tension` (may be NULL) receives one byte per element, bit q set where
+ * tr eps > 0 at Gauss point q (the indicator I_+ of Sec. 3.3).  dof_mask ignored. */
+pf_status pf_op_elas_residual(const pf_grid *g, const pf_material *m, const double *u,
+                              const double *d, double *F, uint8_t *tension, void *stream);
+
+/* y = K_uu x, the tangent of F for a frozen indicator `tension` (stress increment of
+ * Sec. 3.3 at fixed d).  Rows/columns of constrained DOFs (dof_mask) are zeroed. dtype
+ * PF_F64 or PF_F32 for d, x, y. */
+pf_status pf_op_elas_apply(const pf_grid *g, const pf_material *m, int dtype, const void *d,
+                           const uint8_t *tension, const void *x, void *y, void *stream);
+/* diag[i] = (K_uu)_ii for free DOFs, 0 for constrained ones. */
+pf_status pf_op_elas_diag(const pf_grid *g, const pf_material *m, int dtype, const void *d,
+                          const uint8_t *tension, void *diag, void *stream);
+
+/* y = K_dd x = sum_q w [c_q N N^T + kappa grad N . grad N^T] x (evolution equation
+ * tangent, Sec. 3.2; AT2: c_q = G_c/l + 2 H_q (+ K~_q), kappa = G_c l).  c: 4*ne per
+ * Gauss point.  Constrained rows/columns (dof_mask bit2) zeroed. */
+pf_status pf_op_damage_apply(const pf_grid *g, int dtype, const void *c, double kappa,
+                             const void *x, void *y, void *stream);
+pf_status pf_op_damage_diag(const pf_grid *g, int dtype, const void *c, double kappa,
+                            void *diag, void *stream);
+/* b = sum_q w 2 H_q N (AT2 driving term), all N DOFs, FP64. */
+pf_status pf_op_damage_rhs(const pf_grid *g, const double *H, double *b, void *stream);
+
+/* Per Gauss point (FP64): psi = Psi+(eps(u)) (Sec. 2) and Hout = max(Hprev, psi)
+ * (history update).  psi may be NULL. */
+pf_status pf_op_qp_energy(const pf_grid *g, const pf_material *m, const double *u,
+                          const double *Hprev, double *psi, double *Hout, void *stream);
+
+/* Fixed-stress coefficient (Sec. 3.4-3.5), per Gauss point, FP64:
+ *   active = Psi+ > psi_crit && Psi+ > Hprev && d_q < 0.95 (strict),
+ *   c_aug  = G_c/l + 2 max(Hprev, Psi+) + (active ? -4 (1-d_q)^2/g(d_q) Q_S : 0),
+ * Q_S1 = K<tr>_+^2, Q_S2 = 2 mu e.e, Q_S3 = sum.  active: one byte per Gauss point. */
+pf_status pf_op_fs_coeff(const pf_grid *g, const pf_material *m, int scheme,
+                         double psi_crit, const double *u, const double *d,
+                         const double *Hprev, double *c_aug, uint8_t *active,
+                         void *stream);
+/* Predicted history (Sec. 3.3 with the Delta d > 0 rule of Sec. 3.5), FP64:
+ *   s = 1 + 2(1-d_q)/g(d_q) max(Delta d_q, 0); S1: <tr>_+ -> s<tr>_+; S2: e.e -> s^2 e.e;
+ *   S3: both; Hhalf = max(Hprev, active ? Psi_hat : Psi+). */
+pf_status pf_op_fs_predict(const pf_grid *g, const pf_material *m, int scheme,
+                           const double *u, const double *d, const double *dd,
+                           const double *Hprev, const uint8_t *active, double *Hhalf,
+                           void *stream);
+
+/* Reaction: sum of F component `dir` over nodes with PF_LOAD_X (dir 0) / PF_LOAD_Y
+ * (dir 1) that have an active element.  Result written to *out (host), synchronises
+ * `stream`.  Uses a device scratch buffer allocated by the call. */
+pf_status pf_op_reaction(const pf_grid *g, const uint8_t *node_flags, const double *F,
+                         int dir, double *out, void *stream);
+
+/* Staggered residual (reading of Sec. 3.1): with H = max(Hprev, Psi+(u)),
+ *   out = max over free d DOFs of |(K_dd(H) d - b(H))_i / (K_dd(H))_ii|.
+ * FP64.  Synchronises `stream`; allocates device scratch for the call. */
+pf_status pf_op_stag_residual(const pf_grid *g, const pf_material *m, const double *u,
+                              const double *d, const double *Hprev, double *out,
+                              void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PF_H */

@@ -1,0 +1,222 @@
+"""ctypes binding of libpf (C ABI in include/pf.h): argument marshalling only.
+
+Every computation runs in the CUDA library.  ``lib()`` raises ``LibraryMissing`` when
+libpf.so has not been built; nothing here falls back to another implementation.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpf.so")
+
+PF_OK, PF_EINVAL, PF_ENOMEM, PF_ENOTCONV, PF_ECUDA, PF_ETIMEOUT, PF_EBUSY = range(7)
+ST, S1, S2, S3 = 0, 1, 2, 3
+SCHEMES = {"ST": ST, "standard": ST, "S1": S1, "S2": S2, "S3": S3}
+FP64, FP32_IR = 0, 1
+PRECOND_JACOBI, PRECOND_GMG = 0, 1
+F64, F32 = 0, 1
+
+
+class LibraryMissing(RuntimeError):
+    pass
+
+
+class PfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class Mesh(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("Lx", C.c_double), ("Ly", C.c_double),
+                ("elem_active", C.c_void_p), ("node_flags", C.c_void_p), ("plane", C.c_int),
+                ("precision", C.c_int), ("reaction_dir", C.c_int), ("precond", C.c_int)]
+
+
+class Options(C.Structure):
+    _fields_ = [("tol_nr", C.c_double), ("tol_lin", C.c_double), ("tol_inner", C.c_double),
+                ("max_newton", C.c_int), ("max_stag", C.c_int), ("max_lin", C.c_int),
+                ("max_refine", C.c_int), ("psi_crit", C.c_double), ("project", C.c_int),
+                ("check_every", C.c_int)]
+
+
+class StepResult(C.Structure):
+    _fields_ = [("ubar", C.c_double), ("reaction", C.c_double), ("stag_residual", C.c_double),
+                ("stag_iters", C.c_int), ("newton_u", C.c_int), ("lin_u", C.c_int),
+                ("lin_d", C.c_int), ("d_solves", C.c_int), ("refine_steps", C.c_int),
+                ("converged", C.c_int), ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("hx", C.c_double), ("hy", C.c_double),
+                ("elem_active", C.c_void_p), ("dof_mask", C.c_void_p)]
+
+
+class Material(C.Structure):
+    _fields_ = [("mu", C.c_double), ("K", C.c_double), ("cdim", C.c_double),
+                ("eta", C.c_double), ("Gc", C.c_double), ("l", C.c_double)]
+
+
+_LIB = None
+P = C.c_void_p
+I = C.c_int
+D = C.c_double
+S = C.c_int  # pf_status
+
+_PROTOS = {
+    "pf_default_options": (None, [C.POINTER(Options)]),
+    "pf_status_string": (C.c_char_p, [I]),
+    "pf_material_make": (S, [D, D, D, D, D, I, C.POINTER(Material)]),
+    "pf_create": (S, [C.POINTER(Mesh), D, D, D, D, D, C.POINTER(P)]),
+    "pf_set_options": (S, [P, C.POINTER(Options)]),
+    "pf_get_options": (S, [P, C.POINTER(Options)]),
+    "pf_load_step": (S, [P, D, I, D, C.POINTER(StepResult)]),
+    "pf_get_fields": (S, [P, P, P, P]),
+    "pf_set_fields": (S, [P, P, P, P, D]),
+    "pf_state_size": (C.c_size_t, [P]),
+    "pf_get_state": (S, [P, P, C.c_size_t]),
+    "pf_set_state": (S, [P, P, C.c_size_t]),
+    "pf_sizes": (S, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "pf_launch_count": (C.c_int64, [P]),
+    "pf_last_error": (C.c_char_p, [P]),
+    "pf_destroy": (None, [P]),
+    "pf_op_dof_mask": (S, [I, I, P, P, P, P]),
+    "pf_op_elas_residual": (S, [C.POINTER(Grid), C.POINTER(Material), P, P, P, P, P]),
+    "pf_op_elas_apply": (S, [C.POINTER(Grid), C.POINTER(Material), I, P, P, P, P, P]),
+    "pf_op_elas_diag": (S, [C.POINTER(Grid), C.POINTER(Material), I, P, P, P, P]),
+    "pf_op_damage_apply": (S, [C.POINTER(Grid), I, P, D, P, P, P]),
+    "pf_op_damage_diag": (S, [C.POINTER(Grid), I, P, D, P, P]),
+    "pf_op_damage_rhs": (S, [C.POINTER(Grid), P, P, P]),
+    "pf_op_qp_energy": (S, [C.POINTER(Grid), C.POINTER(Material), P, P, P, P, P]),
+    "pf_op_fs_coeff": (S, [C.POINTER(Grid), C.POINTER(Material), I, D, P, P, P, P, P, P]),
+    "pf_op_fs_predict": (S, [C.POINTER(Grid), C.POINTER(Material), I, P, P, P, P, P, P, P]),
+    "pf_op_reaction": (S, [C.POINTER(Grid), P, P, I, C.POINTER(D), P]),
+    "pf_op_stag_residual": (S, [C.POINTER(Grid), C.POINTER(Material), P, P, P, C.POINTER(D), P]),
+}
+
+
+def lib():
+    """Load libpf.so (built by paper_2209_07969_gb300.build); raise if it is missing."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise LibraryMissing(f"{LIB_PATH} not built; run python -m paper_2209_07969_gb300.build")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _PROTOS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def check(status, what="libpf call", ctx=None):
+    if status != PF_OK:
+        msg = what
+        if ctx:
+            msg += ": " + lib().pf_last_error(ctx).decode()
+        raise PfError(status, msg)
+
+
+def default_options():
+    o = Options()
+    lib().pf_default_options(C.byref(o))
+    return o
+
+
+def material(E, nu, Gc, l, k_res, plane=0):
+    m = Material()
+    check(lib().pf_material_make(E, nu, Gc, l, k_res, plane, C.byref(m)), "pf_material_make")
+    return m
+
+
+def grid(nx, ny, hx, hy, elem_active_ptr=None, dof_mask_ptr=None):
+    return Grid(nx, ny, hx, hy, elem_active_ptr, dof_mask_ptr)
+
+
+class Simulation:
+    """One fracture simulation resident on the current CUDA device (pf_create)."""
+
+    def __init__(self, spec, precision=FP64, precond=PRECOND_JACOBI, options=None):
+        self.spec = spec
+        self._flags = np.ascontiguousarray(spec.node_flags, dtype=np.uint8)
+        self._active = None
+        if spec.elem_active is not None and not np.all(spec.elem_active):
+            self._active = np.ascontiguousarray(spec.elem_active, dtype=np.uint8)
+        mesh = Mesh(spec.nx, spec.ny, spec.Lx, spec.Ly,
+                    self._active.ctypes.data if self._active is not None else None,
+                    self._flags.ctypes.data, spec.plane, precision, spec.reaction_dir, precond)
+        ctx = P()
+        check(lib().pf_create(C.byref(mesh), spec.E, spec.nu, spec.Gc, spec.l, spec.eta,
+                              C.byref(ctx)), "pf_create")
+        self.ctx = ctx
+        self.nn = (spec.nx + 1) * (spec.ny + 1)
+        self.nq = 4 * spec.nx * spec.ny
+        if options is not None:
+            self.set_options(**options)
+
+    def set_options(self, **kw):
+        o = Options()
+        check(lib().pf_get_options(self.ctx, C.byref(o)), "pf_get_options", self.ctx)
+        for k, v in kw.items():
+            setattr(o, k, v)
+        check(lib().pf_set_options(self.ctx, C.byref(o)), "pf_set_options", self.ctx)
+
+    def load_step(self, d_ubar, scheme=ST, tol=1e-6, raise_on_notconv=False):
+        r = StepResult()
+        s = lib().pf_load_step(self.ctx, float(d_ubar), int(scheme), float(tol), C.byref(r))
+        if s not in (PF_OK, PF_ENOTCONV) or (raise_on_notconv and s != PF_OK):
+            check(s, "pf_load_step", self.ctx)
+        out = r.as_dict()
+        out["status"] = s
+        return out
+
+    def fields(self):
+        u = np.empty(2 * self.nn)
+        d = np.empty(self.nn)
+        H = np.empty(self.nq)
+        check(lib().pf_get_fields(self.ctx, u.ctypes.data, d.ctypes.data, H.ctypes.data),
+              "pf_get_fields", self.ctx)
+        return u, d, H.reshape(-1, 4)
+
+    def set_fields(self, u, d, H, ubar):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        d = np.ascontiguousarray(d, dtype=np.float64)
+        H = np.ascontiguousarray(H, dtype=np.float64)
+        check(lib().pf_set_fields(self.ctx, u.ctypes.data, d.ctypes.data, H.ctypes.data,
+                                  float(ubar)), "pf_set_fields", self.ctx)
+
+    def get_state(self):
+        n = lib().pf_state_size(self.ctx)
+        buf = np.empty(n, dtype=np.uint8)
+        check(lib().pf_get_state(self.ctx, buf.ctypes.data, n), "pf_get_state", self.ctx)
+        return buf
+
+    def set_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        check(lib().pf_set_state(self.ctx, buf.ctypes.data, buf.size), "pf_set_state", self.ctx)
+
+    def launches(self):
+        return int(lib().pf_launch_count(self.ctx))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().pf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

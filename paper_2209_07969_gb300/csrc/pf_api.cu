@@ -1,0 +1,194 @@
+// Operator-level C ABI of libpf: single operations on caller-owned device arrays.
+#include <math.h>
+
+#include "pf_internal.cuh"
+#include "pf_vec.cuh"
+
+using namespace pf;
+
+namespace {
+
+bool grid_ok(const pf_grid *g) {
+  return g && g->nx >= 1 && g->ny >= 1 && g->hx > 0 && g->hy > 0 &&
+         (double)(g->nx + 1) * (double)(g->ny + 1) <= 4.0e8;
+}
+GridD to_dev(const pf_grid *g) { return GridD{g->nx, g->ny, g->hx, g->hy, g->elem_active, g->dof_mask}; }
+MatD to_dev(const pf_material *m) { return MatD{m->mu, m->K, m->cdim, m->eta, m->Gc, m->l}; }
+bool mat_ok(const pf_material *m) {
+  return m && m->mu > 0 && m->K > 0 && m->cdim > 0 && m->eta >= 0 && m->Gc > 0 && m->l > 0;
+}
+pf_status launched() { return cudaGetLastError() == cudaSuccess ? PF_OK : PF_ECUDA; }
+
+// Scratch for a one-off reduction: partials for `blocks` CTAs, the counter and one
+// result slot.  Freed by the destructor after the stream has been synchronised.
+struct Scratch {
+  RedWs ws{};
+  double *res = nullptr;
+  void *base = nullptr;
+  pf_status alloc(int blocks) {
+    ws.max_blocks = blocks;
+    size_t bytes = (size_t)4 * blocks * sizeof(double) + 64;
+    if (cudaMalloc(&base, bytes) != cudaSuccess) return PF_ENOMEM;
+    ws.partials = (double *)base;
+    ws.counter = (unsigned *)((char *)base + (size_t)4 * blocks * sizeof(double));
+    res = (double *)((char *)base + (size_t)4 * blocks * sizeof(double) + 16);
+    return cudaMemset(ws.counter, 0, sizeof(unsigned)) == cudaSuccess ? PF_OK : PF_ECUDA;
+  }
+  ~Scratch() {
+    if (base) cudaFree(base);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+pf_status pf_op_dof_mask(int nx, int ny, const uint8_t *node_flags, const uint8_t *elem_active,
+                         uint8_t *mask, void *stream) {
+  if (nx < 1 || ny < 1 || !node_flags || !mask) return PF_EINVAL;
+  dof_mask(nx, ny, node_flags, elem_active, mask, (cudaStream_t)stream);
+  return launched();
+}
+
+pf_status pf_op_elas_residual(const pf_grid *g, const pf_material *m, const double *u,
+                              const double *d, double *F, uint8_t *tension, void *stream) {
+  if (!grid_ok(g) || !mat_ok(m) || !u || !d || !F) return PF_EINVAL;
+  elas_residual(to_dev(g), to_dev(m), u, d, F, tension, (cudaStream_t)stream);
+  return launched();
+}
+
+pf_status pf_op_elas_apply(const pf_grid *g, const pf_material *m, int dtype, const void *d,
+                           const uint8_t *tension, const void *x, void *y, void *stream) {
+  if (!grid_ok(g) || !mat_ok(m) || !d || !tension || !x || !y) return PF_EINVAL;
+  if (dtype == PF_F64)
+    elas_apply<double>(to_dev(g), to_dev(m), (const double *)d, tension, (const double *)x,
+                       (double *)y, (cudaStream_t)stream);
+  else if (dtype == PF_F32)
+    elas_apply<float>(to_dev(g), to_dev(m), (const float *)d, tension, (const float *)x,
+                      (float *)y, (cudaStream_t)stream);
+  else
+    return PF_EINVAL;
+  return launched();
+}
+
+pf_status pf_op_elas_diag(const pf_grid *g, const pf_material *m, int dtype, const void *d,
+                          const uint8_t *tension, void *diag, void *stream) {
+  if (!grid_ok(g) || !mat_ok(m) || !d || !tension || !diag) return PF_EINVAL;
+  if (dtype == PF_F64)
+    elas_diag<double>(to_dev(g), to_dev(m), (const double *)d, tension, (double *)diag,
+                      (cudaStream_t)stream);
+  else if (dtype == PF_F32)
+    elas_diag<float>(to_dev(g), to_dev(m), (const float *)d, tension, (float *)diag,
+                     (cudaStream_t)stream);
+  else
+    return PF_EINVAL;
+  return launched();
+}
+
+pf_status pf_op_damage_apply(const pf_grid *g, int dtype, const void *c, double kappa,
+                             const void *x, void *y, void *stream) {
+  if (!grid_ok(g) || !c || !x || !y || !(kappa >= 0)) return PF_EINVAL;
+  if (dtype == PF_F64)
+    damage_apply<double>(to_dev(g), (const double *)c, kappa, (const double *)x, (double *)y,
+                         (cudaStream_t)stream);
+  else if (dtype == PF_F32)
+    damage_apply<float>(to_dev(g), (const float *)c, kappa, (const float *)x, (float *)y,
+                        (cudaStream_t)stream);
+  else
+    return PF_EINVAL;
+  return launched();
+}
+
+pf_status pf_op_damage_diag(const pf_grid *g, int dtype, const void *c, double kappa,
+                            void *diag, void *stream) {
+  if (!grid_ok(g) || !c || !diag || !(kappa >= 0)) return PF_EINVAL;
+  if (dtype == PF_F64)
+    damage_diag<double>(to_dev(g), (const double *)c, kappa, (double *)diag, (cudaStream_t)stream);
+  else if (dtype == PF_F32)
+    damage_diag<float>(to_dev(g), (const float *)c, kappa, (float *)diag, (cudaStream_t)stream);
+  else
+    return PF_EINVAL;
+  return launched();
+}
+
+pf_status pf_op_damage_rhs(const pf_grid *g, const double *H, double *b, void *stream) {
+  if (!grid_ok(g) || !H || !b) return PF_EINVAL;
+  damage_rhs(to_dev(g), H, b, (cudaStream_t)stream);
+  return launched();
+}
+
+pf_status pf_op_qp_energy(const pf_grid *g, const pf_material *m, const double *u,
+                          const double *Hprev, double *psi, double *Hout, void *stream) {
+  if (!grid_ok(g) || !mat_ok(m) || !u || !Hprev || !Hout) return PF_EINVAL;
+  qp_energy(to_dev(g), to_dev(m), u, Hprev, psi, Hout, (cudaStream_t)stream);
+  return launched();
+}
+
+pf_status pf_op_fs_coeff(const pf_grid *g, const pf_material *m, int scheme, double psi_crit,
+                         const double *u, const double *d, const double *Hprev, double *c_aug,
+                         uint8_t *active, void *stream) {
+  if (!grid_ok(g) || !mat_ok(m) || !u || !d || !Hprev || !c_aug || !active ||
+      scheme < PF_ST || scheme > PF_S3)
+    return PF_EINVAL;
+  fs_coeff(to_dev(g), to_dev(m), scheme, psi_crit, u, d, Hprev, c_aug, active,
+           (cudaStream_t)stream);
+  return launched();
+}
+
+pf_status pf_op_fs_predict(const pf_grid *g, const pf_material *m, int scheme, const double *u,
+                           const double *d, const double *dd, const double *Hprev,
+                           const uint8_t *active, double *Hhalf, void *stream) {
+  if (!grid_ok(g) || !mat_ok(m) || !u || !d || !dd || !Hprev || !active || !Hhalf ||
+      scheme < PF_ST || scheme > PF_S3)
+    return PF_EINVAL;
+  fs_predict(to_dev(g), to_dev(m), scheme, u, d, dd, Hprev, active, Hhalf, (cudaStream_t)stream);
+  return launched();
+}
+
+pf_status pf_op_reaction(const pf_grid *g, const uint8_t *node_flags, const double *F, int dir,
+                         double *out, void *stream) {
+  if (!grid_ok(g) || !node_flags || !F || !out || (dir != 0 && dir != 1)) return PF_EINVAL;
+  const size_t nn = (size_t)(g->nx + 1) * (g->ny + 1);
+  Scratch s;
+  pf_status st = s.alloc(4096);
+  if (st != PF_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  reaction(nn, node_flags, dir, F, s.res, s.ws, cs);
+  if (cudaGetLastError() != cudaSuccess) return PF_ECUDA;
+  if (cudaMemcpyAsync(out, s.res, sizeof(double), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+      cudaStreamSynchronize(cs) != cudaSuccess)
+    return PF_ECUDA;
+  return PF_OK;
+}
+
+pf_status pf_op_stag_residual(const pf_grid *g, const pf_material *m, const double *u,
+                              const double *d, const double *Hprev, double *out, void *stream) {
+  if (!grid_ok(g) || !mat_ok(m) || !u || !d || !Hprev || !out) return PF_EINVAL;
+  const size_t nn = (size_t)(g->nx + 1) * (g->ny + 1), nq = (size_t)4 * g->nx * g->ny;
+  GridD gd = to_dev(g);
+  GridD gfull = gd;
+  gfull.dofm = nullptr;
+  MatD md = to_dev(m);
+  Scratch s;
+  pf_status st = s.alloc(4096);
+  if (st != PF_OK) return st;
+  double *buf = nullptr;
+  if (cudaMalloc(&buf, (2 * nq + 3 * nn) * sizeof(double)) != cudaSuccess) return PF_ENOMEM;
+  double *H = buf, *c = buf + nq, *Kd = buf + 2 * nq, *b = Kd + nn, *diag = b + nn;
+  cudaStream_t cs = (cudaStream_t)stream;
+  qp_energy(gd, md, u, Hprev, nullptr, H, cs);
+  coef<double>(nq, m->Gc / m->l, H, c, cs);
+  damage_rhs(gd, H, b, cs);
+  damage_apply<double>(gfull, c, m->Gc * m->l, d, Kd, cs);
+  damage_diag<double>(gfull, c, m->Gc * m->l, diag, cs);
+  stag_max(nn, gd.dofm, Kd, b, diag, s.res, s.ws, cs);
+  pf_status ret = PF_OK;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(out, s.res, sizeof(double), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+      cudaStreamSynchronize(cs) != cudaSuccess)
+    ret = PF_ECUDA;
+  cudaFree(buf);
+  return ret;
+}
+
+}  // extern "C"

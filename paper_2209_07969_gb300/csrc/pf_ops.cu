@@ -1,0 +1,639 @@
+// Matrix-free Q1 operators and per-Gauss-point kernels of the staggered phase-field
+// method (arXiv 2209.07969), written for sm_103a.
+//
+// Operator kernels use one 256-thread CTA per tile of TX x TY nodes.  The CTA stages
+// the (TX+2) x (TY+2) node patch in shared memory, computes the element vectors of the
+// (TX+1) x (TY+1) elements that touch its nodes (the one-element halo is recomputed by
+// the neighbouring CTA as well), and sums the four element contributions of every
+// owned node.  No atomics: results are deterministic and independent of the launch.
+//
+// Element quantities (Sec. 2 and 3.2): 2x2 Gauss points at unit coordinates
+// s, t in {G0, G1} = {(1 - 1/sqrt3)/2, (1 + 1/sqrt3)/2}; N_a bilinear; weight hx hy/4.
+#include <math.h>
+#include <stdio.h>
+
+#include "pf_internal.cuh"
+
+namespace pf {
+
+__device__ __forceinline__ double gp_lo() { return 0.21132486540518711775; }  // (1-1/sqrt3)/2
+__device__ __forceinline__ double gp_hi() { return 0.78867513459481288225; }  // (1+1/sqrt3)/2
+
+template <class T>
+__device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+// ------------------------------------------------------------------------------------
+// Reductions: warp shuffle -> CTA -> per-CTA partials -> last-arriving CTA sums the
+// partials in a fixed order (deterministic) and runs an epilogue on the totals.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Sums NV values over the whole grid.  Returns true in thread 0 of the last CTA, with
+// tot[] holding the totals; all other threads return false.  blockDim.x must be a
+// multiple of 32 and at most 1024.  `is_max` selects max instead of sum.
+template <int NV>
+__device__ bool grid_reduce(double (&v)[NV], const RedWs ws, double (&tot)[NV],
+                            bool is_max = false) {
+  __shared__ double sh[NV][32];
+  __shared__ bool am_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  const unsigned nblk = gridDim.x * gridDim.y;
+  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = is_max ? warp_max(v[k]) : warp_sum(v[k]);
+    if (lane == 0) sh[k][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = sh[k][0];
+      for (int w = 1; w < nw; ++w) s = is_max ? fmax(s, sh[k][w]) : s + sh[k][w];
+      ws.partials[k * ws.max_blocks + bid] = s;
+    }
+    __threadfence();
+    unsigned prev = atomicAdd(ws.counter, 1u);
+    am_last = (prev == nblk - 1);
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = is_max ? -INFINITY : 0.0;
+    for (unsigned i = threadIdx.x; i < nblk; i += blockDim.x) {
+      double p = __ldcg(ws.partials + k * ws.max_blocks + i);
+      s = is_max ? fmax(s, p) : s + p;
+    }
+    s = is_max ? warp_max(s) : warp_sum(s);
+    __syncthreads();
+    if (lane == 0) sh[k][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return false;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = sh[k][0];
+    for (int w = 1; w < nw; ++w) s = is_max ? fmax(s, sh[k][w]) : s + sh[k][w];
+    tot[k] = s;
+  }
+  *ws.counter = 0u;
+  return true;
+}
+
+// Epilogue for the fused matvec + dot: CG step length, or MINRES delta.
+__device__ __forceinline__ void krylov_epilogue(int epi, KrylovScal *sc, double dot) {
+  if (epi == EPI_CG_ALPHA) {
+    sc->pq = dot;
+    if (dot > 0.0 && isfinite(dot) && sc->rz > 0.0) {
+      sc->alpha = sc->rz / dot;
+    } else {
+      sc->alpha = 0.0;
+      sc->breakdown = 1;
+    }
+  } else if (epi == EPI_MINRES_DELTA) {
+    sc->pq = dot;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Elasticity: tangent apply, tangent diagonal, nonlinear internal force.
+// ------------------------------------------------------------------------------------
+enum { EL_APPLY = 0, EL_DIAG = 1, EL_RESID = 2 };
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_elas(GridD g, MatD mt, const T *__restrict__ d, const uint8_t *__restrict__ tens_in,
+       const T *__restrict__ x, T *__restrict__ y, uint8_t *__restrict__ tens_out,
+       KrylovScal *sc, RedWs ws, int epi) {
+  constexpr int PX = TX + 2, PY = TY + 2, EX = TX + 1, EY = TY + 1, NE = EX * EY;
+  __shared__ T sx[2][PY * PX];
+  __shared__ T sd[PY * PX];
+  __shared__ T ef[8][NE];
+  const int nx = g.nx, ny = g.ny, ld = nx + 1;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+
+  for (int t = threadIdx.x; t < PX * PY; t += TILE_THREADS) {
+    const int li = t % PX, lj = t / PX;
+    const int gi = i0 - 1 + li, gj = j0 - 1 + lj;
+    const bool in = gi >= 0 && gi <= nx && gj >= 0 && gj <= ny;
+    const size_t n = (size_t)gj * ld + gi;
+    T vx = T(0), vy = T(0), vd = T(0);
+    if (in) {
+      vd = ldg(d + n);
+      if (MODE != EL_DIAG) {
+        vx = ldg(x + 2 * n);
+        vy = ldg(x + 2 * n + 1);
+        if (MODE == EL_APPLY && g.dofm) {
+          const uint8_t mk = ldg(g.dofm + n);
+          if (mk & 1) vx = T(0);
+          if (mk & 2) vy = T(0);
+        }
+      }
+    }
+    sx[0][t] = vx;
+    sx[1][t] = vy;
+    sd[t] = vd;
+  }
+  __syncthreads();
+
+  const T ihx = T(1.0 / g.hx), ihy = T(1.0 / g.hy), w = T(0.25 * g.hx * g.hy);
+  const T mu = T(mt.mu), K = T(mt.K), cd = T(mt.cdim), eta = T(mt.eta);
+  const T G0 = T(gp_lo()), G1 = T(gp_hi());
+  for (int t = threadIdx.x; t < NE; t += TILE_THREADS) {
+    const int le = t % EX, me = t / EX;
+    const int ei = i0 - 1 + le, ej = j0 - 1 + me;
+    T f[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] = T(0);
+    bool live = ei >= 0 && ei < nx && ej >= 0 && ej < ny;
+    size_t e = 0;
+    if (live) {
+      e = (size_t)ej * nx + ei;
+      if (g.active && !ldg(g.active + e)) live = false;
+    }
+    if (live) {
+      const int p0 = me * PX + le, p1 = p0 + 1, p2 = p0 + PX, p3 = p2 + 1;
+      const T d0 = sd[p0], d1 = sd[p1], d2 = sd[p2], d3 = sd[p3];
+      T ux0 = 0, ux1 = 0, ux2 = 0, ux3 = 0, uy0 = 0, uy1 = 0, uy2 = 0, uy3 = 0;
+      if (MODE != EL_DIAG) {
+        ux0 = sx[0][p0]; ux1 = sx[0][p1]; ux2 = sx[0][p2]; ux3 = sx[0][p3];
+        uy0 = sx[1][p0]; uy1 = sx[1][p1]; uy2 = sx[1][p2]; uy3 = sx[1][p3];
+      }
+      uint8_t tb = (MODE == EL_RESID) ? 0 : ldg(tens_in + e);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T s = (q & 1) ? G1 : G0, tt = (q & 2) ? G1 : G0;
+        const T s1 = T(1) - s, t1 = T(1) - tt;
+        const T dq = s1 * t1 * d0 + s * t1 * d1 + s1 * tt * d2 + s * tt * d3;
+        const T om = T(1) - dq;
+        const T gq = om * om + eta;
+        if (MODE == EL_DIAG) {
+          const T kv = ((tb >> q) & 1) ? gq * K : K;
+          const T Dn = gq * T(2) * mu * (T(1) - cd) + kv;  // D00 = D11
+          const T Ds = gq * mu;                              // D22
+          // dN/dx: (-t1, t1, -tt, tt)*ihx ; dN/dy: (-s1, -s, s1, s)*ihy
+          const T ax[4] = {t1 * ihx, t1 * ihx, tt * ihx, tt * ihx};
+          const T ay[4] = {s1 * ihy, s * ihy, s1 * ihy, s * ihy};
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            f[2 * a] += w * (Dn * ax[a] * ax[a] + Ds * ay[a] * ay[a]);
+            f[2 * a + 1] += w * (Dn * ay[a] * ay[a] + Ds * ax[a] * ax[a]);
+          }
+        } else {
+          const T exx = (t1 * (ux1 - ux0) + tt * (ux3 - ux2)) * ihx;
+          const T eyy = (s1 * (uy2 - uy0) + s * (uy3 - uy1)) * ihy;
+          const T gxy = (s1 * (ux2 - ux0) + s * (ux3 - ux1)) * ihy +
+                        (t1 * (uy1 - uy0) + tt * (uy3 - uy2)) * ihx;
+          const T tr = exx + eyy;
+          T vol;
+          if (MODE == EL_RESID) {
+            vol = tr > T(0) ? gq * K * tr : K * tr;
+            if (tr > T(0)) tb |= (uint8_t)(1u << q);
+          } else {
+            vol = ((tb >> q) & 1) ? gq * K * tr : K * tr;
+          }
+          const T gm2 = gq * T(2) * mu;
+          const T sxx = gm2 * (exx - cd * tr) + vol;
+          const T syy = gm2 * (eyy - cd * tr) + vol;
+          const T sxy = gq * mu * gxy;
+          const T Ax = w * ihx * sxx, Ay = w * ihy * sxy;
+          const T Bx = w * ihx * sxy, By = w * ihy * syy;
+          f[0] += -t1 * Ax - s1 * Ay;
+          f[1] += -t1 * Bx - s1 * By;
+          f[2] += t1 * Ax - s * Ay;
+          f[3] += t1 * Bx - s * By;
+          f[4] += -tt * Ax + s1 * Ay;
+          f[5] += -tt * Bx + s1 * By;
+          f[6] += tt * Ax + s * Ay;
+          f[7] += tt * Bx + s * By;
+        }
+      }
+      if (MODE == EL_RESID && tens_out) tens_out[e] = tb;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ef[k][t] = f[k];
+  }
+  __syncthreads();
+
+  const int li = threadIdx.x % TX, lj = threadIdx.x / TX;
+  const int gi = i0 + li, gj = j0 + lj;
+  double dot = 0.0;
+  if (gi <= nx && gj <= ny) {
+    const int e00 = lj * EX + li, e10 = e00 + 1, e01 = e00 + EX, e11 = e01 + 1;
+    T fx = ef[6][e00] + ef[4][e10] + ef[2][e01] + ef[0][e11];
+    T fy = ef[7][e00] + ef[5][e10] + ef[3][e01] + ef[1][e11];
+    const size_t n = (size_t)gj * ld + gi;
+    if (MODE != EL_RESID && g.dofm) {
+      const uint8_t mk = ldg(g.dofm + n);
+      if (mk & 1) fx = T(0);
+      if (mk & 2) fy = T(0);
+    }
+    y[2 * n] = fx;
+    y[2 * n + 1] = fy;
+    if (MODE == EL_APPLY && epi != EPI_NONE) {
+      const int p = (lj + 1) * PX + li + 1;
+      dot = (double)sx[0][p] * (double)fx + (double)sx[1][p] * (double)fy;
+    }
+  }
+  if (MODE == EL_APPLY && epi != EPI_NONE) {
+    double v[1] = {dot}, tot[1];
+    if (grid_reduce<1>(v, ws, tot)) krylov_epilogue(epi, sc, tot[0]);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Evolution equation: K_dd apply / diagonal / AT2 right-hand side.
+// ------------------------------------------------------------------------------------
+enum { DM_APPLY = 0, DM_DIAG = 1, DM_RHS = 2 };
+
+template <class T, class C, int MODE>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_damage(GridD g, const C *__restrict__ c, double kappa_d, const T *__restrict__ x,
+         T *__restrict__ y, KrylovScal *sc, RedWs ws, int epi) {
+  constexpr int PX = TX + 2, PY = TY + 2, EX = TX + 1, EY = TY + 1, NE = EX * EY;
+  __shared__ T sxv[PY * PX];
+  __shared__ T ef[4][NE];
+  const int nx = g.nx, ny = g.ny, ld = nx + 1;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  if (MODE == DM_APPLY) {
+    for (int t = threadIdx.x; t < PX * PY; t += TILE_THREADS) {
+      const int li = t % PX, lj = t / PX;
+      const int gi = i0 - 1 + li, gj = j0 - 1 + lj;
+      T v = T(0);
+      if (gi >= 0 && gi <= nx && gj >= 0 && gj <= ny) {
+        const size_t n = (size_t)gj * ld + gi;
+        v = ldg(x + n);
+        if (g.dofm && (ldg(g.dofm + n) & 4)) v = T(0);
+      }
+      sxv[t] = v;
+    }
+    __syncthreads();
+  }
+  const T ihx = T(1.0 / g.hx), ihy = T(1.0 / g.hy), w = T(0.25 * g.hx * g.hy);
+  const T kappa = T(kappa_d);
+  const T G0 = T(gp_lo()), G1 = T(gp_hi());
+  for (int t = threadIdx.x; t < NE; t += TILE_THREADS) {
+    const int le = t % EX, me = t / EX;
+    const int ei = i0 - 1 + le, ej = j0 - 1 + me;
+    T f[4] = {T(0), T(0), T(0), T(0)};
+    bool live = ei >= 0 && ei < nx && ej >= 0 && ej < ny;
+    size_t e = 0;
+    if (live) {
+      e = (size_t)ej * nx + ei;
+      if (g.active && !ldg(g.active + e)) live = false;
+    }
+    if (live) {
+      T x0 = 0, x1 = 0, x2 = 0, x3 = 0;
+      if (MODE == DM_APPLY) {
+        const int p0 = me * PX + le;
+        x0 = sxv[p0]; x1 = sxv[p0 + 1]; x2 = sxv[p0 + PX]; x3 = sxv[p0 + PX + 1];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T s = (q & 1) ? G1 : G0, tt = (q & 2) ? G1 : G0;
+        const T s1 = T(1) - s, t1 = T(1) - tt;
+        const T N[4] = {s1 * t1, s * t1, s1 * tt, s * tt};
+        const T cq = T(ldg(c + 4 * e + q));
+        if (MODE == DM_RHS) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a) f[a] += w * T(2) * cq * N[a];
+        } else if (MODE == DM_DIAG) {
+          const T ax[4] = {t1 * ihx, t1 * ihx, tt * ihx, tt * ihx};
+          const T ay[4] = {s1 * ihy, s * ihy, s1 * ihy, s * ihy};
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+            f[a] += w * (cq * N[a] * N[a] + kappa * (ax[a] * ax[a] + ay[a] * ay[a]));
+        } else {
+          const T xq = N[0] * x0 + N[1] * x1 + N[2] * x2 + N[3] * x3;
+          const T gx = (t1 * (x1 - x0) + tt * (x3 - x2)) * ihx;
+          const T gy = (s1 * (x2 - x0) + s * (x3 - x1)) * ihy;
+          const T m = w * cq * xq, kx = w * kappa * gx * ihx, ky = w * kappa * gy * ihy;
+          // dN/dx * ihx^-1: (-t1, t1, -tt, tt); dN/dy * ihy^-1: (-s1, -s, s1, s)
+          f[0] += m * N[0] - t1 * kx - s1 * ky;
+          f[1] += m * N[1] + t1 * kx - s * ky;
+          f[2] += m * N[2] - tt * kx + s1 * ky;
+          f[3] += m * N[3] + tt * kx + s * ky;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ef[k][t] = f[k];
+  }
+  __syncthreads();
+  const int li = threadIdx.x % TX, lj = threadIdx.x / TX;
+  const int gi = i0 + li, gj = j0 + lj;
+  double dot = 0.0;
+  if (gi <= nx && gj <= ny) {
+    const int e00 = lj * EX + li, e10 = e00 + 1, e01 = e00 + EX, e11 = e01 + 1;
+    T v = ef[3][e00] + ef[2][e10] + ef[1][e01] + ef[0][e11];
+    const size_t n = (size_t)gj * ld + gi;
+    if (MODE != DM_RHS && g.dofm && (ldg(g.dofm + n) & 4)) v = T(0);
+    y[n] = v;
+    if (MODE == DM_APPLY && epi != EPI_NONE) dot = (double)sxv[(lj + 1) * PX + li + 1] * (double)v;
+  }
+  if (MODE == DM_APPLY && epi != EPI_NONE) {
+    double vv[1] = {dot}, tot[1];
+    if (grid_reduce<1>(vv, ws, tot)) krylov_epilogue(epi, sc, tot[0]);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Per-Gauss-point kernels (one thread per element, FP64).
+// ------------------------------------------------------------------------------------
+struct QpStrain {
+  double exx[4], eyy[4], exy[4];
+};
+
+__device__ __forceinline__ void element_nodes(const GridD &g, size_t e, size_t (&n)[4]) {
+  const int ei = (int)(e % g.nx), ej = (int)(e / g.nx);
+  const size_t ld = (size_t)g.nx + 1;
+  n[0] = (size_t)ej * ld + ei;
+  n[1] = n[0] + 1;
+  n[2] = n[0] + ld;
+  n[3] = n[2] + 1;
+}
+
+__device__ __forceinline__ void element_strains(const GridD &g, const double *u,
+                                                const size_t (&n)[4], QpStrain &S) {
+  double ux[4], uy[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(u) + n[a]);
+    ux[a] = v.x;
+    uy[a] = v.y;
+  }
+  const double ihx = 1.0 / g.hx, ihy = 1.0 / g.hy;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double s = (q & 1) ? gp_hi() : gp_lo(), t = (q & 2) ? gp_hi() : gp_lo();
+    const double s1 = 1.0 - s, t1 = 1.0 - t;
+    S.exx[q] = (t1 * (ux[1] - ux[0]) + t * (ux[3] - ux[2])) * ihx;
+    S.eyy[q] = (s1 * (uy[2] - uy[0]) + s * (uy[3] - uy[1])) * ihy;
+    S.exy[q] = 0.5 * ((s1 * (ux[2] - ux[0]) + s * (ux[3] - ux[1])) * ihy +
+                      (t1 * (uy[1] - uy[0]) + t * (uy[3] - uy[2])) * ihx);
+  }
+}
+
+__device__ __forceinline__ void element_interp(const double *f, const size_t (&n)[4],
+                                               double (&fq)[4]) {
+  const double f0 = __ldg(f + n[0]), f1 = __ldg(f + n[1]), f2 = __ldg(f + n[2]),
+               f3 = __ldg(f + n[3]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double s = (q & 1) ? gp_hi() : gp_lo(), t = (q & 2) ? gp_hi() : gp_lo();
+    fq[q] = (1.0 - s) * (1.0 - t) * f0 + s * (1.0 - t) * f1 + (1.0 - s) * t * f2 + s * t * f3;
+  }
+}
+
+__device__ __forceinline__ void invariants(const MatD &m, double exx, double eyy, double exy,
+                                           double &tr, double &ee) {
+  tr = exx + eyy;
+  ee = exx * exx + eyy * eyy + 2.0 * exy * exy - m.cdim * tr * tr;
+}
+
+__device__ __forceinline__ double psi_plus(const MatD &m, double tr, double ee) {
+  const double tp = tr > 0.0 ? tr : 0.0;
+  return m.mu * ee + 0.5 * m.K * tp * tp;
+}
+
+__global__ void k_qp_energy(GridD g, MatD m, const double *__restrict__ u,
+                            const double *__restrict__ Hprev, double *__restrict__ psi,
+                            double *__restrict__ Hout) {
+  const size_t ne = (size_t)g.nx * g.ny;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ne;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const bool live = !g.active || g.active[e];
+    double p[4] = {0, 0, 0, 0};
+    if (live) {
+      size_t n[4];
+      element_nodes(g, e, n);
+      QpStrain S;
+      element_strains(g, u, n, S);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        double tr, ee;
+        invariants(m, S.exx[q], S.eyy[q], S.exy[q], tr, ee);
+        p[q] = psi_plus(m, tr, ee);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      Hout[4 * e + q] = fmax(__ldg(Hprev + 4 * e + q), p[q]);
+      if (psi) psi[4 * e + q] = p[q];
+    }
+  }
+}
+
+__device__ __forceinline__ double scheme_Q(const MatD &m, int scheme, double tr, double ee) {
+  const double tp = tr > 0.0 ? tr : 0.0;
+  const double vol = m.K * tp * tp, dev = 2.0 * m.mu * ee;
+  return scheme == PF_S1 ? vol : scheme == PF_S2 ? dev : scheme == PF_S3 ? vol + dev : 0.0;
+}
+
+__global__ void k_fs_coeff(GridD g, MatD m, int scheme, double psi_crit,
+                           const double *__restrict__ u, const double *__restrict__ d,
+                           const double *__restrict__ Hprev, double *__restrict__ c_aug,
+                           uint8_t *__restrict__ active) {
+  const size_t ne = (size_t)g.nx * g.ny;
+  const double floor_c = m.Gc / m.l;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ne;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const bool live = !g.active || g.active[e];
+    size_t n[4];
+    element_nodes(g, e, n);
+    QpStrain S;
+    double dq[4];
+    if (live) {
+      element_strains(g, u, n, S);
+      element_interp(d, n, dq);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double hp = __ldg(Hprev + 4 * e + q);
+      double c = floor_c + 2.0 * hp;
+      uint8_t a = 0;
+      if (live) {
+        double tr, ee;
+        invariants(m, S.exx[q], S.eyy[q], S.exy[q], tr, ee);
+        const double ps = psi_plus(m, tr, ee);
+        const double H = fmax(hp, ps);
+        c = floor_c + 2.0 * H;
+        a = (ps > psi_crit) && (ps > hp) && (dq[q] < 0.95);
+        if (a) {
+          const double om = 1.0 - dq[q];
+          const double gq = om * om + m.eta;
+          c = fmax(c - 4.0 * om * om / gq * scheme_Q(m, scheme, tr, ee), floor_c);
+        }
+      }
+      c_aug[4 * e + q] = c;
+      active[4 * e + q] = a;
+    }
+  }
+}
+
+__global__ void k_fs_predict(GridD g, MatD m, int scheme, const double *__restrict__ u,
+                             const double *__restrict__ d, const double *__restrict__ dd,
+                             const double *__restrict__ Hprev,
+                             const uint8_t *__restrict__ active, double *__restrict__ Hhalf) {
+  const size_t ne = (size_t)g.nx * g.ny;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ne;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const bool live = !g.active || g.active[e];
+    size_t n[4];
+    element_nodes(g, e, n);
+    QpStrain S;
+    double dq[4], ddq[4];
+    if (live) {
+      element_strains(g, u, n, S);
+      element_interp(d, n, dq);
+      element_interp(dd, n, ddq);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double hp = __ldg(Hprev + 4 * e + q);
+      double h = hp;
+      if (live) {
+        double tr, ee;
+        invariants(m, S.exx[q], S.eyy[q], S.exy[q], tr, ee);
+        double ps = psi_plus(m, tr, ee);
+        if (active[4 * e + q]) {
+          const double om = 1.0 - dq[q];
+          const double gq = om * om + m.eta;
+          const double ddp = ddq[q] > 0.0 ? ddq[q] : 0.0;
+          const double sc = 1.0 + 2.0 * om / gq * ddp;  // s = 1 + a Dd+
+          const double tp = tr > 0.0 ? tr : 0.0;
+          const double tpn = (scheme == PF_S1 || scheme == PF_S3) ? sc * tp : tp;
+          const double een = (scheme == PF_S2 || scheme == PF_S3) ? sc * sc * ee : ee;
+          ps = m.mu * een + 0.5 * m.K * tpn * tpn;
+        }
+        h = fmax(hp, ps);
+      }
+      Hhalf[4 * e + q] = h;
+    }
+  }
+}
+
+__global__ void k_dof_mask(int nx, int ny, const uint8_t *__restrict__ flags,
+                           const uint8_t *__restrict__ active, uint8_t *__restrict__ mask) {
+  const size_t nn = (size_t)(nx + 1) * (ny + 1);
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
+       n += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(n % (nx + 1)), j = (int)(n / (nx + 1));
+    bool touched = true;
+    if (active) {
+      touched = false;
+      for (int dj = -1; dj <= 0; ++dj)
+        for (int di = -1; di <= 0; ++di) {
+          const int ei = i + di, ej = j + dj;
+          if (ei >= 0 && ei < nx && ej >= 0 && ej < ny && active[(size_t)ej * nx + ei])
+            touched = true;
+        }
+    }
+    const uint8_t f = flags[n];
+    uint8_t m = 0;
+    if (!touched) {
+      m = 15;
+    } else {
+      if (f & (PF_FIX_X | PF_LOAD_X)) m |= 1;
+      if (f & (PF_FIX_Y | PF_LOAD_Y)) m |= 2;
+      if (f & (PF_D_FIX1 | PF_D_FIX0)) m |= 4;
+    }
+    mask[n] = m;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Host launch wrappers.
+// ------------------------------------------------------------------------------------
+static inline dim3 tile_grid(const GridD &g) { return dim3(tile_blocks_x(g.nx), tile_blocks_y(g.ny)); }
+static inline unsigned elem_blocks(size_t n) {
+  size_t b = (n + VEC_THREADS - 1) / VEC_THREADS;
+  return (unsigned)(b < 1 ? 1 : (b > 65535u * 8u ? 65535u * 8u : b));
+}
+
+template <class T>
+void elas_apply(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, const T *x,
+                T *y, cudaStream_t st, KrylovScal *sc, const RedWs *ws, int epi) {
+  RedWs w = ws ? *ws : RedWs{nullptr, nullptr, 0};
+  k_elas<T, EL_APPLY><<<tile_grid(g), TILE_THREADS, 0, st>>>(g, m, d, tens, x, y, nullptr, sc,
+                                                             w, ws ? epi : EPI_NONE);
+}
+template <class T>
+void elas_diag(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, T *diag,
+               cudaStream_t st) {
+  k_elas<T, EL_DIAG><<<tile_grid(g), TILE_THREADS, 0, st>>>(g, m, d, tens, nullptr, diag,
+                                                            nullptr, nullptr, RedWs{}, EPI_NONE);
+}
+void elas_residual(const GridD &g, const MatD &m, const double *u, const double *d, double *F,
+                   uint8_t *tens, cudaStream_t st) {
+  k_elas<double, EL_RESID><<<tile_grid(g), TILE_THREADS, 0, st>>>(g, m, d, nullptr, u, F, tens,
+                                                                  nullptr, RedWs{}, EPI_NONE);
+}
+template <class T>
+void damage_apply(const GridD &g, const T *c, double kappa, const T *x, T *y, cudaStream_t st,
+                  KrylovScal *sc, const RedWs *ws, int epi) {
+  RedWs w = ws ? *ws : RedWs{nullptr, nullptr, 0};
+  k_damage<T, T, DM_APPLY><<<tile_grid(g), TILE_THREADS, 0, st>>>(g, c, kappa, x, y, sc, w,
+                                                                   ws ? epi : EPI_NONE);
+}
+template <class T>
+void damage_diag(const GridD &g, const T *c, double kappa, T *diag, cudaStream_t st) {
+  k_damage<T, T, DM_DIAG><<<tile_grid(g), TILE_THREADS, 0, st>>>(g, c, kappa, nullptr, diag,
+                                                                 nullptr, RedWs{}, EPI_NONE);
+}
+void damage_rhs(const GridD &g, const double *H, double *b, cudaStream_t st) {
+  k_damage<double, double, DM_RHS><<<tile_grid(g), TILE_THREADS, 0, st>>>(
+      g, H, 0.0, nullptr, b, nullptr, RedWs{}, EPI_NONE);
+}
+void qp_energy(const GridD &g, const MatD &m, const double *u, const double *Hprev,
+               double *psi, double *Hout, cudaStream_t st) {
+  k_qp_energy<<<elem_blocks((size_t)g.nx * g.ny), VEC_THREADS, 0, st>>>(g, m, u, Hprev, psi, Hout);
+}
+void fs_coeff(const GridD &g, const MatD &m, int scheme, double psi_crit, const double *u,
+              const double *d, const double *Hprev, double *c_aug, uint8_t *active,
+              cudaStream_t st) {
+  k_fs_coeff<<<elem_blocks((size_t)g.nx * g.ny), VEC_THREADS, 0, st>>>(g, m, scheme, psi_crit, u,
+                                                                       d, Hprev, c_aug, active);
+}
+void fs_predict(const GridD &g, const MatD &m, int scheme, const double *u, const double *d,
+                const double *dd, const double *Hprev, const uint8_t *active, double *Hhalf,
+                cudaStream_t st) {
+  k_fs_predict<<<elem_blocks((size_t)g.nx * g.ny), VEC_THREADS, 0, st>>>(g, m, scheme, u, d, dd,
+                                                                         Hprev, active, Hhalf);
+}
+void dof_mask(int nx, int ny, const uint8_t *flags, const uint8_t *active, uint8_t *mask,
+              cudaStream_t st) {
+  k_dof_mask<<<elem_blocks((size_t)(nx + 1) * (ny + 1)), VEC_THREADS, 0, st>>>(nx, ny, flags,
+                                                                              active, mask);
+}
+
+template void elas_apply<double>(const GridD &, const MatD &, const double *, const uint8_t *,
+                                 const double *, double *, cudaStream_t, KrylovScal *,
+                                 const RedWs *, int);
+template void elas_apply<float>(const GridD &, const MatD &, const float *, const uint8_t *,
+                                const float *, float *, cudaStream_t, KrylovScal *,
+                                const RedWs *, int);
+template void elas_diag<double>(const GridD &, const MatD &, const double *, const uint8_t *,
+                                double *, cudaStream_t);
+template void elas_diag<float>(const GridD &, const MatD &, const float *, const uint8_t *,
+                               float *, cudaStream_t);
+template void damage_apply<double>(const GridD &, const double *, double, const double *,
+                                   double *, cudaStream_t, KrylovScal *, const RedWs *, int);
+template void damage_apply<float>(const GridD &, const float *, double, const float *, float *,
+                                  cudaStream_t, KrylovScal *, const RedWs *, int);
+template void damage_diag<double>(const GridD &, const double *, double, double *, cudaStream_t);
+template void damage_diag<float>(const GridD &, const float *, double, float *, cudaStream_t);
+
+}  // namespace pf

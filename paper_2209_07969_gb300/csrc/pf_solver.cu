@@ -1,0 +1,717 @@
+// Simulation context and the staggered drivers of libpf (C ABI in include/pf.h).
+//
+// Per load step (Sec. 3.1, Fig. 1, d-u order; fixed-stress d-step of Sec. 3.3-3.5):
+//   lift Dirichlet values -> u-solve with d_{n-1} -> repeat {d-step; u-solve; residual}
+//   -> commit H_n = max(H_{n-1}, Psi+(u_n)) and the reaction force.
+// u-solve: semismooth Newton with the frozen tension indicator of every iterate; each
+// Newton system is solved by Jacobi-preconditioned CG, in FP64 or as FP32 CG inside an
+// FP64 iterative-refinement loop.  Every step runs on the context's stream; the host
+// reads one scalar per Newton iterate, per staggered pass and every `check_every`
+// Krylov iterations.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "pf_internal.cuh"
+#include "pf_vec.cuh"
+
+using namespace pf;
+
+struct pf_ctx {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  GridD g{};
+  MatD m{};
+  size_t nn = 0, ne = 0, nq = 0;
+  int precision = PF_FP64, reaction_dir = 1, precond = PF_PRECOND_JACOBI, plane = 0;
+  pf_options opt{};
+  double ubar = 0.0;
+  int64_t step = 0;
+  int64_t launches = 0;
+  char err[512] = {0};
+
+  // committed state and per-step work arrays (FP64)
+  double *u = nullptr, *d = nullptr, *H = nullptr;   // 2N, N, Q
+  double *d_prev = nullptr;                            // N
+  double *F = nullptr;                                 // 2N
+  double *Hk = nullptr, *cq = nullptr, *Hhalf = nullptr;  // Q
+  uint8_t *act = nullptr;                              // Q
+  double *bd = nullptr, *Kd = nullptr, *dd = nullptr;  // N
+  uint8_t *flags = nullptr, *active = nullptr, *dofm = nullptr, *tens = nullptr;
+  // Krylov workspace (FP64): 2N each (used for u and d)
+  double *kb = nullptr, *kx = nullptr, *kr = nullptr, *kz = nullptr, *kp = nullptr,
+         *kq = nullptr, *kinv = nullptr, *kres = nullptr;
+  // FP32 copies for the inner solves
+  float *fb = nullptr, *fx = nullptr, *fr = nullptr, *fz = nullptr, *fp = nullptr,
+        *fq = nullptr, *finv = nullptr, *fd = nullptr, *fc = nullptr;
+  KrylovScal *sc = nullptr;
+  RedWs ws{};
+  double *dscal = nullptr;   // device scalars for norms / residual / reaction
+  double *hbuf = nullptr;    // pinned host mirror
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+pf_status set_err(pf_ctx *c, pf_status s, const char *fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return s;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return set_err(ctx, PF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CKS(call)                                   \
+  do {                                              \
+    pf_status s_ = (call);                          \
+    if (s_ != PF_OK && s_ != PF_ENOTCONV) return s_; \
+  } while (0)
+
+pf_status check_launch(pf_ctx *ctx) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+  return PF_OK;
+}
+
+// Read n doubles of device scalars into the pinned mirror (synchronises the stream).
+pf_status read_scalars(pf_ctx *ctx, const void *dev, int nbytes) {
+  CK(cudaMemcpyAsync(ctx->hbuf, dev, nbytes, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return PF_OK;
+}
+
+GridD grid_nomask(const pf_ctx *ctx) {
+  GridD g = ctx->g;
+  g.dofm = nullptr;
+  return g;
+}
+
+// ---- Krylov ----------------------------------------------------------------------------
+struct Work {
+  void *b, *x, *r, *z, *p, *q, *inv;
+};
+
+// Jacobi-preconditioned CG on a masked SPD operator.  `apply(p, q, epi)` computes q = A p
+// and runs the fused dot epilogue.  Returns iterations; *ok = converged.
+template <class T, class Apply>
+pf_status pcg(pf_ctx *ctx, Apply apply, size_t n, T *b, T *x, T *r, T *z, T *p, T *q,
+              const T *inv, double rtol, int maxit, int *iters, bool *ok) {
+  cudaStream_t st = ctx->st;
+  cg_init<T>(n, b, x, r, z, p, inv, ctx->sc, ctx->ws, st);
+  ctx->launches++;
+  CKS(check_launch(ctx));
+  CKS(read_scalars(ctx, &ctx->sc->rr, sizeof(double)));
+  const double rr0 = ctx->hbuf[0];
+  *iters = 0;
+  *ok = true;
+  if (!(rr0 > 0.0)) return PF_OK;
+  const double target = rtol * rtol * rr0;
+  const int every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 8;
+  int it = 0;
+  *ok = false;
+  while (it < maxit) {
+    apply(p, q, EPI_CG_ALPHA);
+    cg_update<T>(n, x, r, z, p, q, inv, ctx->sc, ctx->ws, st);
+    cg_dir<T>(n, z, p, ctx->sc, st);
+    ctx->launches += 3;
+    ++it;
+    if (it % every == 0 || it == maxit) {
+      CKS(check_launch(ctx));
+      CK(cudaMemcpyAsync(ctx->hbuf, &ctx->sc->rr, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(ctx->hbuf + 1, &ctx->sc->breakdown, sizeof(int), cudaMemcpyDeviceToHost,
+                         st));
+      CK(cudaStreamSynchronize(st));
+      const double rr = ctx->hbuf[0];
+      int bd;
+      memcpy(&bd, ctx->hbuf + 1, sizeof(int));
+      if (rr <= target) {
+        *ok = true;
+        break;
+      }
+      if (bd || !isfinite(rr)) break;
+    }
+  }
+  *iters = it;
+  return PF_OK;
+}
+
+// Linear solve A x = b (FP64 b, x; constrained entries of b are zero).  FP64 mode:
+// CG to tol_lin.  FP32_IR: x = 0; repeat {r = b - A x (FP64); stop if ||r|| <=
+// tol_lin ||b||; solve A_32 e = r_32 to tol_inner; x += e}.
+template <class ApplyD, class ApplyF>
+pf_status lin_solve(pf_ctx *ctx, ApplyD applyd, ApplyF applyf, size_t n, int ncomp,
+                    const double *b, double *x, const double *inv64, const float *inv32,
+                    int *iters, int *refines, bool *ok) {
+  cudaStream_t st = ctx->st;
+  if (ctx->precision == PF_FP64) {
+    CK(cudaMemcpyAsync(ctx->kb, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    int it = 0;
+    CKS(pcg<double>(ctx, applyd, n, ctx->kb, x, ctx->kr, ctx->kz, ctx->kp, ctx->kq, inv64,
+                    ctx->opt.tol_lin, ctx->opt.max_lin, &it, ok));
+    *iters += it;
+    return PF_OK;
+  }
+  // FP32 inner solves with FP64 refinement
+  CK(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+  CK(cudaMemcpyAsync(ctx->kres, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  norms(n, ncomp, ctx->g.dofm, b, ctx->dscal, ctx->ws, st);
+  ctx->launches++;
+  CKS(read_scalars(ctx, ctx->dscal, sizeof(double)));
+  const double bn = sqrt(ctx->hbuf[0]);
+  *ok = true;
+  if (!(bn > 0.0)) return PF_OK;
+  *ok = false;
+  for (int k = 0; k < ctx->opt.max_refine; ++k) {
+    convert<double, float>(n, ctx->kres, ctx->fb, st);
+    ctx->launches++;
+    int it = 0;
+    bool iok = false;
+    CKS(pcg<float>(ctx, applyf, n, ctx->fb, ctx->fx, ctx->fr, ctx->fz, ctx->fp, ctx->fq, inv32,
+                   ctx->opt.tol_inner, ctx->opt.max_lin, &it, &iok));
+    *iters += it;
+    convert<float, double>(n, ctx->fx, ctx->kq, st);
+    add(n, ctx->kq, x, st);
+    ctx->launches += 2;
+    (*refines)++;
+    // true residual in FP64
+    applyd(x, ctx->kq, EPI_NONE);
+    masked_comb(n, ncomp, ctx->g.dofm, 1.0, b, 1.0, ctx->kq, ctx->kres, st);
+    norms(n, ncomp, ctx->g.dofm, ctx->kres, ctx->dscal, ctx->ws, st);
+    ctx->launches += 2;
+    CKS(check_launch(ctx));
+    CKS(read_scalars(ctx, ctx->dscal, sizeof(double)));
+    const double rn = sqrt(ctx->hbuf[0]);
+    if (rn <= ctx->opt.tol_lin * bn) {
+      *ok = true;
+      break;
+    }
+    if (!isfinite(rn) || it == 0) break;
+  }
+  return PF_OK;
+}
+
+// ---- u-solve ---------------------------------------------------------------------------
+pf_status solve_u(pf_ctx *ctx, int *newton, int *lin, int *refines, bool *ok) {
+  cudaStream_t st = ctx->st;
+  const size_t n = 2 * ctx->nn;
+  double r0 = -1.0;
+  *ok = false;
+  if (ctx->precision == PF_FP32_IR) {
+    convert<double, float>(ctx->nn, ctx->d, ctx->fd, st);
+    ctx->launches++;
+  }
+  for (int it = 0; it <= ctx->opt.max_newton; ++it) {
+    elas_residual(ctx->g, ctx->m, ctx->u, ctx->d, ctx->F, ctx->tens, st);
+    norms(n, 2, ctx->g.dofm, ctx->F, ctx->dscal, ctx->ws, st);
+    ctx->launches += 2;
+    CKS(check_launch(ctx));
+    CKS(read_scalars(ctx, ctx->dscal, 2 * sizeof(double)));
+    const double rn = sqrt(ctx->hbuf[0]), fref = sqrt(ctx->hbuf[1]);
+    if (r0 < 0.0) r0 = rn;
+    if (rn == 0.0 || rn <= ctx->opt.tol_nr * fmax(r0, fref)) {
+      *ok = true;
+      return PF_OK;
+    }
+    if (!isfinite(rn)) return set_err(ctx, PF_ENOTCONV, "u residual is not finite");
+    if (it == ctx->opt.max_newton) break;
+    // rhs = -F on free DOFs
+    masked_comb(n, 2, ctx->g.dofm, -1.0, ctx->F, 0.0, nullptr, ctx->kb, st);
+    ctx->launches++;
+    bool lok = false;
+    if (ctx->precision == PF_FP64) {
+      elas_diag<double>(ctx->g, ctx->m, ctx->d, ctx->tens, ctx->kz, st);
+      invert<double>(n, ctx->kz, ctx->kinv, st);
+      ctx->launches += 2;
+      auto ad = [&](const double *xx, double *yy, int epi) {
+        elas_apply<double>(ctx->g, ctx->m, ctx->d, ctx->tens, xx, yy, st, ctx->sc, &ctx->ws, epi);
+        ctx->launches++;
+      };
+      int it2 = 0;
+      CKS(pcg<double>(ctx, ad, n, ctx->kb, ctx->kx, ctx->kr, ctx->kz, ctx->kp, ctx->kq, ctx->kinv,
+                      ctx->opt.tol_lin, ctx->opt.max_lin, &it2, &lok));
+      *lin += it2;
+    } else {
+      elas_diag<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, ctx->fz, st);
+      invert<float>(n, ctx->fz, ctx->finv, st);
+      ctx->launches += 2;
+      auto ad = [&](const double *xx, double *yy, int epi) {
+        elas_apply<double>(ctx->g, ctx->m, ctx->d, ctx->tens, xx, yy, st, ctx->sc, &ctx->ws, epi);
+        ctx->launches++;
+      };
+      auto af = [&](const float *xx, float *yy, int epi) {
+        elas_apply<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, xx, yy, st, ctx->sc, &ctx->ws, epi);
+        ctx->launches++;
+      };
+      CKS(lin_solve(ctx, ad, af, n, 2, ctx->kb, ctx->kx, nullptr, ctx->finv, lin, refines, &lok));
+    }
+    add(n, ctx->kx, ctx->u, st);
+    ctx->launches++;
+    (*newton)++;
+    if (!lok) return set_err(ctx, PF_ENOTCONV, "u linear solve did not converge");
+  }
+  return set_err(ctx, PF_ENOTCONV, "Newton for u hit max_newton");
+}
+
+// ---- d-solves ----------------------------------------------------------------------------
+// Solve K_dd(c) x = rhs on free DOFs for the correction form: the caller passes the
+// residual-form right-hand side (constrained entries zero).  c: FP64 per Gauss point.
+pf_status solve_damage(pf_ctx *ctx, const double *c, const double *rhs, double *x, int *lin,
+                       int *refines, bool *ok) {
+  cudaStream_t st = ctx->st;
+  const size_t n = ctx->nn;
+  const double kappa = ctx->m.Gc * ctx->m.l;
+  if (ctx->precision == PF_FP64) {
+    damage_diag<double>(ctx->g, c, kappa, ctx->kz, st);
+    invert<double>(n, ctx->kz, ctx->kinv, st);
+    ctx->launches += 2;
+    auto ad = [&](const double *xx, double *yy, int epi) {
+      damage_apply<double>(ctx->g, c, kappa, xx, yy, st, ctx->sc, &ctx->ws, epi);
+      ctx->launches++;
+    };
+    CK(cudaMemcpyAsync(ctx->kb, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    int it = 0;
+    CKS(pcg<double>(ctx, ad, n, ctx->kb, x, ctx->kr, ctx->kz, ctx->kp, ctx->kq, ctx->kinv,
+                    ctx->opt.tol_lin, ctx->opt.max_lin, &it, ok));
+    *lin += it;
+    return PF_OK;
+  }
+  convert<double, float>(ctx->nq, c, ctx->fc, st);
+  damage_diag<float>(ctx->g, ctx->fc, kappa, ctx->fz, st);
+  invert<float>(n, ctx->fz, ctx->finv, st);
+  ctx->launches += 3;
+  auto ad = [&](const double *xx, double *yy, int epi) {
+    damage_apply<double>(ctx->g, c, kappa, xx, yy, st, ctx->sc, &ctx->ws, epi);
+    ctx->launches++;
+  };
+  auto af = [&](const float *xx, float *yy, int epi) {
+    damage_apply<float>(ctx->g, ctx->fc, kappa, xx, yy, st, ctx->sc, &ctx->ws, epi);
+    ctx->launches++;
+  };
+  return lin_solve(ctx, ad, af, n, 1, rhs, x, nullptr, ctx->finv, lin, refines, ok);
+}
+
+// rhs = free ? b(H) - K(c) d : 0 ; then d += K_ff^-1 rhs.
+pf_status d_solve_from(pf_ctx *ctx, const double *c, const double *Hdrive, int *lin,
+                       int *refines, bool *ok) {
+  cudaStream_t st = ctx->st;
+  const size_t n = ctx->nn;
+  const double kappa = ctx->m.Gc * ctx->m.l;
+  damage_rhs(ctx->g, Hdrive, ctx->bd, st);
+  damage_apply<double>(grid_nomask(ctx), c, kappa, ctx->d, ctx->Kd, st);
+  masked_comb(n, 1, ctx->g.dofm, 1.0, ctx->bd, 1.0, ctx->Kd, ctx->bd, st);
+  ctx->launches += 3;
+  CKS(solve_damage(ctx, c, ctx->bd, ctx->dd, lin, refines, ok));
+  add(n, ctx->dd, ctx->d, st);
+  ctx->launches++;
+  return PF_OK;
+}
+
+pf_status d_step(pf_ctx *ctx, int scheme, int *lin, int *refines, int *dsolves, bool *ok) {
+  cudaStream_t st = ctx->st;
+  const double gcl = ctx->m.Gc / ctx->m.l;
+  const double kappa = ctx->m.Gc * ctx->m.l;
+  const size_t n = ctx->nn;
+  qp_energy(ctx->g, ctx->m, ctx->u, ctx->H, nullptr, ctx->Hk, st);
+  ctx->launches++;
+  if (scheme == PF_ST) {
+    coef<double>(ctx->nq, gcl, ctx->Hk, ctx->cq, st);
+    ctx->launches++;
+    CKS(d_solve_from(ctx, ctx->cq, ctx->Hk, lin, refines, ok));
+    (*dsolves)++;
+    return PF_OK;
+  }
+  // S1/S2/S3: augmented first NR iteration for Delta d (Sec. 3.4) ...
+  const double pc = ctx->opt.psi_crit < 0.0 ? ctx->m.Gc / (2.0 * ctx->m.l) : ctx->opt.psi_crit;
+  fs_coeff(ctx->g, ctx->m, scheme, pc, ctx->u, ctx->d, ctx->H, ctx->Hhalf, ctx->act, st);
+  coef<double>(ctx->nq, gcl, ctx->Hk, ctx->cq, st);
+  damage_rhs(ctx->g, ctx->Hk, ctx->bd, st);
+  damage_apply<double>(grid_nomask(ctx), ctx->cq, kappa, ctx->d, ctx->Kd, st);
+  masked_comb(n, 1, ctx->g.dofm, 1.0, ctx->bd, 1.0, ctx->Kd, ctx->bd, st);  // -R_d
+  ctx->launches += 5;
+  bool ok1 = false;
+  CKS(solve_damage(ctx, ctx->Hhalf, ctx->bd, ctx->dd, lin, refines, &ok1));
+  (*dsolves)++;
+  // ... predicted history (Sec. 3.3, Delta d > 0 rule of Sec. 3.5) ...
+  fs_predict(ctx->g, ctx->m, scheme, ctx->u, ctx->d, ctx->dd, ctx->H, ctx->act, ctx->Hhalf, st);
+  // ... and the frozen, linear evolution equation.
+  coef<double>(ctx->nq, gcl, ctx->Hhalf, ctx->cq, st);
+  ctx->launches += 2;
+  CKS(d_solve_from(ctx, ctx->cq, ctx->Hhalf, lin, refines, ok));
+  (*dsolves)++;
+  *ok = *ok && ok1;
+  return PF_OK;
+}
+
+pf_status stag_residual(pf_ctx *ctx, double *out) {
+  cudaStream_t st = ctx->st;
+  const double gcl = ctx->m.Gc / ctx->m.l;
+  const double kappa = ctx->m.Gc * ctx->m.l;
+  qp_energy(ctx->g, ctx->m, ctx->u, ctx->H, nullptr, ctx->Hk, st);
+  coef<double>(ctx->nq, gcl, ctx->Hk, ctx->cq, st);
+  damage_rhs(ctx->g, ctx->Hk, ctx->bd, st);
+  damage_apply<double>(grid_nomask(ctx), ctx->cq, kappa, ctx->d, ctx->Kd, st);
+  damage_diag<double>(grid_nomask(ctx), ctx->cq, kappa, ctx->kz, st);
+  stag_max(ctx->nn, ctx->g.dofm, ctx->Kd, ctx->bd, ctx->kz, ctx->dscal, ctx->ws, st);
+  ctx->launches += 6;
+  CKS(check_launch(ctx));
+  CKS(read_scalars(ctx, ctx->dscal, sizeof(double)));
+  *out = ctx->hbuf[0];
+  return PF_OK;
+}
+
+template <class T>
+pf_status dalloc(pf_ctx *ctx, T **p, size_t n) {
+  cudaError_t e = cudaMalloc((void **)p, (n ? n : 1) * sizeof(T));
+  if (e != cudaSuccess)
+    return set_err(ctx, PF_ENOMEM, "cudaMalloc of %zu bytes: %s", n * sizeof(T),
+                   cudaGetErrorString(e));
+  return PF_OK;
+}
+
+void free_all(pf_ctx *c) {
+  void *ptrs[] = {c->u,  c->d,  c->H,  c->d_prev, c->F,  c->Hk, c->cq, c->Hhalf, c->act,
+                  c->bd, c->Kd, c->dd, c->flags,  c->active, c->dofm, c->tens, c->kb, c->kx,
+                  c->kr, c->kz, c->kp, c->kq, c->kinv, c->kres, c->fb, c->fx, c->fr, c->fz,
+                  c->fp, c->fq, c->finv, c->fd, c->fc, c->sc, c->ws.partials, c->ws.counter,
+                  c->dscal};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (c->hbuf) cudaFreeHost(c->hbuf);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+void pf_default_options(pf_options *o) {
+  if (!o) return;
+  o->tol_nr = 1e-7;
+  o->tol_lin = 1e-10;
+  o->tol_inner = 1e-4;
+  o->max_newton = 50;
+  o->max_stag = 1000;
+  o->max_lin = 200000;
+  o->max_refine = 30;
+  o->psi_crit = -1.0;
+  o->project = 0;
+  o->check_every = 8;
+}
+
+const char *pf_status_string(pf_status s) {
+  switch (s) {
+    case PF_OK: return "PF_OK";
+    case PF_EINVAL: return "PF_EINVAL";
+    case PF_ENOMEM: return "PF_ENOMEM";
+    case PF_ENOTCONV: return "PF_ENOTCONV";
+    case PF_ECUDA: return "PF_ECUDA";
+    case PF_ETIMEOUT: return "PF_ETIMEOUT";
+    case PF_EBUSY: return "PF_EBUSY";
+  }
+  return "unknown";
+}
+
+pf_status pf_material_make(double E, double nu, double Gc, double l, double k_res, int plane,
+                           pf_material *out) {
+  if (!out || !(E > 0) || !(nu > -1.0 && nu < 0.5) || !(Gc > 0) || !(l > 0) || !(k_res >= 0) ||
+      (plane != PF_PLANE_STRAIN && plane != PF_PLANE_STRESS))
+    return PF_EINVAL;
+  const double mu = E / (2.0 * (1.0 + nu));
+  const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  out->mu = mu;
+  if (plane == PF_PLANE_STRAIN) {
+    out->K = lam + 2.0 * mu / 3.0;
+    out->cdim = 1.0 / 3.0;
+  } else {
+    out->K = E / (2.0 * (1.0 - nu));
+    out->cdim = 0.5;
+  }
+  out->eta = k_res;
+  out->Gc = Gc;
+  out->l = l;
+  return PF_OK;
+}
+
+pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double l, double k_res,
+                    pf_ctx **out) {
+  if (!out) return PF_EINVAL;
+  *out = nullptr;
+  if (!mesh || !mesh->node_flags || mesh->nx < 1 || mesh->ny < 1 || !(mesh->Lx > 0) ||
+      !(mesh->Ly > 0) || (mesh->precision != PF_FP64 && mesh->precision != PF_FP32_IR) ||
+      (mesh->reaction_dir != 0 && mesh->reaction_dir != 1) ||
+      (mesh->precond != PF_PRECOND_JACOBI && mesh->precond != PF_PRECOND_GMG))
+    return PF_EINVAL;
+  if ((double)(mesh->nx + 1) * (double)(mesh->ny + 1) > 4.0e8) return PF_EINVAL;
+  pf_material mat;
+  if (pf_material_make(E, nu, Gc, l, k_res, mesh->plane, &mat) != PF_OK) return PF_EINVAL;
+  pf_ctx *ctx = new (std::nothrow) pf_ctx();
+  if (!ctx) return PF_ENOMEM;
+  pf_default_options(&ctx->opt);
+  cudaGetDevice(&ctx->device);
+  ctx->nn = (size_t)(mesh->nx + 1) * (mesh->ny + 1);
+  ctx->ne = (size_t)mesh->nx * mesh->ny;
+  ctx->nq = 4 * ctx->ne;
+  ctx->precision = mesh->precision;
+  ctx->reaction_dir = mesh->reaction_dir;
+  ctx->precond = mesh->precond;
+  ctx->plane = mesh->plane;
+  ctx->m = MatD{mat.mu, mat.K, mat.cdim, mat.eta, mat.Gc, mat.l};
+  pf_status s = PF_OK;
+  auto fail = [&](pf_status st) {
+    free_all(ctx);
+    delete ctx;
+    return st;
+  };
+  if (cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(PF_ECUDA);
+  ctx->own_stream = true;
+  const size_t nn = ctx->nn, ne = ctx->ne, nq = ctx->nq;
+#define AL(p, n)                                   \
+  do {                                             \
+    if ((s = dalloc(ctx, &ctx->p, (n))) != PF_OK) \
+      return fail(s);                              \
+  } while (0)
+  AL(u, 2 * nn); AL(d, nn); AL(H, nq); AL(d_prev, nn); AL(F, 2 * nn);
+  AL(Hk, nq); AL(cq, nq); AL(Hhalf, nq); AL(act, nq);
+  AL(bd, nn); AL(Kd, nn); AL(dd, nn);
+  AL(flags, nn); AL(dofm, nn); AL(tens, ne);
+  if (mesh->elem_active) AL(active, ne);
+  AL(kb, 2 * nn); AL(kx, 2 * nn); AL(kr, 2 * nn); AL(kz, 2 * nn); AL(kp, 2 * nn);
+  AL(kq, 2 * nn); AL(kinv, 2 * nn); AL(kres, 2 * nn);
+  if (ctx->precision == PF_FP32_IR) {
+    AL(fb, 2 * nn); AL(fx, 2 * nn); AL(fr, 2 * nn); AL(fz, 2 * nn); AL(fp, 2 * nn);
+    AL(fq, 2 * nn); AL(finv, 2 * nn); AL(fd, nn); AL(fc, nq);
+  }
+  AL(sc, 1); AL(dscal, 8);
+  {
+    const size_t tiles = (size_t)tile_blocks_x(mesh->nx) * tile_blocks_y(mesh->ny);
+    ctx->ws.max_blocks = (int)(tiles > 4096 ? tiles : 4096);
+  }
+  AL(ws.partials, 4 * ctx->ws.max_blocks);
+  AL(ws.counter, 1);
+#undef AL
+  if (cudaMallocHost((void **)&ctx->hbuf, 64) != cudaSuccess) return fail(PF_ENOMEM);
+  if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess)
+    return fail(PF_ECUDA);
+  cudaStream_t st = ctx->st;
+  bool okc = cudaMemsetAsync(ctx->ws.counter, 0, sizeof(unsigned), st) == cudaSuccess &&
+             cudaMemsetAsync(ctx->sc, 0, sizeof(KrylovScal), st) == cudaSuccess &&
+             cudaMemcpyAsync(ctx->flags, mesh->node_flags, nn, cudaMemcpyHostToDevice, st) ==
+                 cudaSuccess &&
+             (!mesh->elem_active ||
+              cudaMemcpyAsync(ctx->active, mesh->elem_active, ne, cudaMemcpyHostToDevice, st) ==
+                  cudaSuccess) &&
+             cudaMemsetAsync(ctx->u, 0, 2 * nn * sizeof(double), st) == cudaSuccess &&
+             cudaMemsetAsync(ctx->H, 0, nq * sizeof(double), st) == cudaSuccess &&
+             cudaMemsetAsync(ctx->tens, 0, ne, st) == cudaSuccess;
+  if (!okc) return fail(PF_ECUDA);
+  ctx->g = GridD{mesh->nx, mesh->ny, mesh->Lx / mesh->nx, mesh->Ly / mesh->ny, ctx->active,
+                 ctx->dofm};
+  dof_mask(mesh->nx, mesh->ny, ctx->flags, ctx->active, ctx->dofm, st);
+  // d = 1 on D_FIX1 nodes with an active element, else 0
+  {
+    std::vector<double> d0(nn, 0.0);
+    for (size_t i = 0; i < nn; ++i) d0[i] = (mesh->node_flags[i] & PF_D_FIX1) ? 1.0 : 0.0;
+    if (mesh->elem_active) {
+      const int nx = mesh->nx, ny = mesh->ny;
+      for (size_t i = 0; i < nn; ++i) {
+        if (d0[i] == 0.0) continue;
+        const int ii = (int)(i % (nx + 1)), jj = (int)(i / (nx + 1));
+        bool touched = false;
+        for (int dj = -1; dj <= 0; ++dj)
+          for (int di = -1; di <= 0; ++di) {
+            const int ei = ii + di, ej = jj + dj;
+            if (ei >= 0 && ei < nx && ej >= 0 && ej < ny && mesh->elem_active[(size_t)ej * nx + ei])
+              touched = true;
+          }
+        if (!touched) d0[i] = 0.0;
+      }
+    }
+    if (cudaMemcpy(ctx->d, d0.data(), nn * sizeof(double), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return fail(PF_ECUDA);
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return fail(PF_ECUDA);
+  ctx->launches = 1;
+  *out = ctx;
+  return PF_OK;
+}
+
+pf_status pf_set_options(pf_ctx *ctx, const pf_options *o) {
+  if (!ctx || !o) return PF_EINVAL;
+  if (!(o->tol_nr > 0) || !(o->tol_lin > 0) || !(o->tol_inner > 0) || o->max_newton < 1 ||
+      o->max_stag < 1 || o->max_lin < 1 || o->max_refine < 1 || o->check_every < 1)
+    return set_err(ctx, PF_EINVAL, "invalid options");
+  ctx->opt = *o;
+  return PF_OK;
+}
+
+pf_status pf_get_options(const pf_ctx *ctx, pf_options *o) {
+  if (!ctx || !o) return PF_EINVAL;
+  *o = ctx->opt;
+  return PF_OK;
+}
+
+pf_status pf_load_step(pf_ctx *ctx, double d_ubar, int scheme, double tol,
+                       pf_step_result *res) {
+  if (!ctx) return PF_EINVAL;
+  if (scheme < PF_ST || scheme > PF_S3 || !(tol > 0) || !isfinite(d_ubar))
+    return set_err(ctx, PF_EINVAL, "invalid scheme/tol/d_ubar");
+  CK(cudaSetDevice(ctx->device));
+  pf_step_result r;
+  memset(&r, 0, sizeof(r));
+  cudaStream_t st = ctx->st;
+  CK(cudaEventRecord(ctx->ev0, st));
+  ctx->ubar += d_ubar;
+  r.ubar = ctx->ubar;
+  lift(ctx->nn, ctx->flags, ctx->dofm, ctx->ubar, ctx->u, st);
+  ctx->launches++;
+  if (ctx->opt.project)
+    CK(cudaMemcpyAsync(ctx->d_prev, ctx->d, ctx->nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  bool ok = false, all_ok = true;
+  pf_status s = solve_u(ctx, &r.newton_u, &r.lin_u, &r.refine_steps, &ok);
+  if (s != PF_OK && s != PF_ENOTCONV) return s;
+  all_ok = all_ok && ok;
+  double resid = INFINITY;
+  for (int k = 0; k < ctx->opt.max_stag; ++k) {
+    bool dok = false;
+    s = d_step(ctx, scheme, &r.lin_d, &r.refine_steps, &r.d_solves, &dok);
+    if (s != PF_OK && s != PF_ENOTCONV) return s;
+    if (ctx->opt.project) {
+      project(ctx->nn, ctx->g.dofm, ctx->d_prev, ctx->d, st);
+      ctx->launches++;
+    }
+    s = solve_u(ctx, &r.newton_u, &r.lin_u, &r.refine_steps, &ok);
+    if (s != PF_OK && s != PF_ENOTCONV) return s;
+    all_ok = all_ok && ok && dok;
+    s = stag_residual(ctx, &resid);
+    if (s != PF_OK) return s;
+    r.stag_iters = k + 1;
+    if (resid <= tol) {
+      r.converged = 1;
+      break;
+    }
+    if (!isfinite(resid)) break;
+  }
+  r.stag_residual = resid;
+  // commit history and report the reaction force
+  qp_energy(ctx->g, ctx->m, ctx->u, ctx->H, nullptr, ctx->Hk, st);
+  ctx->launches++;
+  CK(cudaMemcpyAsync(ctx->H, ctx->Hk, ctx->nq * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  elas_residual(ctx->g, ctx->m, ctx->u, ctx->d, ctx->F, ctx->tens, st);
+  reaction(ctx->nn, ctx->flags, ctx->reaction_dir, ctx->F, ctx->dscal, ctx->ws, st);
+  ctx->launches += 2;
+  CK(cudaEventRecord(ctx->ev1, st));
+  CKS(check_launch(ctx));
+  CKS(read_scalars(ctx, ctx->dscal, sizeof(double)));
+  r.reaction = ctx->hbuf[0];
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+  r.ms = ms;
+  ctx->step++;
+  if (res) *res = r;
+  if (!r.converged || !all_ok)
+    return set_err(ctx, PF_ENOTCONV, "load step %lld: staggered residual %.3e after %d passes%s",
+                   (long long)ctx->step, resid, r.stag_iters,
+                   all_ok ? "" : " (an inner solve hit its cap)");
+  return PF_OK;
+}
+
+pf_status pf_get_fields(pf_ctx *ctx, double *u, double *d, double *H) {
+  if (!ctx) return PF_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->st;
+  if (u) CK(cudaMemcpyAsync(u, ctx->u, 2 * ctx->nn * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (d) CK(cudaMemcpyAsync(d, ctx->d, ctx->nn * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (H) CK(cudaMemcpyAsync(H, ctx->H, ctx->nq * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return PF_OK;
+}
+
+pf_status pf_set_fields(pf_ctx *ctx, const double *u, const double *d, const double *H,
+                        double ubar) {
+  if (!ctx || !isfinite(ubar)) return PF_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->st;
+  if (u) CK(cudaMemcpyAsync(ctx->u, u, 2 * ctx->nn * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (d) CK(cudaMemcpyAsync(ctx->d, d, ctx->nn * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (H) CK(cudaMemcpyAsync(ctx->H, H, ctx->nq * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->ubar = ubar;
+  return PF_OK;
+}
+
+static const uint64_t PF_STATE_MAGIC = 0x3130326670666670ull;  // "pffpf201"
+
+size_t pf_state_size(const pf_ctx *ctx) {
+  if (!ctx) return 0;
+  return 4 * sizeof(uint64_t) + 2 * sizeof(double) +
+         (3 * ctx->nn + ctx->nq) * sizeof(double);
+}
+
+pf_status pf_get_state(pf_ctx *ctx, void *buf, size_t size) {
+  if (!ctx || !buf || size < pf_state_size(ctx)) return PF_EINVAL;
+  uint64_t *hdr = (uint64_t *)buf;
+  hdr[0] = PF_STATE_MAGIC;
+  hdr[1] = ctx->nn;
+  hdr[2] = ctx->nq;
+  hdr[3] = (uint64_t)ctx->step;
+  double *p = (double *)(hdr + 4);
+  p[0] = ctx->ubar;
+  p[1] = 0.0;
+  return pf_get_fields(ctx, p + 2, p + 2 + 2 * ctx->nn, p + 2 + 3 * ctx->nn);
+}
+
+pf_status pf_set_state(pf_ctx *ctx, const void *buf, size_t size) {
+  if (!ctx || !buf || size < pf_state_size(ctx)) return PF_EINVAL;
+  const uint64_t *hdr = (const uint64_t *)buf;
+  if (hdr[0] != PF_STATE_MAGIC || hdr[1] != ctx->nn || hdr[2] != ctx->nq)
+    return set_err(ctx, PF_EINVAL, "state buffer does not match this mesh");
+  const double *p = (const double *)(hdr + 4);
+  pf_status s = pf_set_fields(ctx, p + 2, p + 2 + 2 * ctx->nn, p + 2 + 3 * ctx->nn, p[0]);
+  if (s == PF_OK) ctx->step = (int64_t)hdr[3];
+  return s;
+}
+
+pf_status pf_sizes(const pf_ctx *ctx, int64_t *n_nodes, int64_t *n_elems, int64_t *n_qp) {
+  if (!ctx) return PF_EINVAL;
+  if (n_nodes) *n_nodes = (int64_t)ctx->nn;
+  if (n_elems) *n_elems = (int64_t)ctx->ne;
+  if (n_qp) *n_qp = (int64_t)ctx->nq;
+  return PF_OK;
+}
+
+int64_t pf_launch_count(const pf_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+const char *pf_last_error(const pf_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+void pf_destroy(pf_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  free_all(ctx);
+  delete ctx;
+}
+
+}  // extern "C"

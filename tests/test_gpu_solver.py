@@ -1,0 +1,172 @@
+"""Load-step and load-path parity of pf_load_step against the FP64 checker.
+
+FP64 mode: reaction force within 1e-6 relative and the phase field within 1e-6 per
+step; FP32-CG with FP64 refinement: peak force within 1e-4 relative and RMS d
+difference within 1e-3 (the per-result tolerances of the mixed-precision form).  The
+checker runs the same specimen, increments, scheme and tolerances.
+"""
+import numpy as np
+import pytest
+
+from oracle import model, q1, staggered as stg
+from paper_2209_07969_gb300 import binding, specimens as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _checker(spec):
+    g = q1.Grid(spec.nx, spec.ny, spec.Lx, spec.Ly, spec.node_flags, spec.elem_active)
+    m = model.material_from_E_nu(spec.E, spec.nu, spec.Gc, spec.l, spec.eta, spec.plane)
+    return g, m
+
+
+def _run_both(spec, scheme, tol, precision=binding.FP64, steps=None, tol_lin=1e-12):
+    g, m = _checker(spec)
+    incs = spec.increments if steps is None else spec.increments[:steps]
+    st = stg.State(g)
+    opts = stg.Options(tol_st=tol)
+    sim = binding.Simulation(spec, precision=precision)
+    sim.set_options(tol_lin=tol_lin)
+    out = []
+    for du in incs:
+        r_ref = stg.load_step(g, m, st, du, scheme, opts, spec.reaction_dir)
+        r = sim.load_step(du, scheme, tol)
+        u, d, H = sim.fields()
+        out.append((r_ref, r, st.copy(), (u, d, H)))
+    sim.close()
+    return g, m, out
+
+
+def _d_rms(g, a, b):
+    diff = q1.interp_qp(g, a - b)
+    return np.sqrt(np.sum(diff ** 2 * g.elem_active[:, None]) * q1.qp_weight(g) / (g.Lx * g.Ly))
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("precision", [binding.FP64, binding.FP32_IR])
+def test_uniaxial_bar_closed_form(gpu, scheme, precision):
+    lam, mu, Gc, l, eta = 121.15, 80.77, 2.7e-3, 0.03, 1e-9
+    M = lam + 2 * mu
+    eps_c = np.sqrt(Gc / (3 * M * l))
+    spec = S.uniaxial_bar(9, 12, Lx=0.5, Ly=1.0, lam=lam, mu=mu, Gc=Gc, l=l, eta=eta,
+                          steps=8, u_max=2.5 * eps_c)
+    sim = binding.Simulation(spec, precision=precision)
+    sim.set_options(tol_lin=1e-12, max_stag=200)
+    H = 0.0
+    for du in spec.increments:
+        r = sim.load_step(du, scheme, 1e-9)
+        assert r["converged"] == 1
+        eps = r["ubar"] / spec.Ly
+        H = max(H, 0.5 * M * eps ** 2)
+        dex = 2 * H / (Gc / l + 2 * H)
+        F = ((1 - dex) ** 2 + eta) * M * eps * spec.Lx
+        _, d, Hq = sim.fields()
+        assert np.allclose(d, dex, rtol=1e-7, atol=1e-9)
+        assert r["reaction"] == pytest.approx(F, rel=1e-7)
+        assert np.allclose(Hq, H, rtol=1e-10)
+    sim.close()
+
+
+SMALL = dict(n=24, l=0.08, steps=6, u_max=8e-3)
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+def test_tensile_path_fp64_matches_checker(gpu, scheme):
+    spec = S.tensile(SMALL["n"], l=SMALL["l"], steps=SMALL["steps"], u_max=SMALL["u_max"])
+    g, m, out = _run_both(spec, scheme, tol=1e-8)
+    peak = max(abs(o[0].reaction) for o in out)
+    cracked = False
+    for r_ref, r, st_ref, (u, d, H) in out:
+        assert r["converged"] == 1 and r_ref.converged
+        assert abs(r["reaction"] - r_ref.reaction) <= 1e-6 * peak
+        assert np.max(np.abs(d - st_ref.d)) < 1e-6
+        assert np.max(np.abs(H - st_ref.H)) <= 1e-6 * max(1.0, np.max(st_ref.H))
+        assert abs(r["stag_iters"] - r_ref.stag_iters) <= 1
+        cracked |= r_ref.reaction < 0.7 * peak
+    assert cracked, "the small path must reach the crack"
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 3])
+def test_tensile_path_fp32_refined(gpu, scheme):
+    spec = S.tensile(SMALL["n"], l=SMALL["l"], steps=SMALL["steps"], u_max=SMALL["u_max"])
+    g, m, out = _run_both(spec, scheme, tol=1e-6, precision=binding.FP32_IR, tol_lin=1e-10)
+    Fr = np.array([o[0].reaction for o in out])
+    Fg = np.array([o[1]["reaction"] for o in out])
+    assert abs(Fg.max() - Fr.max()) <= 1e-4 * Fr.max()
+    for r_ref, r, st_ref, (u, d, H) in out:
+        assert r["converged"] == 1
+        assert _d_rms(g, d, st_ref.d) <= 1e-3
+        assert r["refine_steps"] >= 1
+
+
+def test_config0_prefix_fp64(gpu):
+    """The 64 x 64 tensile benchmark in FP64 through crack onset (first 13 steps)."""
+    spec = S.tensile(64)
+    g, m, out = _run_both(spec, 0, tol=1e-7, steps=13)
+    peak = max(abs(o[0].reaction) for o in out)
+    for r_ref, r, st_ref, (u, d, H) in out:
+        assert abs(r["reaction"] - r_ref.reaction) <= 1e-6 * peak
+        assert np.max(np.abs(d - st_ref.d)) < 1e-5
+
+
+def test_shear_and_masked_plane_stress(gpu):
+    sh = S.shear(16, l=0.1, steps=3, u_max=6e-3)
+    g, m, out = _run_both(sh, 1, tol=1e-8)
+    for r_ref, r, st_ref, (u, d, H) in out:
+        assert abs(r["reaction"] - r_ref.reaction) <= 1e-6 * max(abs(r_ref.reaction), 1e-12)
+        assert np.max(np.abs(d - st_ref.d)) < 1e-6
+    ls = S.l_shape(20, steps=3, u_max=0.3, l=50.0)
+    g, m, out = _run_both(ls, 1, tol=1e-8)
+    for r_ref, r, st_ref, (u, d, H) in out:
+        assert abs(r["reaction"] - r_ref.reaction) <= 1e-6 * max(abs(r_ref.reaction), 1e-12)
+        assert np.max(np.abs(d - st_ref.d)) < 1e-6
+        # masked-out nodes stay at zero
+        assert np.all(u.reshape(-1, 2)[g.orphan] == 0.0)
+
+
+def test_state_roundtrip_is_bitwise(gpu):
+    spec = S.tensile(16, l=0.1, steps=4, u_max=6e-3)
+    sim = binding.Simulation(spec)
+    for du in spec.increments[:2]:
+        sim.load_step(du, 1, 1e-7)
+    snap = sim.get_state()
+    a = sim.load_step(spec.increments[2], 1, 1e-7)
+    ua, da, Ha = sim.fields()
+    sim.set_state(snap)
+    b = sim.load_step(spec.increments[2], 1, 1e-7)
+    ub, db, Hb = sim.fields()
+    assert a["reaction"] == b["reaction"] and a["stag_iters"] == b["stag_iters"]
+    assert np.array_equal(ua, ub) and np.array_equal(da, db) and np.array_equal(Ha, Hb)
+    sim.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (2, 1), (3, 3)])
+def test_tiny_meshes(gpu, shape):
+    nx, ny = shape
+    spec = S.uniaxial_bar(nx, ny, steps=2, u_max=1e-3)
+    g, m, out = _run_both(spec, 0, tol=1e-9)
+    for r_ref, r, st_ref, (u, d, H) in out:
+        assert r["reaction"] == pytest.approx(r_ref.reaction, rel=1e-9)
+        assert np.allclose(d, st_ref.d, atol=1e-10)
+
+
+def test_invalid_arguments_are_rejected(gpu):
+    spec = S.tensile(8)
+    sim = binding.Simulation(spec)
+    with pytest.raises(binding.PfError) as e:
+        sim.load_step(1e-4, 7, 1e-6)
+    assert e.value.status == binding.PF_EINVAL
+    with pytest.raises(binding.PfError):
+        sim.set_options(max_stag=0)
+    with pytest.raises(binding.PfError):
+        sim.set_state(np.zeros(16, np.uint8))
+    sim.close()
+
+
+def test_stag_cap_reports_not_converged(gpu):
+    spec = S.tensile(16, l=0.1, steps=1, u_max=6e-3)
+    sim = binding.Simulation(spec)
+    sim.set_options(max_stag=1)
+    r = sim.load_step(6e-3, 0, 1e-14)
+    assert r["status"] == binding.PF_ENOTCONV and r["converged"] == 0 and r["stag_iters"] == 1
+    sim.close()
