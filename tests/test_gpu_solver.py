@@ -81,7 +81,9 @@ def test_tensile_path_fp64_matches_checker(gpu, scheme):
         assert abs(r["reaction"] - r_ref.reaction) <= 1e-6 * peak
         assert np.max(np.abs(d - st_ref.d)) < 1e-6
         assert np.max(np.abs(H - st_ref.H)) <= 1e-6 * max(1.0, np.max(st_ref.H))
-        assert abs(r["stag_iters"] - r_ref.stag_iters) <= 1
+        # the pass count of a slowly contracting iteration is not a unique result; the
+        # converged state is (checked above)
+        assert abs(r["stag_iters"] - r_ref.stag_iters) <= max(1, 0.1 * r_ref.stag_iters)
         cracked |= r_ref.reaction < 0.7 * peak
     assert cracked, "the small path must reach the crack"
 
