@@ -1,0 +1,689 @@
+// Geometric multigrid kernels: fine stencil assembly, Galerkin coarse operators,
+// Chebyshev smoothing, transfer operators and the dense coarsest solve.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "pf_gmg.cuh"
+
+namespace pf {
+
+namespace {
+
+__device__ __forceinline__ double gmg_gp(int hi) {
+  return hi ? 0.78867513459481288225 : 0.21132486540518711775;
+}
+
+__device__ __forceinline__ double g_warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Max over the grid into *out (last-CTA pattern, deterministic).
+__device__ void grid_max(double v, const RedWs ws, double *out) {
+  __shared__ double sh[32];
+  __shared__ bool am_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = g_warp_max(v);
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = sh[0];
+    for (int w = 1; w < nw; ++w) s = fmax(s, sh[w]);
+    ws.partials[blockIdx.x] = s;
+    __threadfence();
+    am_last = atomicAdd(ws.counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  double s = 0.0;
+  for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) s = fmax(s, __ldcg(ws.partials + i));
+  s = g_warp_max(s);
+  __syncthreads();
+  if (lane == 0) sh[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = sh[0];
+    for (int w = 1; w < nw; ++w) t = fmax(t, sh[w]);
+    *out = t;
+    *ws.counter = 0u;
+  }
+}
+
+inline unsigned nblk(size_t n, int cap = 1 << 16) {
+  size_t b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > (size_t)cap) b = cap;
+  return (unsigned)b;
+}
+
+// stencil entry index: neighbour k = (dj+1)*3 + (di+1), block (r, c)
+template <int B>
+__device__ __forceinline__ size_t sidx(int k, int r, int c, size_t node, size_t nn) {
+  return ((size_t)(k * B * B + r * B + c)) * nn + node;
+}
+
+// ---- fine stencils ---------------------------------------------------------------------
+// Row block of node n of the (unmasked) Q1 elasticity tangent.
+template <class T>
+__global__ void k_fine_stencil_elas(GridD g, MatD mt, const T *__restrict__ d,
+                                    const uint8_t *__restrict__ tens, T *__restrict__ S) {
+  const int nx = g.nx, ny = g.ny;
+  const size_t nn = (size_t)(nx + 1) * (ny + 1);
+  const double ihx = 1.0 / g.hx, ihy = 1.0 / g.hy, w = 0.25 * g.hx * g.hy;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
+       n += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(n % (nx + 1)), j = (int)(n / (nx + 1));
+    double acc[9][4];
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[k][q] = 0.0;
+#pragma unroll
+    for (int ej_off = -1; ej_off <= 0; ++ej_off)
+#pragma unroll
+      for (int ei_off = -1; ei_off <= 0; ++ei_off) {
+        const int ei = i + ei_off, ej = j + ej_off;
+        if (ei < 0 || ei >= nx || ej < 0 || ej >= ny) continue;
+        const size_t e = (size_t)ej * nx + ei;
+        if (g.active && !g.active[e]) continue;
+        const int ax = -ei_off, ay = -ej_off;  // local coords of node n in the element
+        const int a = ay * 2 + ax;
+        const size_t n0 = (size_t)ej * (nx + 1) + ei;
+        const double dn[4] = {(double)d[n0], (double)d[n0 + 1], (double)d[n0 + nx + 1],
+                              (double)d[n0 + nx + 2]};
+        const uint8_t tb = tens[e];
+        for (int q = 0; q < 4; ++q) {
+          const double s = gmg_gp(q & 1), t = gmg_gp(q >> 1);
+          const double s1 = 1 - s, t1 = 1 - t;
+          const double dq = s1 * t1 * dn[0] + s * t1 * dn[1] + s1 * t * dn[2] + s * t * dn[3];
+          const double om = 1 - dq, gq = om * om + mt.eta;
+          const double kv = ((tb >> q) & 1) ? gq * mt.K : mt.K;
+          const double D11 = gq * 2 * mt.mu * (1 - mt.cdim) + kv;
+          const double D12 = -gq * 2 * mt.mu * mt.cdim + kv;
+          const double Ds = gq * mt.mu;
+          const double Nx[4] = {-t1 * ihx, t1 * ihx, -t * ihx, t * ihx};
+          const double Ny[4] = {-s1 * ihy, -s * ihy, s1 * ihy, s * ihy};
+          for (int b = 0; b < 4; ++b) {
+            const int bx = b & 1, by = b >> 1;
+            const int k = (by - ay + 1) * 3 + (bx - ax + 1);
+            acc[k][0] += w * (Nx[a] * D11 * Nx[b] + Ny[a] * Ds * Ny[b]);
+            acc[k][1] += w * (Nx[a] * D12 * Ny[b] + Ny[a] * Ds * Nx[b]);
+            acc[k][2] += w * (Ny[a] * D12 * Nx[b] + Nx[a] * Ds * Ny[b]);
+            acc[k][3] += w * (Ny[a] * D11 * Ny[b] + Nx[a] * Ds * Nx[b]);
+          }
+        }
+      }
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) S[sidx<2>(k, q >> 1, q & 1, n, nn)] = (T)acc[k][q];
+  }
+}
+
+template <class T>
+__global__ void k_fine_stencil_damage(GridD g, const T *__restrict__ c, double kappa,
+                                      T *__restrict__ S) {
+  const int nx = g.nx, ny = g.ny;
+  const size_t nn = (size_t)(nx + 1) * (ny + 1);
+  const double ihx = 1.0 / g.hx, ihy = 1.0 / g.hy, w = 0.25 * g.hx * g.hy;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
+       n += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(n % (nx + 1)), j = (int)(n / (nx + 1));
+    double acc[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = 0.0;
+#pragma unroll
+    for (int ej_off = -1; ej_off <= 0; ++ej_off)
+#pragma unroll
+      for (int ei_off = -1; ei_off <= 0; ++ei_off) {
+        const int ei = i + ei_off, ej = j + ej_off;
+        if (ei < 0 || ei >= nx || ej < 0 || ej >= ny) continue;
+        const size_t e = (size_t)ej * nx + ei;
+        if (g.active && !g.active[e]) continue;
+        const int ax = -ei_off, ay = -ej_off, a = ay * 2 + ax;
+        for (int q = 0; q < 4; ++q) {
+          const double s = gmg_gp(q & 1), t = gmg_gp(q >> 1);
+          const double s1 = 1 - s, t1 = 1 - t;
+          const double N[4] = {s1 * t1, s * t1, s1 * t, s * t};
+          const double Nx[4] = {-t1 * ihx, t1 * ihx, -t * ihx, t * ihx};
+          const double Ny[4] = {-s1 * ihy, -s * ihy, s1 * ihy, s * ihy};
+          const double cq = (double)c[4 * e + q];
+          for (int b = 0; b < 4; ++b) {
+            const int k = ((b >> 1) - ay + 1) * 3 + ((b & 1) - ax + 1);
+            acc[k] += w * (cq * N[a] * N[b] + kappa * (Nx[a] * Nx[b] + Ny[a] * Ny[b]));
+          }
+        }
+      }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) S[sidx<1>(k, 0, 0, n, nn)] = (T)acc[k];
+  }
+}
+
+// Level-0 free mask from the DOF mask: bit c = component c free.
+template <int B>
+__global__ void k_fm0(size_t nn, const uint8_t *__restrict__ dofm, uint8_t *__restrict__ fm) {
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
+       n += (size_t)gridDim.x * blockDim.x) {
+    const uint8_t m = dofm ? dofm[n] : 0;
+    fm[n] = (B == 2) ? (uint8_t)(~m & 3) : (uint8_t)((m & 4) ? 0 : 1);
+  }
+}
+
+// Inverse diagonal, free mask (diag > 0 and previously free) and Gershgorin bound of
+// D^-1 A over free rows/columns.
+template <class T, int B>
+__global__ void k_diag_bound(int nx, int ny, const T *__restrict__ S, uint8_t *__restrict__ fm,
+                             T *__restrict__ invd) {
+  const size_t nn = (size_t)(nx + 1) * (ny + 1);
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
+       n += (size_t)gridDim.x * blockDim.x) {
+    uint8_t f = fm[n];
+    uint8_t fnew = 0;
+    for (int r = 0; r < B; ++r) {
+      const double a = (double)S[sidx<B>(4, r, r, n, nn)];
+      const bool free_r = ((f >> r) & 1) && a > 0.0;
+      invd[B * n + r] = free_r ? (T)(1.0 / a) : T(0);
+      if (free_r) fnew |= (uint8_t)(1u << r);
+    }
+    fm[n] = fnew;
+  }
+}
+
+template <class T, int B>
+__global__ void k_bound(int nx, int ny, const T *__restrict__ S, const uint8_t *__restrict__ fm,
+                        RedWs ws, double *lmax) {
+  const size_t nn = (size_t)(nx + 1) * (ny + 1);
+  double bound = 0.0;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
+       n += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(n % (nx + 1)), j = (int)(n / (nx + 1));
+    const uint8_t f = fm[n];
+    for (int r = 0; r < B; ++r) {
+      if (!((f >> r) & 1)) continue;
+      double rs = 0.0;
+      for (int k = 0; k < 9; ++k) {
+        const int di = k % 3 - 1, dj = k / 3 - 1;
+        const int ii = i + di, jj = j + dj;
+        if (ii < 0 || ii > nx || jj < 0 || jj > ny) continue;
+        const uint8_t fn = fm[(size_t)jj * (nx + 1) + ii];
+        for (int c = 0; c < B; ++c)
+          if ((fn >> c) & 1) rs += fabs((double)S[sidx<B>(k, r, c, n, nn)]);
+      }
+      bound = fmax(bound, rs / (double)S[sidx<B>(4, r, r, n, nn)]);
+    }
+  }
+  grid_max(bound, ws, lmax);
+}
+
+// Galerkin product A_c = P^T A_f P with P bilinear, rows of non-free fine DOFs removed.
+template <class T, int B>
+__global__ void k_rap(int nxf, int nyf, const T *__restrict__ Sf, const uint8_t *__restrict__ fmf,
+                      int nxc, int nyc, T *__restrict__ Sc) {
+  const size_t nnf = (size_t)(nxf + 1) * (nyf + 1);
+  const size_t nnc = (size_t)(nxc + 1) * (nyc + 1);
+  for (size_t I = blockIdx.x * (size_t)blockDim.x + threadIdx.x; I < nnc;
+       I += (size_t)gridDim.x * blockDim.x) {
+    const int Ix = (int)(I % (nxc + 1)), Iy = (int)(I / (nxc + 1));
+    double acc[9][B * B];
+    for (int k = 0; k < 9; ++k)
+      for (int q = 0; q < B * B; ++q) acc[k][q] = 0.0;
+    for (int a = -1; a <= 1; ++a)
+      for (int b = -1; b <= 1; ++b) {
+        const int ix = 2 * Ix + a, iy = 2 * Iy + b;
+        if (ix < 0 || ix > nxf || iy < 0 || iy > nyf) continue;
+        const double wi = (a == 0 ? 1.0 : 0.5) * (b == 0 ? 1.0 : 0.5);
+        const size_t fi = (size_t)iy * (nxf + 1) + ix;
+        const uint8_t mi = fmf[fi];
+        if (!mi) continue;
+        for (int k = 0; k < 9; ++k) {
+          const int jx = ix + k % 3 - 1, jy = iy + k / 3 - 1;
+          if (jx < 0 || jx > nxf || jy < 0 || jy > nyf) continue;
+          const uint8_t mj = fmf[(size_t)jy * (nxf + 1) + jx];
+          if (!mj) continue;
+          double av[B * B];
+          for (int r = 0; r < B; ++r)
+            for (int c = 0; c < B; ++c)
+              av[r * B + c] = (((mi >> r) & 1) && ((mj >> c) & 1))
+                                  ? (double)Sf[sidx<B>(k, r, c, fi, nnf)] : 0.0;
+          // coarse parents of (jx, jy)
+          const int px0 = jx >> 1, py0 = jy >> 1;
+          const int npx = (jx & 1) ? 2 : 1, npy = (jy & 1) ? 2 : 1;
+          for (int u = 0; u < npx; ++u)
+            for (int v = 0; v < npy; ++v) {
+              const int Jx = px0 + u, Jy = py0 + v;
+              const double wj = (npx == 2 ? 0.5 : 1.0) * (npy == 2 ? 0.5 : 1.0);
+              const int kc = (Jy - Iy + 1) * 3 + (Jx - Ix + 1);
+              for (int q = 0; q < B * B; ++q) acc[kc][q] += wi * wj * av[q];
+            }
+        }
+      }
+    for (int k = 0; k < 9; ++k)
+      for (int q = 0; q < B * B; ++q) Sc[sidx<B>(k, q / B, q % B, I, nnc)] = (T)acc[k][q];
+  }
+}
+
+// Coarse free mask before the diagonal test: a coarse DOF is a candidate if any fine
+// child DOF of that component is free.
+template <int B>
+__global__ void k_fm_coarse(int nxf, int nyf, const uint8_t *__restrict__ fmf, int nxc, int nyc,
+                            uint8_t *__restrict__ fmc) {
+  const size_t nnc = (size_t)(nxc + 1) * (nyc + 1);
+  for (size_t I = blockIdx.x * (size_t)blockDim.x + threadIdx.x; I < nnc;
+       I += (size_t)gridDim.x * blockDim.x) {
+    const int Ix = (int)(I % (nxc + 1)), Iy = (int)(I / (nxc + 1));
+    uint8_t m = 0;
+    for (int a = -1; a <= 1; ++a)
+      for (int b = -1; b <= 1; ++b) {
+        const int ix = 2 * Ix + a, iy = 2 * Iy + b;
+        if (ix < 0 || ix > nxf || iy < 0 || iy > nyf) continue;
+        m |= fmf[(size_t)iy * (nxf + 1) + ix];
+      }
+    fmc[I] = m;
+  }
+}
+
+// y = A x  (mode 0) or y = b - A x (mode 1), rows of non-free DOFs zero.
+template <class T, int B>
+__global__ void k_sten_apply(int nx, int ny, const T *__restrict__ S,
+                             const uint8_t *__restrict__ fm, const T *__restrict__ x,
+                             const T *__restrict__ b, T *__restrict__ y, int mode) {
+  const size_t nn = (size_t)(nx + 1) * (ny + 1);
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
+       n += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(n % (nx + 1)), j = (int)(n / (nx + 1));
+    const uint8_t f = fm[n];
+    T acc[B];
+    for (int r = 0; r < B; ++r) acc[r] = T(0);
+    for (int k = 0; k < 9; ++k) {
+      const int ii = i + k % 3 - 1, jj = j + k / 3 - 1;
+      if (ii < 0 || ii > nx || jj < 0 || jj > ny) continue;
+      const size_t m = (size_t)jj * (nx + 1) + ii;
+      const uint8_t fn = fm[m];
+      for (int c = 0; c < B; ++c) {
+        if (!((fn >> c) & 1)) continue;
+        const T xv = x[B * m + c];
+        for (int r = 0; r < B; ++r) acc[r] += S[sidx<B>(k, r, c, n, nn)] * xv;
+      }
+    }
+    for (int r = 0; r < B; ++r) {
+      T v = mode ? b[B * n + r] - acc[r] : acc[r];
+      y[B * n + r] = ((f >> r) & 1) ? v : T(0);
+    }
+  }
+}
+
+// Chebyshev on [lmax/10, lmax]: theta = 0.55 lmax, delta = 0.45 lmax, sigma = 11/9.
+// first step from x = 0: d = D^-1 b / theta; x = d; r = b
+template <class T>
+__global__ void k_cheb_first(size_t n, const T *__restrict__ b, const T *__restrict__ invd,
+                             const double *lmax, T *__restrict__ x, T *__restrict__ d,
+                             T *__restrict__ r) {
+  const T it = (T)(1.0 / (0.55 * *lmax));
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const T bi = b[i];
+    const T di = invd[i] * bi * it;
+    d[i] = di;
+    x[i] = di;
+    r[i] = bi;
+  }
+}
+// first step from x != 0 with y = A x: r = b - y; d = D^-1 r / theta; x += d
+template <class T>
+__global__ void k_cheb_first_x(size_t n, const T *__restrict__ b, const T *__restrict__ y,
+                               const T *__restrict__ invd, const double *lmax, T *__restrict__ x,
+                               T *__restrict__ d, T *__restrict__ r) {
+  const T it = (T)(1.0 / (0.55 * *lmax));
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const T ri = b[i] - y[i];
+    const T di = invd[i] * ri * it;
+    r[i] = ri;
+    d[i] = di;
+    x[i] += di;
+  }
+}
+// later step with y = A d: r -= y; d = c1 d + c2 D^-1 r; x += d
+template <class T>
+__global__ void k_cheb_step(size_t n, const T *__restrict__ y, const T *__restrict__ invd,
+                            const double *lmax, double c1, double c2, T *__restrict__ x,
+                            T *__restrict__ d, T *__restrict__ r) {
+  const T a = (T)c1, bb = (T)(c2 / (0.45 * *lmax));
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const T ri = r[i] - y[i];
+    const T di = a * d[i] + bb * invd[i] * ri;
+    r[i] = ri;
+    d[i] = di;
+    x[i] += di;
+  }
+}
+// r = b - y
+template <class T>
+__global__ void k_sub(size_t n, const T *__restrict__ b, const T *__restrict__ y, T *__restrict__ r) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    r[i] = b[i] - y[i];
+}
+
+// b_c = P^T r_f over free DOFs.
+template <class T, int B>
+__global__ void k_restrict(int nxf, int nyf, const T *__restrict__ rf, const uint8_t *__restrict__ fmf,
+                           int nxc, int nyc, const uint8_t *__restrict__ fmc, T *__restrict__ bc) {
+  const size_t nnc = (size_t)(nxc + 1) * (nyc + 1);
+  for (size_t I = blockIdx.x * (size_t)blockDim.x + threadIdx.x; I < nnc;
+       I += (size_t)gridDim.x * blockDim.x) {
+    const int Ix = (int)(I % (nxc + 1)), Iy = (int)(I / (nxc + 1));
+    T acc[B];
+    for (int c = 0; c < B; ++c) acc[c] = T(0);
+    for (int a = -1; a <= 1; ++a)
+      for (int b = -1; b <= 1; ++b) {
+        const int ix = 2 * Ix + a, iy = 2 * Iy + b;
+        if (ix < 0 || ix > nxf || iy < 0 || iy > nyf) continue;
+        const T wi = T((a == 0 ? 1.0 : 0.5) * (b == 0 ? 1.0 : 0.5));
+        const size_t fi = (size_t)iy * (nxf + 1) + ix;
+        const uint8_t m = fmf[fi];
+        for (int c = 0; c < B; ++c)
+          if ((m >> c) & 1) acc[c] += wi * rf[B * fi + c];
+      }
+    const uint8_t mc = fmc[I];
+    for (int c = 0; c < B; ++c) bc[B * I + c] = ((mc >> c) & 1) ? acc[c] : T(0);
+  }
+}
+
+// x_f += P x_c over free fine DOFs.
+template <class T, int B>
+__global__ void k_prolong_add(int nxf, int nyf, const uint8_t *__restrict__ fmf, int nxc,
+                              const T *__restrict__ xc, T *__restrict__ xf) {
+  const size_t nnf = (size_t)(nxf + 1) * (nyf + 1);
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nnf;
+       n += (size_t)gridDim.x * blockDim.x) {
+    const uint8_t m = fmf[n];
+    if (!m) continue;
+    const int ix = (int)(n % (nxf + 1)), iy = (int)(n / (nxf + 1));
+    const int px0 = ix >> 1, py0 = iy >> 1;
+    const int npx = (ix & 1) ? 2 : 1, npy = (iy & 1) ? 2 : 1;
+    T acc[B];
+    for (int c = 0; c < B; ++c) acc[c] = T(0);
+    for (int u = 0; u < npx; ++u)
+      for (int v = 0; v < npy; ++v) {
+        const T wj = T((npx == 2 ? 0.5 : 1.0) * (npy == 2 ? 0.5 : 1.0));
+        const size_t J = (size_t)(py0 + v) * (nxc + 1) + (px0 + u);
+        for (int c = 0; c < B; ++c) acc[c] += wj * xc[B * J + c];
+      }
+    for (int c = 0; c < B; ++c)
+      if ((m >> c) & 1) xf[B * n + c] += acc[c];
+  }
+}
+
+// x = Cinv b (dense, one CTA).
+template <class T>
+__global__ void k_dense(int nc, const T *__restrict__ Cinv, const T *__restrict__ b,
+                        T *__restrict__ x) {
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < nc; ++j) s += (double)Cinv[(size_t)i * nc + j] * (double)b[j];
+    x[i] = (T)s;
+  }
+}
+
+// FP64 host Cholesky inverse of an SPD matrix (in place); non-positive pivots are
+// lifted to a small fraction of the largest diagonal entry.
+void host_spd_inverse(double *A, int n) {
+  double dmax = 0.0;
+  for (int i = 0; i < n; ++i) dmax = fmax(dmax, A[(size_t)i * n + i]);
+  const double floor_p = (dmax > 0 ? dmax : 1.0) * 1e-14;
+  std::vector<double> L((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double s = A[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+    if (!(s > floor_p)) s = floor_p;
+    const double ljj = sqrt(s);
+    L[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+      L[(size_t)i * n + j] = t / ljj;
+    }
+  }
+  // inverse via solves with unit vectors
+  std::vector<double> y(n);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) {
+      double t = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) t -= L[(size_t)i * n + k] * y[k];
+      y[i] = t / L[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double t = y[i];
+      for (int k = i + 1; k < n; ++k) t -= L[(size_t)k * n + i] * A[(size_t)k * n + c];
+      A[(size_t)i * n + c] = t / L[(size_t)i * n + i];
+    }
+  }
+}
+
+}  // namespace
+
+// ---- host side ------------------------------------------------------------------------------
+template <class T>
+cudaError_t gmg_alloc(Gmg<T> &G, int nx, int ny, int B, const RedWs &ws) {
+  G.B = B;
+  G.ws = ws;
+  int l = 0;
+  int cx = nx, cy = ny;
+  while (true) {
+    GmgLevel<T> &L = G.lv[l];
+    L.nx = cx;
+    L.ny = cy;
+    L.nn = (size_t)(cx + 1) * (cy + 1);
+    const size_t nb = (size_t)B * L.nn;
+    cudaError_t e;
+    if ((e = cudaMalloc(&L.S, 9 * B * B * L.nn * sizeof(T))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&L.invd, nb * sizeof(T))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&L.x, nb * sizeof(T))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&L.b, nb * sizeof(T))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&L.r, nb * sizeof(T))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&L.dv, nb * sizeof(T))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&L.y, nb * sizeof(T))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&L.fm, L.nn)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&L.lmax, sizeof(double))) != cudaSuccess) return e;
+    ++l;
+    if ((cx <= GMG_COARSE_MAX && cy <= GMG_COARSE_MAX) || l == GMG_MAX_LEVELS) break;
+    cx = (cx + 1) / 2;
+    cy = (cy + 1) / 2;
+  }
+  G.nl = l;
+  const GmgLevel<T> &C = G.lv[l - 1];
+  G.ncoarse = (int)(B * C.nn);
+  cudaError_t e = cudaMalloc(&G.cinv, (size_t)G.ncoarse * G.ncoarse * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&G.hS, 9 * B * B * C.nn * sizeof(T) + C.nn)) != cudaSuccess) return e;
+  G.hA = new double[(size_t)G.ncoarse * G.ncoarse];
+  G.hInv = new T[(size_t)G.ncoarse * G.ncoarse];
+  return cudaSuccess;
+}
+
+template <class T>
+void gmg_free(Gmg<T> &G) {
+  for (int l = 0; l < G.nl; ++l) {
+    GmgLevel<T> &L = G.lv[l];
+    void *p[] = {L.S, L.invd, L.x, L.b, L.r, L.dv, L.y, L.fm, L.lmax};
+    for (void *q : p)
+      if (q) cudaFree(q);
+    L = GmgLevel<T>();
+  }
+  if (G.cinv) cudaFree(G.cinv);
+  if (G.hS) cudaFreeHost(G.hS);
+  delete[] G.hA;
+  delete[] G.hInv;
+  G.cinv = nullptr;
+  G.hS = nullptr;
+  G.hA = nullptr;
+  G.hInv = nullptr;
+  G.nl = 0;
+}
+
+template <class T, int B>
+static cudaError_t gmg_setup_common(Gmg<T> &G, const GridD &g, cudaStream_t st) {
+  // level 0 mask, diagonal, bound
+  GmgLevel<T> &L0 = G.lv[0];
+  k_fm0<B><<<nblk(L0.nn), 256, 0, st>>>(L0.nn, g.dofm, L0.fm);
+  for (int l = 0; l < G.nl; ++l) {
+    GmgLevel<T> &L = G.lv[l];
+    if (l > 0) {
+      GmgLevel<T> &F = G.lv[l - 1];
+      k_rap<T, B><<<nblk(L.nn), 128, 0, st>>>(F.nx, F.ny, F.S, F.fm, L.nx, L.ny, L.S);
+      k_fm_coarse<B><<<nblk(L.nn), 256, 0, st>>>(F.nx, F.ny, F.fm, L.nx, L.ny, L.fm);
+    }
+    k_diag_bound<T, B><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.fm, L.invd);
+    k_bound<T, B><<<nblk(L.nn, G.ws.max_blocks), 256, 0, st>>>(L.nx, L.ny, L.S, L.fm, G.ws, L.lmax);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // coarsest dense inverse on the host
+  GmgLevel<T> &C = G.lv[G.nl - 1];
+  const size_t sb = 9 * B * B * C.nn * sizeof(T);
+  if ((e = cudaMemcpyAsync(G.hS, C.S, sb, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  uint8_t *hfm = (uint8_t *)((char *)G.hS + sb);
+  if ((e = cudaMemcpyAsync(hfm, C.fm, C.nn, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  const int n = G.ncoarse, nx = C.nx, ny = C.ny;
+  double *A = G.hA;
+  memset(A, 0, sizeof(double) * (size_t)n * n);
+  for (size_t node = 0; node < C.nn; ++node) {
+    const int i = (int)(node % (nx + 1)), j = (int)(node / (nx + 1));
+    for (int r = 0; r < B; ++r) {
+      const int row = (int)(B * node + r);
+      if (!((hfm[node] >> r) & 1)) {
+        A[(size_t)row * n + row] = 1.0;
+        continue;
+      }
+      for (int k = 0; k < 9; ++k) {
+        const int ii = i + k % 3 - 1, jj = j + k / 3 - 1;
+        if (ii < 0 || ii > nx || jj < 0 || jj > ny) continue;
+        const size_t m = (size_t)jj * (nx + 1) + ii;
+        for (int c = 0; c < B; ++c) {
+          if (!((hfm[m] >> c) & 1)) continue;
+          A[(size_t)row * n + (B * m + c)] = (double)G.hS[((size_t)(k * B * B + r * B + c)) * C.nn + node];
+        }
+      }
+    }
+  }
+  // symmetrise (the Galerkin product is symmetric up to rounding)
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      const double v = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
+      A[(size_t)i * n + j] = A[(size_t)j * n + i] = v;
+    }
+  host_spd_inverse(A, n);
+  for (size_t q = 0; q < (size_t)n * n; ++q) G.hInv[q] = (T)A[q];
+  // zero rows/cols of non-free coarse DOFs so the coarse correction vanishes there
+  for (size_t node = 0; node < C.nn; ++node)
+    for (int r = 0; r < B; ++r)
+      if (!((hfm[node] >> r) & 1)) {
+        const int row = (int)(B * node + r);
+        for (int c = 0; c < n; ++c) G.hInv[(size_t)row * n + c] = G.hInv[(size_t)c * n + row] = T(0);
+      }
+  if ((e = cudaMemcpyAsync(G.cinv, G.hInv, sizeof(T) * (size_t)n * n, cudaMemcpyHostToDevice, st)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  G.ready = true;
+  return cudaSuccess;
+}
+
+template <class T>
+cudaError_t gmg_setup_elas(Gmg<T> &G, const GridD &g, const MatD &m, const T *d,
+                           const uint8_t *tens, cudaStream_t st) {
+  k_fine_stencil_elas<T><<<nblk(G.lv[0].nn), 128, 0, st>>>(g, m, d, tens, G.lv[0].S);
+  return gmg_setup_common<T, 2>(G, g, st);
+}
+
+template <class T>
+cudaError_t gmg_setup_damage(Gmg<T> &G, const GridD &g, const T *c, double kappa,
+                             cudaStream_t st) {
+  k_fine_stencil_damage<T><<<nblk(G.lv[0].nn), 128, 0, st>>>(g, c, kappa, G.lv[0].S);
+  return gmg_setup_common<T, 1>(G, g, st);
+}
+
+// ---- V-cycle launchers ------------------------------------------------------------------------
+template <class T>
+void gmg_sten_apply(const Gmg<T> &G, int l, const T *x, const T *b, T *y, int mode,
+                    cudaStream_t st) {
+  const GmgLevel<T> &L = G.lv[l];
+  if (G.B == 2)
+    k_sten_apply<T, 2><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.fm, x, b, y, mode);
+  else
+    k_sten_apply<T, 1><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.fm, x, b, y, mode);
+}
+template <class T>
+void gmg_cheb_first(const Gmg<T> &G, int l, const T *b, T *x, T *d, T *r, cudaStream_t st) {
+  const GmgLevel<T> &L = G.lv[l];
+  const size_t n = (size_t)G.B * L.nn;
+  k_cheb_first<T><<<nblk(n), 256, 0, st>>>(n, b, L.invd, L.lmax, x, d, r);
+}
+template <class T>
+void gmg_cheb_first_x(const Gmg<T> &G, int l, const T *b, const T *y, T *x, T *d, T *r,
+                      cudaStream_t st) {
+  const GmgLevel<T> &L = G.lv[l];
+  const size_t n = (size_t)G.B * L.nn;
+  k_cheb_first_x<T><<<nblk(n), 256, 0, st>>>(n, b, y, L.invd, L.lmax, x, d, r);
+}
+template <class T>
+void gmg_cheb_step(const Gmg<T> &G, int l, const T *y, T *x, T *d, T *r, cudaStream_t st) {
+  // rho0 = 1/sigma = 9/11, rho1 = 1/(2 sigma - rho0) = 99/161
+  const double rho0 = 9.0 / 11.0, rho1 = 99.0 / 161.0;
+  const GmgLevel<T> &L = G.lv[l];
+  const size_t n = (size_t)G.B * L.nn;
+  k_cheb_step<T><<<nblk(n), 256, 0, st>>>(n, y, L.invd, L.lmax, rho1 * rho0, 2.0 * rho1, x, d, r);
+}
+template <class T>
+void gmg_sub(size_t n, const T *b, const T *y, T *r, cudaStream_t st) {
+  k_sub<T><<<nblk(n), 256, 0, st>>>(n, b, y, r);
+}
+template <class T>
+void gmg_restrict(const Gmg<T> &G, int l, const T *rf, T *bc, cudaStream_t st) {
+  const GmgLevel<T> &F = G.lv[l], &C = G.lv[l + 1];
+  if (G.B == 2)
+    k_restrict<T, 2><<<nblk(C.nn), 256, 0, st>>>(F.nx, F.ny, rf, F.fm, C.nx, C.ny, C.fm, bc);
+  else
+    k_restrict<T, 1><<<nblk(C.nn), 256, 0, st>>>(F.nx, F.ny, rf, F.fm, C.nx, C.ny, C.fm, bc);
+}
+template <class T>
+void gmg_prolong_add(const Gmg<T> &G, int l, const T *xc, T *xf, cudaStream_t st) {
+  const GmgLevel<T> &F = G.lv[l], &C = G.lv[l + 1];
+  if (G.B == 2)
+    k_prolong_add<T, 2><<<nblk(F.nn), 256, 0, st>>>(F.nx, F.ny, F.fm, C.nx, xc, xf);
+  else
+    k_prolong_add<T, 1><<<nblk(F.nn), 256, 0, st>>>(F.nx, F.ny, F.fm, C.nx, xc, xf);
+}
+template <class T>
+void gmg_dense(const Gmg<T> &G, const T *b, T *x, cudaStream_t st) {
+  k_dense<T><<<1, 256, 0, st>>>(G.ncoarse, G.cinv, b, x);
+}
+
+#define GMG_INST(T)                                                                            \
+  template cudaError_t gmg_alloc<T>(Gmg<T> &, int, int, int, const RedWs &);                   \
+  template void gmg_free<T>(Gmg<T> &);                                                         \
+  template cudaError_t gmg_setup_elas<T>(Gmg<T> &, const GridD &, const MatD &, const T *,     \
+                                         const uint8_t *, cudaStream_t);                       \
+  template cudaError_t gmg_setup_damage<T>(Gmg<T> &, const GridD &, const T *, double,         \
+                                           cudaStream_t);                                      \
+  template void gmg_sten_apply<T>(const Gmg<T> &, int, const T *, const T *, T *, int,         \
+                                  cudaStream_t);                                               \
+  template void gmg_cheb_first<T>(const Gmg<T> &, int, const T *, T *, T *, T *, cudaStream_t); \
+  template void gmg_cheb_first_x<T>(const Gmg<T> &, int, const T *, const T *, T *, T *, T *,  \
+                                    cudaStream_t);                                             \
+  template void gmg_cheb_step<T>(const Gmg<T> &, int, const T *, T *, T *, T *, cudaStream_t);  \
+  template void gmg_sub<T>(size_t, const T *, const T *, T *, cudaStream_t);                    \
+  template void gmg_restrict<T>(const Gmg<T> &, int, const T *, T *, cudaStream_t);             \
+  template void gmg_prolong_add<T>(const Gmg<T> &, int, const T *, T *, cudaStream_t);          \
+  template void gmg_dense<T>(const Gmg<T> &, const T *, T *, cudaStream_t);
+GMG_INST(double)
+GMG_INST(float)
+
+}  // namespace pf

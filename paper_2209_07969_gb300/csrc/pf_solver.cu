@@ -17,10 +17,17 @@
 #include <new>
 #include <vector>
 
+#include "pf_gmg.cuh"
 #include "pf_internal.cuh"
 #include "pf_vec.cuh"
 
 using namespace pf;
+
+struct GraphSlot {
+  cudaGraphExec_t exec = nullptr;
+  int launches = 0;
+  size_t n = 0;
+};
 
 struct pf_ctx {
   int device = 0;
@@ -50,8 +57,13 @@ struct pf_ctx {
   // FP32 copies for the inner solves
   float *fb = nullptr, *fx = nullptr, *fr = nullptr, *fz = nullptr, *fp = nullptr,
         *fq = nullptr, *finv = nullptr, *fd = nullptr, *fc = nullptr;
+  double *csolve = nullptr;  // Q: coefficient of the current d-solve
   KrylovScal *sc = nullptr;
   RedWs ws{};
+  Gmg<double> gu, gd;        // multigrid hierarchies (FP64 mode)
+  Gmg<float> gu32, gd32;     // multigrid hierarchies (FP32 inner solves)
+  GraphSlot graphs[4];
+  bool use_graphs = true;
   double *dscal = nullptr;   // device scalars for norms / residual / reaction
   double *hbuf = nullptr;    // pinned host mirror
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -102,33 +114,80 @@ GridD grid_nomask(const pf_ctx *ctx) {
 }
 
 // ---- Krylov ----------------------------------------------------------------------------
-struct Work {
-  void *b, *x, *r, *z, *p, *q, *inv;
-};
+// Graph slots: one captured CUDA graph per solver instance (operator x preconditioner x
+// precision).  Every pointer an iteration touches is a fixed context buffer, so a graph
+// captured once stays valid; operator data (d, tension bits, coefficients, multigrid
+// stencils) are rewritten in place between solves.
+enum { SL_U = 0, SL_D = 1, SL_COUNT = 2 };
 
-// Jacobi-preconditioned CG on a masked SPD operator.  `apply(p, q, epi)` computes q = A p
-// and runs the fused dot epilogue.  Returns iterations; *ok = converged.
-template <class T, class Apply>
-pf_status pcg(pf_ctx *ctx, Apply apply, size_t n, T *b, T *x, T *r, T *z, T *p, T *q,
-              const T *inv, double rtol, int maxit, int *iters, bool *ok) {
+// Preconditioned CG on a masked SPD operator.  apply(p, q, epi): q = A p with the fused
+// dot epilogue; fine(x, y): y = A x without epilogue (multigrid smoothing).  G == nullptr
+// selects Jacobi with inverse diagonal `inv`.
+template <class T, class Apply, class Fine>
+pf_status pcg(pf_ctx *ctx, int slot, Apply apply, Fine fine, Gmg<T> *G, size_t n, T *b, T *x,
+              T *r, T *z, T *p, T *q, const T *inv, double rtol, int maxit, int *iters,
+              bool *ok) {
   cudaStream_t st = ctx->st;
-  cg_init<T>(n, b, x, r, z, p, inv, ctx->sc, ctx->ws, st);
+  *iters = 0;
+  if (G) {
+    pcg_init<T>(n, b, x, r, ctx->sc, ctx->ws, st);
+  } else {
+    cg_init<T>(n, b, x, r, z, p, inv, ctx->sc, ctx->ws, st);
+  }
   ctx->launches++;
   CKS(check_launch(ctx));
   CKS(read_scalars(ctx, &ctx->sc->rr, sizeof(double)));
   const double rr0 = ctx->hbuf[0];
-  *iters = 0;
   *ok = true;
   if (!(rr0 > 0.0)) return PF_OK;
+  if (G) {
+    ctx->launches += gmg_vcycle<T>(*G, fine, r, z, st);
+    pcg_rz<T>(n, r, z, p, 1, ctx->sc, ctx->ws, st);
+    ctx->launches++;
+  }
+  auto body = [&]() -> int {
+    int nl = 1;
+    apply(p, q, EPI_CG_ALPHA);
+    if (G) {
+      pcg_update<T>(n, x, r, p, q, ctx->sc, ctx->ws, st);
+      nl += 1 + gmg_vcycle<T>(*G, fine, r, z, st);
+      pcg_rz<T>(n, r, z, p, 0, ctx->sc, ctx->ws, st);
+      cg_dir<T>(n, z, p, ctx->sc, st);
+      nl += 2;
+    } else {
+      cg_update<T>(n, x, r, z, p, q, inv, ctx->sc, ctx->ws, st);
+      cg_dir<T>(n, z, p, ctx->sc, st);
+      nl += 2;
+    }
+    return nl;
+  };
+  const int sidx = slot * 2 + (G ? 1 : 0);
+  GraphSlot &S = ctx->graphs[sidx];
+  if (ctx->use_graphs && !S.exec) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    S.launches = body();
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&S.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      S.exec = nullptr;
+      return set_err(ctx, PF_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    S.n = n;
+  }
   const double target = rtol * rtol * rr0;
   const int every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 8;
   int it = 0;
   *ok = false;
   while (it < maxit) {
-    apply(p, q, EPI_CG_ALPHA);
-    cg_update<T>(n, x, r, z, p, q, inv, ctx->sc, ctx->ws, st);
-    cg_dir<T>(n, z, p, ctx->sc, st);
-    ctx->launches += 3;
+    if (S.exec) {
+      CK(cudaGraphLaunch(S.exec, st));
+      ctx->launches += S.launches;
+    } else {
+      ctx->launches += body();
+    }
     ++it;
     if (it % every == 0 || it == maxit) {
       CKS(check_launch(ctx));
@@ -150,23 +209,13 @@ pf_status pcg(pf_ctx *ctx, Apply apply, size_t n, T *b, T *x, T *r, T *z, T *p, 
   return PF_OK;
 }
 
-// Linear solve A x = b (FP64 b, x; constrained entries of b are zero).  FP64 mode:
-// CG to tol_lin.  FP32_IR: x = 0; repeat {r = b - A x (FP64); stop if ||r|| <=
-// tol_lin ||b||; solve A_32 e = r_32 to tol_inner; x += e}.
-template <class ApplyD, class ApplyF>
-pf_status lin_solve(pf_ctx *ctx, ApplyD applyd, ApplyF applyf, size_t n, int ncomp,
-                    const double *b, double *x, const double *inv64, const float *inv32,
-                    int *iters, int *refines, bool *ok) {
+// FP32 inner solves inside FP64 iterative refinement:  x = 0; repeat {solve A_32 e =
+// r_32 to tol_inner; x += e; r = b - A_64 x; stop when ||r|| <= tol_lin ||b||}.
+// inner(iters, ok) solves with rhs ctx->fb into ctx->fx.
+template <class ApplyD, class Inner>
+pf_status refine(pf_ctx *ctx, ApplyD applyd, Inner inner, size_t n, int ncomp, const double *b,
+                 double *x, int *iters, int *refines, bool *ok) {
   cudaStream_t st = ctx->st;
-  if (ctx->precision == PF_FP64) {
-    CK(cudaMemcpyAsync(ctx->kb, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    int it = 0;
-    CKS(pcg<double>(ctx, applyd, n, ctx->kb, x, ctx->kr, ctx->kz, ctx->kp, ctx->kq, inv64,
-                    ctx->opt.tol_lin, ctx->opt.max_lin, &it, ok));
-    *iters += it;
-    return PF_OK;
-  }
-  // FP32 inner solves with FP64 refinement
   CK(cudaMemsetAsync(x, 0, n * sizeof(double), st));
   CK(cudaMemcpyAsync(ctx->kres, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   norms(n, ncomp, ctx->g.dofm, b, ctx->dscal, ctx->ws, st);
@@ -181,18 +230,16 @@ pf_status lin_solve(pf_ctx *ctx, ApplyD applyd, ApplyF applyf, size_t n, int nco
     ctx->launches++;
     int it = 0;
     bool iok = false;
-    CKS(pcg<float>(ctx, applyf, n, ctx->fb, ctx->fx, ctx->fr, ctx->fz, ctx->fp, ctx->fq, inv32,
-                   ctx->opt.tol_inner, ctx->opt.max_lin, &it, &iok));
+    CKS(inner(&it, &iok));
     *iters += it;
     convert<float, double>(n, ctx->fx, ctx->kq, st);
     add(n, ctx->kq, x, st);
     ctx->launches += 2;
     (*refines)++;
-    // true residual in FP64
-    applyd(x, ctx->kq, EPI_NONE);
+    applyd(x, ctx->kq);
     masked_comb(n, ncomp, ctx->g.dofm, 1.0, b, 1.0, ctx->kq, ctx->kres, st);
     norms(n, ncomp, ctx->g.dofm, ctx->kres, ctx->dscal, ctx->ws, st);
-    ctx->launches += 2;
+    ctx->launches += 3;
     CKS(check_launch(ctx));
     CKS(read_scalars(ctx, ctx->dscal, sizeof(double)));
     const double rn = sqrt(ctx->hbuf[0]);
@@ -206,6 +253,58 @@ pf_status lin_solve(pf_ctx *ctx, ApplyD applyd, ApplyF applyf, size_t n, int nco
 }
 
 // ---- u-solve ---------------------------------------------------------------------------
+// One Newton correction: K_t(d, tension) kx = kb on free DOFs.
+pf_status newton_correction(pf_ctx *ctx, int *lin, int *refines, bool *ok) {
+  cudaStream_t st = ctx->st;
+  const size_t n = 2 * ctx->nn;
+  const bool mg = ctx->precond == PF_PRECOND_GMG;
+  if (ctx->precision == PF_FP64) {
+    auto A = [ctx, st](const double *xx, double *yy, int epi) {
+      elas_apply<double>(ctx->g, ctx->m, ctx->d, ctx->tens, xx, yy, st, ctx->sc, &ctx->ws, epi);
+    };
+    auto Af = [ctx, st](const double *xx, double *yy) {
+      elas_apply<double>(ctx->g, ctx->m, ctx->d, ctx->tens, xx, yy, st);
+    };
+    if (mg) {
+      cudaError_t e = gmg_setup_elas<double>(ctx->gu, ctx->g, ctx->m, ctx->d, ctx->tens, st);
+      if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
+    } else {
+      elas_diag<double>(ctx->g, ctx->m, ctx->d, ctx->tens, ctx->kz, st);
+      invert<double>(n, ctx->kz, ctx->kinv, st);
+      ctx->launches += 2;
+    }
+    int it = 0;
+    CKS(pcg<double>(ctx, SL_U, A, Af, mg ? &ctx->gu : nullptr, n, ctx->kb, ctx->kx, ctx->kr,
+                    ctx->kz, ctx->kp, ctx->kq, ctx->kinv, ctx->opt.tol_lin, ctx->opt.max_lin,
+                    &it, ok));
+    *lin += it;
+    return PF_OK;
+  }
+  auto Af32 = [ctx, st](const float *xx, float *yy, int epi) {
+    elas_apply<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, xx, yy, st, ctx->sc, &ctx->ws, epi);
+  };
+  auto Ff32 = [ctx, st](const float *xx, float *yy) {
+    elas_apply<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, xx, yy, st);
+  };
+  if (mg) {
+    cudaError_t e = gmg_setup_elas<float>(ctx->gu32, ctx->g, ctx->m, ctx->fd, ctx->tens, st);
+    if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
+  } else {
+    elas_diag<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, ctx->fz, st);
+    invert<float>(n, ctx->fz, ctx->finv, st);
+    ctx->launches += 2;
+  }
+  auto inner = [&](int *it, bool *iok) {
+    return pcg<float>(ctx, SL_U, Af32, Ff32, mg ? &ctx->gu32 : nullptr, n, ctx->fb, ctx->fx,
+                      ctx->fr, ctx->fz, ctx->fp, ctx->fq, ctx->finv, ctx->opt.tol_inner,
+                      ctx->opt.max_lin, it, iok);
+  };
+  auto AD = [ctx, st](const double *xx, double *yy) {
+    elas_apply<double>(ctx->g, ctx->m, ctx->d, ctx->tens, xx, yy, st);
+  };
+  return refine(ctx, AD, inner, n, 2, ctx->kb, ctx->kx, lin, refines, ok);
+}
+
 pf_status solve_u(pf_ctx *ctx, int *newton, int *lin, int *refines, bool *ok) {
   cudaStream_t st = ctx->st;
   const size_t n = 2 * ctx->nn;
@@ -233,32 +332,7 @@ pf_status solve_u(pf_ctx *ctx, int *newton, int *lin, int *refines, bool *ok) {
     masked_comb(n, 2, ctx->g.dofm, -1.0, ctx->F, 0.0, nullptr, ctx->kb, st);
     ctx->launches++;
     bool lok = false;
-    if (ctx->precision == PF_FP64) {
-      elas_diag<double>(ctx->g, ctx->m, ctx->d, ctx->tens, ctx->kz, st);
-      invert<double>(n, ctx->kz, ctx->kinv, st);
-      ctx->launches += 2;
-      auto ad = [&](const double *xx, double *yy, int epi) {
-        elas_apply<double>(ctx->g, ctx->m, ctx->d, ctx->tens, xx, yy, st, ctx->sc, &ctx->ws, epi);
-        ctx->launches++;
-      };
-      int it2 = 0;
-      CKS(pcg<double>(ctx, ad, n, ctx->kb, ctx->kx, ctx->kr, ctx->kz, ctx->kp, ctx->kq, ctx->kinv,
-                      ctx->opt.tol_lin, ctx->opt.max_lin, &it2, &lok));
-      *lin += it2;
-    } else {
-      elas_diag<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, ctx->fz, st);
-      invert<float>(n, ctx->fz, ctx->finv, st);
-      ctx->launches += 2;
-      auto ad = [&](const double *xx, double *yy, int epi) {
-        elas_apply<double>(ctx->g, ctx->m, ctx->d, ctx->tens, xx, yy, st, ctx->sc, &ctx->ws, epi);
-        ctx->launches++;
-      };
-      auto af = [&](const float *xx, float *yy, int epi) {
-        elas_apply<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, xx, yy, st, ctx->sc, &ctx->ws, epi);
-        ctx->launches++;
-      };
-      CKS(lin_solve(ctx, ad, af, n, 2, ctx->kb, ctx->kx, nullptr, ctx->finv, lin, refines, &lok));
-    }
+    CKS(newton_correction(ctx, lin, refines, &lok));
     add(n, ctx->kx, ctx->u, st);
     ctx->launches++;
     (*newton)++;
@@ -268,41 +342,65 @@ pf_status solve_u(pf_ctx *ctx, int *newton, int *lin, int *refines, bool *ok) {
 }
 
 // ---- d-solves ----------------------------------------------------------------------------
-// Solve K_dd(c) x = rhs on free DOFs for the correction form: the caller passes the
-// residual-form right-hand side (constrained entries zero).  c: FP64 per Gauss point.
+// Solve K_dd(c) x = rhs on free DOFs (rhs constrained entries zero).  c: FP64 per Gauss
+// point, copied into the fixed coefficient buffer the captured graphs read.
 pf_status solve_damage(pf_ctx *ctx, const double *c, const double *rhs, double *x, int *lin,
                        int *refines, bool *ok) {
   cudaStream_t st = ctx->st;
   const size_t n = ctx->nn;
   const double kappa = ctx->m.Gc * ctx->m.l;
+  const bool mg = ctx->precond == PF_PRECOND_GMG;
+  if (c != ctx->csolve)
+    CK(cudaMemcpyAsync(ctx->csolve, c, ctx->nq * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (ctx->precision == PF_FP64) {
-    damage_diag<double>(ctx->g, c, kappa, ctx->kz, st);
-    invert<double>(n, ctx->kz, ctx->kinv, st);
-    ctx->launches += 2;
-    auto ad = [&](const double *xx, double *yy, int epi) {
-      damage_apply<double>(ctx->g, c, kappa, xx, yy, st, ctx->sc, &ctx->ws, epi);
-      ctx->launches++;
+    auto A = [ctx, st, kappa](const double *xx, double *yy, int epi) {
+      damage_apply<double>(ctx->g, ctx->csolve, kappa, xx, yy, st, ctx->sc, &ctx->ws, epi);
     };
+    auto Af = [ctx, st, kappa](const double *xx, double *yy) {
+      damage_apply<double>(ctx->g, ctx->csolve, kappa, xx, yy, st);
+    };
+    if (mg) {
+      cudaError_t e = gmg_setup_damage<double>(ctx->gd, ctx->g, ctx->csolve, kappa, st);
+      if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
+    } else {
+      damage_diag<double>(ctx->g, ctx->csolve, kappa, ctx->kz, st);
+      invert<double>(n, ctx->kz, ctx->kinv, st);
+      ctx->launches += 2;
+    }
     CK(cudaMemcpyAsync(ctx->kb, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     int it = 0;
-    CKS(pcg<double>(ctx, ad, n, ctx->kb, x, ctx->kr, ctx->kz, ctx->kp, ctx->kq, ctx->kinv,
-                    ctx->opt.tol_lin, ctx->opt.max_lin, &it, ok));
+    CKS(pcg<double>(ctx, SL_D, A, Af, mg ? &ctx->gd : nullptr, n, ctx->kb, ctx->dd, ctx->kr,
+                    ctx->kz, ctx->kp, ctx->kq, ctx->kinv, ctx->opt.tol_lin, ctx->opt.max_lin,
+                    &it, ok));
+    if (x != ctx->dd) CK(cudaMemcpyAsync(x, ctx->dd, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     *lin += it;
     return PF_OK;
   }
-  convert<double, float>(ctx->nq, c, ctx->fc, st);
-  damage_diag<float>(ctx->g, ctx->fc, kappa, ctx->fz, st);
-  invert<float>(n, ctx->fz, ctx->finv, st);
-  ctx->launches += 3;
-  auto ad = [&](const double *xx, double *yy, int epi) {
-    damage_apply<double>(ctx->g, c, kappa, xx, yy, st, ctx->sc, &ctx->ws, epi);
-    ctx->launches++;
-  };
-  auto af = [&](const float *xx, float *yy, int epi) {
+  convert<double, float>(ctx->nq, ctx->csolve, ctx->fc, st);
+  ctx->launches++;
+  auto Af32 = [ctx, st, kappa](const float *xx, float *yy, int epi) {
     damage_apply<float>(ctx->g, ctx->fc, kappa, xx, yy, st, ctx->sc, &ctx->ws, epi);
-    ctx->launches++;
   };
-  return lin_solve(ctx, ad, af, n, 1, rhs, x, nullptr, ctx->finv, lin, refines, ok);
+  auto Ff32 = [ctx, st, kappa](const float *xx, float *yy) {
+    damage_apply<float>(ctx->g, ctx->fc, kappa, xx, yy, st);
+  };
+  if (mg) {
+    cudaError_t e = gmg_setup_damage<float>(ctx->gd32, ctx->g, ctx->fc, kappa, st);
+    if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
+  } else {
+    damage_diag<float>(ctx->g, ctx->fc, kappa, ctx->fz, st);
+    invert<float>(n, ctx->fz, ctx->finv, st);
+    ctx->launches += 2;
+  }
+  auto inner = [&](int *it, bool *iok) {
+    return pcg<float>(ctx, SL_D, Af32, Ff32, mg ? &ctx->gd32 : nullptr, n, ctx->fb, ctx->fx,
+                      ctx->fr, ctx->fz, ctx->fp, ctx->fq, ctx->finv, ctx->opt.tol_inner,
+                      ctx->opt.max_lin, it, iok);
+  };
+  auto AD = [ctx, st, kappa](const double *xx, double *yy) {
+    damage_apply<double>(ctx->g, ctx->csolve, kappa, xx, yy, st);
+  };
+  return refine(ctx, AD, inner, n, 1, rhs, x, lin, refines, ok);
 }
 
 // rhs = free ? b(H) - K(c) d : 0 ; then d += K_ff^-1 rhs.
@@ -388,9 +486,15 @@ void free_all(pf_ctx *c) {
                   c->bd, c->Kd, c->dd, c->flags,  c->active, c->dofm, c->tens, c->kb, c->kx,
                   c->kr, c->kz, c->kp, c->kq, c->kinv, c->kres, c->fb, c->fx, c->fr, c->fz,
                   c->fp, c->fq, c->finv, c->fd, c->fc, c->sc, c->ws.partials, c->ws.counter,
-                  c->dscal};
+                  c->dscal, c->csolve};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  gmg_free<double>(c->gu);
+  gmg_free<double>(c->gd);
+  gmg_free<float>(c->gu32);
+  gmg_free<float>(c->gd32);
+  for (GraphSlot &g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (c->hbuf) cudaFreeHost(c->hbuf);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -493,7 +597,7 @@ pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double 
   } while (0)
   AL(u, 2 * nn); AL(d, nn); AL(H, nq); AL(d_prev, nn); AL(F, 2 * nn);
   AL(Hk, nq); AL(cq, nq); AL(Hhalf, nq); AL(act, nq);
-  AL(bd, nn); AL(Kd, nn); AL(dd, nn);
+  AL(bd, nn); AL(Kd, nn); AL(dd, nn); AL(csolve, nq);
   AL(flags, nn); AL(dofm, nn); AL(tens, ne);
   if (mesh->elem_active) AL(active, ne);
   AL(kb, 2 * nn); AL(kx, 2 * nn); AL(kr, 2 * nn); AL(kz, 2 * nn); AL(kp, 2 * nn);
@@ -510,6 +614,17 @@ pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double 
   AL(ws.partials, 4 * ctx->ws.max_blocks);
   AL(ws.counter, 1);
 #undef AL
+  if (ctx->precond == PF_PRECOND_GMG) {
+    cudaError_t e1, e2;
+    if (ctx->precision == PF_FP64) {
+      e1 = gmg_alloc<double>(ctx->gu, mesh->nx, mesh->ny, 2, ctx->ws);
+      e2 = gmg_alloc<double>(ctx->gd, mesh->nx, mesh->ny, 1, ctx->ws);
+    } else {
+      e1 = gmg_alloc<float>(ctx->gu32, mesh->nx, mesh->ny, 2, ctx->ws);
+      e2 = gmg_alloc<float>(ctx->gd32, mesh->nx, mesh->ny, 1, ctx->ws);
+    }
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(PF_ENOMEM);
+  }
   if (cudaMallocHost((void **)&ctx->hbuf, 64) != cudaSuccess) return fail(PF_ENOMEM);
   if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess)
     return fail(PF_ECUDA);

@@ -141,6 +141,68 @@ __global__ void k_cg_dir(size_t n, const T *__restrict__ z, T *__restrict__ p,
     p[i] = z[i] + bt * p[i];
 }
 
+// ---- CG with an external preconditioner (multigrid) --------------------------------------
+// x = 0, r = b; rr = r.r
+template <class T>
+__global__ void k_pcg_init(size_t n, const T *__restrict__ b, T *__restrict__ x,
+                           T *__restrict__ r, KrylovScal *sc, RedWs ws) {
+  double rr = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const T ri = b[i];
+    x[i] = T(0);
+    r[i] = ri;
+    rr += (double)ri * (double)ri;
+  }
+  double v[1] = {rr}, tot[1];
+  if (vgrid_reduce<1>(v, ws, tot, false)) {
+    sc->rr = tot[0];
+    sc->rz = 0.0;
+    sc->breakdown = 0;
+    sc->alpha = 0.0;
+    sc->beta = 0.0;
+  }
+}
+
+// x += alpha p; r -= alpha q; rr = r.r
+template <class T>
+__global__ void k_pcg_update(size_t n, T *__restrict__ x, T *__restrict__ r,
+                             const T *__restrict__ p, const T *__restrict__ q, KrylovScal *sc,
+                             RedWs ws) {
+  const T a = (T)sc->alpha;
+  double rr = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    x[i] += a * p[i];
+    const T ri = r[i] - a * q[i];
+    r[i] = ri;
+    rr += (double)ri * (double)ri;
+  }
+  double v[1] = {rr}, tot[1];
+  if (vgrid_reduce<1>(v, ws, tot, false)) sc->rr = tot[0];
+}
+
+// rz_new = r.z; beta = rz_new / rz (0 on the first call, flagged by rz == 0); p = z + beta p
+// is left to k_cg_dir.  first != 0: p = z is written here directly.
+template <class T>
+__global__ void k_pcg_rz(size_t n, const T *__restrict__ r, const T *__restrict__ z,
+                         T *__restrict__ p, int first, KrylovScal *sc, RedWs ws) {
+  double rz = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const T zi = z[i];
+    rz += (double)r[i] * (double)zi;
+    if (first) p[i] = zi;
+  }
+  double v[1] = {rz}, tot[1];
+  if (vgrid_reduce<1>(v, ws, tot, false)) {
+    const double old = sc->rz;
+    sc->beta = (!first && old > 0.0 && isfinite(tot[0])) ? tot[0] / old : 0.0;
+    sc->rz = tot[0];
+    if (!(tot[0] > 0.0)) sc->breakdown = 1;
+  }
+}
+
 // ---- helpers ---------------------------------------------------------------------------
 // inv[i] = free && diag > 0 ? 1/diag : 0.
 template <class T>
@@ -274,6 +336,20 @@ void cg_dir(size_t n, const T *z, T *p, const KrylovScal *sc, cudaStream_t st) {
   k_cg_dir<T><<<vblocks(n, 1 << 16), VEC_THREADS, 0, st>>>(n, z, p, sc);
 }
 template <class T>
+void pcg_init(size_t n, const T *b, T *x, T *r, KrylovScal *sc, const RedWs &ws, cudaStream_t st) {
+  k_pcg_init<T><<<vblocks(n, ws.max_blocks), VEC_THREADS, 0, st>>>(n, b, x, r, sc, ws);
+}
+template <class T>
+void pcg_update(size_t n, T *x, T *r, const T *p, const T *q, KrylovScal *sc, const RedWs &ws,
+                cudaStream_t st) {
+  k_pcg_update<T><<<vblocks(n, ws.max_blocks), VEC_THREADS, 0, st>>>(n, x, r, p, q, sc, ws);
+}
+template <class T>
+void pcg_rz(size_t n, const T *r, const T *z, T *p, int first, KrylovScal *sc, const RedWs &ws,
+            cudaStream_t st) {
+  k_pcg_rz<T><<<vblocks(n, ws.max_blocks), VEC_THREADS, 0, st>>>(n, r, z, p, first, sc, ws);
+}
+template <class T>
 void invert(size_t n, const T *diag, T *inv, cudaStream_t st) {
   k_invert<T><<<vblocks(n, 1 << 16), VEC_THREADS, 0, st>>>(n, diag, inv);
 }
@@ -319,6 +395,12 @@ void project(size_t n, const uint8_t *dofm, const double *dlo, double *d, cudaSt
                              KrylovScal *, const RedWs &, cudaStream_t);                     \
   template void cg_dir<T>(size_t, const T *, T *, const KrylovScal *, cudaStream_t);         \
   template void invert<T>(size_t, const T *, T *, cudaStream_t);                             \
+  template void pcg_init<T>(size_t, const T *, T *, T *, KrylovScal *, const RedWs &,         \
+                            cudaStream_t);                                                    \
+  template void pcg_update<T>(size_t, T *, T *, const T *, const T *, KrylovScal *,           \
+                              const RedWs &, cudaStream_t);                                   \
+  template void pcg_rz<T>(size_t, const T *, const T *, T *, int, KrylovScal *, const RedWs &, \
+                          cudaStream_t);                                                      \
   template void coef<T>(size_t, double, const double *, T *, cudaStream_t);
 PF_INST(double)
 PF_INST(float)

@@ -13,6 +13,14 @@ template <class T>
 void cg_dir(size_t n, const T *z, T *p, const KrylovScal *sc, cudaStream_t st);
 template <class T>
 void invert(size_t n, const T *diag, T *inv, cudaStream_t st);
+template <class T>
+void pcg_init(size_t n, const T *b, T *x, T *r, KrylovScal *sc, const RedWs &ws, cudaStream_t st);
+template <class T>
+void pcg_update(size_t n, T *x, T *r, const T *p, const T *q, KrylovScal *sc, const RedWs &ws,
+                cudaStream_t st);
+template <class T>
+void pcg_rz(size_t n, const T *r, const T *z, T *p, int first, KrylovScal *sc, const RedWs &ws,
+            cudaStream_t st);
 void masked_comb(size_t n, int ncomp, const uint8_t *dofm, double s, const double *a, double t,
                  const double *b, double *out, cudaStream_t st);
 void add(size_t n, const double *x, double *y, cudaStream_t st);

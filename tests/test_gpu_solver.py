@@ -20,12 +20,13 @@ def _checker(spec):
     return g, m
 
 
-def _run_both(spec, scheme, tol, precision=binding.FP64, steps=None, tol_lin=1e-12):
+def _run_both(spec, scheme, tol, precision=binding.FP64, steps=None, tol_lin=1e-12,
+              precond=binding.PRECOND_JACOBI):
     g, m = _checker(spec)
     incs = spec.increments if steps is None else spec.increments[:steps]
     st = stg.State(g)
     opts = stg.Options(tol_st=tol)
-    sim = binding.Simulation(spec, precision=precision)
+    sim = binding.Simulation(spec, precision=precision, precond=precond)
     sim.set_options(tol_lin=tol_lin)
     out = []
     for du in incs:
@@ -42,15 +43,19 @@ def _d_rms(g, a, b):
     return np.sqrt(np.sum(diff ** 2 * g.elem_active[:, None]) * q1.qp_weight(g) / (g.Lx * g.Ly))
 
 
+PRECONDS = [binding.PRECOND_JACOBI, binding.PRECOND_GMG]
+
+
+@pytest.mark.parametrize("precond", PRECONDS)
 @pytest.mark.parametrize("scheme", [0, 1, 2, 3])
 @pytest.mark.parametrize("precision", [binding.FP64, binding.FP32_IR])
-def test_uniaxial_bar_closed_form(gpu, scheme, precision):
+def test_uniaxial_bar_closed_form(gpu, scheme, precision, precond):
     lam, mu, Gc, l, eta = 121.15, 80.77, 2.7e-3, 0.03, 1e-9
     M = lam + 2 * mu
     eps_c = np.sqrt(Gc / (3 * M * l))
     spec = S.uniaxial_bar(9, 12, Lx=0.5, Ly=1.0, lam=lam, mu=mu, Gc=Gc, l=l, eta=eta,
                           steps=8, u_max=2.5 * eps_c)
-    sim = binding.Simulation(spec, precision=precision)
+    sim = binding.Simulation(spec, precision=precision, precond=precond)
     sim.set_options(tol_lin=1e-12, max_stag=200)
     H = 0.0
     for du in spec.increments:
@@ -70,10 +75,11 @@ def test_uniaxial_bar_closed_form(gpu, scheme, precision):
 SMALL = dict(n=24, l=0.08, steps=6, u_max=8e-3)
 
 
+@pytest.mark.parametrize("precond", PRECONDS)
 @pytest.mark.parametrize("scheme", [0, 1, 2, 3])
-def test_tensile_path_fp64_matches_checker(gpu, scheme):
+def test_tensile_path_fp64_matches_checker(gpu, scheme, precond):
     spec = S.tensile(SMALL["n"], l=SMALL["l"], steps=SMALL["steps"], u_max=SMALL["u_max"])
-    g, m, out = _run_both(spec, scheme, tol=1e-8)
+    g, m, out = _run_both(spec, scheme, tol=1e-8, precond=precond)
     peak = max(abs(o[0].reaction) for o in out)
     cracked = False
     for r_ref, r, st_ref, (u, d, H) in out:
@@ -88,10 +94,12 @@ def test_tensile_path_fp64_matches_checker(gpu, scheme):
     assert cracked, "the small path must reach the crack"
 
 
+@pytest.mark.parametrize("precond", PRECONDS)
 @pytest.mark.parametrize("scheme", [0, 1, 3])
-def test_tensile_path_fp32_refined(gpu, scheme):
+def test_tensile_path_fp32_refined(gpu, scheme, precond):
     spec = S.tensile(SMALL["n"], l=SMALL["l"], steps=SMALL["steps"], u_max=SMALL["u_max"])
-    g, m, out = _run_both(spec, scheme, tol=1e-6, precision=binding.FP32_IR, tol_lin=1e-10)
+    g, m, out = _run_both(spec, scheme, tol=1e-6, precision=binding.FP32_IR, tol_lin=1e-10,
+                          precond=precond)
     Fr = np.array([o[0].reaction for o in out])
     Fg = np.array([o[1]["reaction"] for o in out])
     assert abs(Fg.max() - Fr.max()) <= 1e-4 * Fr.max()
