@@ -6,10 +6,11 @@ after it; FP32-CG with FP64 refinement: peak force within 1e-4 relative and RMS 
 difference within 1e-3 (the per-result tolerances of the mixed-precision form).  The
 checker runs the same specimen, increments, scheme and tolerances.
 
-Inside a fully broken band (g(d) ~ eta = 1e-9) the displacement, hence Psi+ and H, is
-determined only up to the linear-solver tolerance divided by eta, so single nodes next
-to the band may take different values of d in the two codes while the force and the
-field in L2 agree; the pointwise 1e-6 check is therefore applied before cracking.
+The notched square is mirror-symmetric about the slit row (y -> Ly - y with
+u_y -> ubar - u_y), so when the crack leaves the slit tip it may grow into the upper or
+the lower half: both branches solve the discrete equations, with the same reaction
+force.  Rounding decides the branch, so fields are compared with the checker's state or
+its mirror image, whichever is closer; the force is compared directly.
 """
 import numpy as np
 import pytest
@@ -44,9 +45,42 @@ def _run_both(spec, scheme, tol, precision=binding.FP64, steps=None, tol_lin=1e-
     return g, m, out
 
 
-def _d_rms(g, a, b):
+def _mirror_nodes(g, f):
+    return f.reshape(g.ny + 1, g.nx + 1)[::-1].ravel()
+
+
+def _mirror_H(g, H):
+    Hm = H.reshape(g.ny, g.nx, 4)[::-1]
+    return Hm[:, :, [2, 3, 0, 1]].reshape(-1, 4)
+
+
+def _d_rms1(g, a, b):
     diff = q1.interp_qp(g, a - b)
     return np.sqrt(np.sum(diff ** 2 * g.elem_active[:, None]) * q1.qp_weight(g) / (g.Lx * g.Ly))
+
+
+def _d_rms(g, a, b):
+    """RMS difference of d against the reference or, for symmetric specimens, its mirror."""
+    best = _d_rms1(g, a, b)
+    if _symmetric(g):
+        best = min(best, _d_rms1(g, a, _mirror_nodes(g, b)))
+    return best
+
+
+def _symmetric(g):
+    f = g.node_flags.reshape(g.ny + 1, g.nx + 1)
+    return bool(np.array_equal(f[::-1] & 16, f & 16)) and g.ny % 2 == 0 and np.all(g.elem_active)
+
+
+def _max_diff(g, d, H, st_ref):
+    """Pointwise max differences of (d, H) against the reference or its mirror image."""
+    out = (np.max(np.abs(d - st_ref.d)), np.max(np.abs(H - st_ref.H)))
+    if _symmetric(g):
+        mir = (np.max(np.abs(d - _mirror_nodes(g, st_ref.d))),
+               np.max(np.abs(H - _mirror_H(g, st_ref.H))))
+        if mir[0] < out[0]:
+            out = mir
+    return out
 
 
 PRECONDS = [binding.PRECOND_JACOBI, binding.PRECOND_GMG]
@@ -91,10 +125,9 @@ def test_tensile_path_fp64_matches_checker(gpu, scheme, precond):
     for r_ref, r, st_ref, (u, d, H) in out:
         assert r["converged"] == 1 and r_ref.converged
         assert abs(r["reaction"] - r_ref.reaction) <= 1e-6 * peak
-        assert _d_rms(g, d, st_ref.d) <= 1e-3
-        if not cracked:
-            assert np.max(np.abs(d - st_ref.d)) < 1e-6
-            assert np.max(np.abs(H - st_ref.H)) <= 1e-6 * max(1.0, np.max(st_ref.H))
+        dd, dH = _max_diff(g, d, H, st_ref)
+        assert dd < 1e-6
+        assert dH <= 1e-6 * max(1.0, np.max(st_ref.H))
         # the pass count of a slowly contracting iteration is not a unique result; the
         # converged state is (checked above)
         assert abs(r["stag_iters"] - r_ref.stag_iters) <= max(1, 0.1 * r_ref.stag_iters)
@@ -124,7 +157,7 @@ def test_config0_prefix_fp64(gpu):
     peak = max(abs(o[0].reaction) for o in out)
     for r_ref, r, st_ref, (u, d, H) in out:
         assert abs(r["reaction"] - r_ref.reaction) <= 1e-6 * peak
-        assert _d_rms(g, d, st_ref.d) <= 1e-3
+        assert _max_diff(g, d, H, st_ref)[0] < 1e-5
 
 
 def test_shear_and_masked_plane_stress(gpu):
