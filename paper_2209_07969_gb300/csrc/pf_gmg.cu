@@ -286,6 +286,28 @@ __global__ void k_fm_coarse(int nxf, int nyf, const uint8_t *__restrict__ fmf, i
   }
 }
 
+// (A x)_n for one node: vectors are zero on non-free DOFs at every level, so the
+// neighbours' masks are not needed; out-of-grid neighbours have no stencil entry.
+template <class T, int B>
+__device__ __forceinline__ void sten_row(int nx, int ny, size_t nn, const T *__restrict__ S,
+                                         const T *__restrict__ x, size_t n, T (&acc)[B]) {
+  const int i = (int)(n % (nx + 1)), j = (int)(n / (nx + 1));
+#pragma unroll
+  for (int r = 0; r < B; ++r) acc[r] = T(0);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int ii = i + k % 3 - 1, jj = j + k / 3 - 1;
+    if (ii < 0 || ii > nx || jj < 0 || jj > ny) continue;
+    const size_t m = (size_t)jj * (nx + 1) + ii;
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      const T xv = x[B * m + c];
+#pragma unroll
+      for (int r = 0; r < B; ++r) acc[r] += S[sidx<B>(k, r, c, n, nn)] * xv;
+    }
+  }
+}
+
 // y = A x  (mode 0) or y = b - A x (mode 1), rows of non-free DOFs zero.
 template <class T, int B>
 __global__ void k_sten_apply(int nx, int ny, const T *__restrict__ S,
@@ -294,25 +316,192 @@ __global__ void k_sten_apply(int nx, int ny, const T *__restrict__ S,
   const size_t nn = (size_t)(nx + 1) * (ny + 1);
   for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
        n += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(n % (nx + 1)), j = (int)(n / (nx + 1));
-    const uint8_t f = fm[n];
     T acc[B];
-    for (int r = 0; r < B; ++r) acc[r] = T(0);
-    for (int k = 0; k < 9; ++k) {
-      const int ii = i + k % 3 - 1, jj = j + k / 3 - 1;
-      if (ii < 0 || ii > nx || jj < 0 || jj > ny) continue;
-      const size_t m = (size_t)jj * (nx + 1) + ii;
-      const uint8_t fn = fm[m];
-      for (int c = 0; c < B; ++c) {
-        if (!((fn >> c) & 1)) continue;
-        const T xv = x[B * m + c];
-        for (int r = 0; r < B; ++r) acc[r] += S[sidx<B>(k, r, c, n, nn)] * xv;
-      }
-    }
+    sten_row<T, B>(nx, ny, nn, S, x, n, acc);
+    const uint8_t f = fm[n];
+#pragma unroll
     for (int r = 0; r < B; ++r) {
       T v = mode ? b[B * n + r] - acc[r] : acc[r];
       y[B * n + r] = ((f >> r) & 1) ? v : T(0);
     }
+  }
+}
+
+// Fused Chebyshev step on a stencil level: y = A d_in; r -= y; d_out = c1 d_in +
+// c2/(0.45 lmax) D^-1 r; x += d_out.  d is double-buffered (neighbours read d_in).
+template <class T, int B>
+__global__ void k_sten_cheb(int nx, int ny, const T *__restrict__ S, const T *__restrict__ invd,
+                            const double *lmax, double c1, double c2, const T *__restrict__ din,
+                            T *__restrict__ dout, T *__restrict__ x, T *__restrict__ r) {
+  const size_t nn = (size_t)(nx + 1) * (ny + 1);
+  const T a = (T)c1, bb = (T)(c2 / (0.45 * *lmax));
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
+       n += (size_t)gridDim.x * blockDim.x) {
+    T acc[B];
+    sten_row<T, B>(nx, ny, nn, S, din, n, acc);
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      const size_t i = B * n + c;
+      const T ri = r[i] - acc[c];
+      const T di = a * din[i] + bb * invd[i] * ri;
+      r[i] = ri;
+      dout[i] = di;
+      x[i] += di;
+    }
+  }
+}
+
+// ---- coarse levels in one CTA ------------------------------------------------------------
+template <class T>
+struct CoarseLevel {
+  int nx, ny;
+  const T *S, *invd;
+  T *x, *b, *r, *d, *y;
+  const uint8_t *fm;
+  const double *lmax;
+};
+template <class T>
+struct CoarseArgs {
+  int nlev;                 // number of levels handled (the last one is solved densely)
+  CoarseLevel<T> L[GMG_MAX_LEVELS];
+  const T *b0;              // right-hand side of the first handled level
+  T *x0;                    // solution of the first handled level
+  const T *cinv;
+  int ncoarse;
+};
+
+template <class T, int B>
+__device__ void cta_apply(const CoarseLevel<T> &L, const T *x, const T *b, T *y, int mode) {
+  const size_t nn = (size_t)(L.nx + 1) * (L.ny + 1);
+  for (size_t n = threadIdx.x; n < nn; n += blockDim.x) {
+    T acc[B];
+    sten_row<T, B>(L.nx, L.ny, nn, L.S, x, n, acc);
+    const uint8_t f = L.fm[n];
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+      T v = mode ? b[B * n + r] - acc[r] : acc[r];
+      y[B * n + r] = ((f >> r) & 1) ? v : T(0);
+    }
+  }
+}
+
+// One V-cycle over levels [0, nlev) of `a` inside a single CTA (blockDim 1024).
+template <class T, int B>
+__global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> a) {
+  const double rho0 = 9.0 / 11.0, rho1 = 99.0 / 161.0;
+  const int last = a.nlev - 1;
+  for (int l = 0; l < last; ++l) {
+    const CoarseLevel<T> &L = a.L[l];
+    const T *b = l == 0 ? a.b0 : L.b;
+    T *x = l == 0 ? a.x0 : L.x;
+    const size_t n = (size_t)B * (L.nx + 1) * (L.ny + 1);
+    const T it = (T)(1.0 / (0.55 * *L.lmax));
+    const T c2 = (T)(2.0 * rho1 / (0.45 * *L.lmax)), c1 = (T)(rho1 * rho0);
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const T di = L.invd[i] * b[i] * it;
+      L.d[i] = di;
+      x[i] = di;
+      L.r[i] = b[i];
+    }
+    __syncthreads();
+    cta_apply<T, B>(L, L.d, nullptr, L.y, 0);
+    __syncthreads();
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const T ri = L.r[i] - L.y[i];
+      const T di = c1 * L.d[i] + c2 * L.invd[i] * ri;
+      L.r[i] = ri;
+      L.d[i] = di;
+      x[i] += di;
+    }
+    __syncthreads();
+    cta_apply<T, B>(L, x, b, L.r, 1);
+    __syncthreads();
+    // restrict r -> b of level l+1
+    const CoarseLevel<T> &C = a.L[l + 1];
+    const size_t nnc = (size_t)(C.nx + 1) * (C.ny + 1);
+    for (size_t I = threadIdx.x; I < nnc; I += blockDim.x) {
+      const int Ix = (int)(I % (C.nx + 1)), Iy = (int)(I / (C.nx + 1));
+      T acc[B];
+#pragma unroll
+      for (int c = 0; c < B; ++c) acc[c] = T(0);
+      for (int p = -1; p <= 1; ++p)
+        for (int q = -1; q <= 1; ++q) {
+          const int ix = 2 * Ix + p, iy = 2 * Iy + q;
+          if (ix < 0 || ix > L.nx || iy < 0 || iy > L.ny) continue;
+          const T wi = T((p == 0 ? 1.0 : 0.5) * (q == 0 ? 1.0 : 0.5));
+          const size_t fi = (size_t)iy * (L.nx + 1) + ix;
+#pragma unroll
+          for (int c = 0; c < B; ++c) acc[c] += wi * L.r[B * fi + c];
+        }
+      const uint8_t mc = C.fm[I];
+#pragma unroll
+      for (int c = 0; c < B; ++c) C.b[B * I + c] = ((mc >> c) & 1) ? acc[c] : T(0);
+    }
+    __syncthreads();
+  }
+  // dense solve on the last level: one warp per row
+  {
+    const CoarseLevel<T> &C = a.L[last];
+    const T *b = last == 0 ? a.b0 : C.b;
+    T *x = last == 0 ? a.x0 : C.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < a.ncoarse; i += nw) {
+      double s = 0.0;
+      for (int j = lane; j < a.ncoarse; j += 32) s += (double)a.cinv[(size_t)i * a.ncoarse + j] * (double)b[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) x[i] = (T)s;
+    }
+    __syncthreads();
+  }
+  for (int l = last - 1; l >= 0; --l) {
+    const CoarseLevel<T> &L = a.L[l];
+    const CoarseLevel<T> &C = a.L[l + 1];
+    const T *b = l == 0 ? a.b0 : L.b;
+    T *x = l == 0 ? a.x0 : L.x;
+    const T *xc = (l + 1 == last && last == 0) ? a.x0 : C.x;
+    const size_t nnf = (size_t)(L.nx + 1) * (L.ny + 1);
+    for (size_t nf = threadIdx.x; nf < nnf; nf += blockDim.x) {
+      const uint8_t m = L.fm[nf];
+      if (!m) continue;
+      const int ix = (int)(nf % (L.nx + 1)), iy = (int)(nf / (L.nx + 1));
+      const int px0 = ix >> 1, py0 = iy >> 1, npx = (ix & 1) ? 2 : 1, npy = (iy & 1) ? 2 : 1;
+      T acc[B];
+#pragma unroll
+      for (int c = 0; c < B; ++c) acc[c] = T(0);
+      for (int u = 0; u < npx; ++u)
+        for (int v = 0; v < npy; ++v) {
+          const T wj = T((npx == 2 ? 0.5 : 1.0) * (npy == 2 ? 0.5 : 1.0));
+          const size_t J = (size_t)(py0 + v) * (C.nx + 1) + (px0 + u);
+#pragma unroll
+          for (int c = 0; c < B; ++c) acc[c] += wj * xc[B * J + c];
+        }
+#pragma unroll
+      for (int c = 0; c < B; ++c)
+        if ((m >> c) & 1) x[B * nf + c] += acc[c];
+    }
+    __syncthreads();
+    const size_t n = (size_t)B * nnf;
+    const T it = (T)(1.0 / (0.55 * *L.lmax));
+    const T c2 = (T)(2.0 * rho1 / (0.45 * *L.lmax)), c1 = (T)(rho1 * rho0);
+    cta_apply<T, B>(L, x, b, L.r, 1);
+    __syncthreads();
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const T di = L.invd[i] * L.r[i] * it;
+      L.d[i] = di;
+      x[i] += di;
+    }
+    __syncthreads();
+    cta_apply<T, B>(L, L.d, nullptr, L.y, 0);
+    __syncthreads();
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const T ri = L.r[i] - L.y[i];
+      const T di = c1 * L.d[i] + c2 * L.invd[i] * ri;
+      L.r[i] = ri;
+      L.d[i] = di;
+      x[i] += di;
+    }
+    __syncthreads();
   }
 }
 
@@ -489,6 +678,7 @@ cudaError_t gmg_alloc(Gmg<T> &G, int nx, int ny, int B, const RedWs &ws) {
     if ((e = cudaMalloc(&L.r, nb * sizeof(T))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&L.dv, nb * sizeof(T))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&L.y, nb * sizeof(T))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&L.dv2, nb * sizeof(T))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&L.fm, L.nn)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&L.lmax, sizeof(double))) != cudaSuccess) return e;
     ++l;
@@ -497,6 +687,12 @@ cudaError_t gmg_alloc(Gmg<T> &G, int nx, int ny, int B, const RedWs &ws) {
     cy = (cy + 1) / 2;
   }
   G.nl = l;
+  G.lc = G.nl - 1;
+  for (int k = 0; k < G.nl; ++k)
+    if (G.lv[k].nn <= (size_t)GMG_CTA_NODES) {
+      G.lc = k;
+      break;
+    }
   const GmgLevel<T> &C = G.lv[l - 1];
   G.ncoarse = (int)(B * C.nn);
   cudaError_t e = cudaMalloc(&G.cinv, (size_t)G.ncoarse * G.ncoarse * sizeof(T));
@@ -511,7 +707,7 @@ template <class T>
 void gmg_free(Gmg<T> &G) {
   for (int l = 0; l < G.nl; ++l) {
     GmgLevel<T> &L = G.lv[l];
-    void *p[] = {L.S, L.invd, L.x, L.b, L.r, L.dv, L.y, L.fm, L.lmax};
+    void *p[] = {L.S, L.invd, L.x, L.b, L.r, L.dv, L.dv2, L.y, L.fm, L.lmax};
     for (void *q : p)
       if (q) cudaFree(q);
     L = GmgLevel<T>();
@@ -540,7 +736,7 @@ static cudaError_t gmg_setup_common(Gmg<T> &G, const GridD &g, cudaStream_t st) 
       k_fm_coarse<B><<<nblk(L.nn), 256, 0, st>>>(F.nx, F.ny, F.fm, L.nx, L.ny, L.fm);
     }
     k_diag_bound<T, B><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.fm, L.invd);
-    k_bound<T, B><<<nblk(L.nn, G.ws.max_blocks), 256, 0, st>>>(L.nx, L.ny, L.S, L.fm, G.ws, L.lmax);
+    k_bound<T, B><<<nblk(L.nn, red_blocks()), 256, 0, st>>>(L.nx, L.ny, L.S, L.fm, G.ws, L.lmax);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -665,6 +861,34 @@ template <class T>
 void gmg_dense(const Gmg<T> &G, const T *b, T *x, cudaStream_t st) {
   k_dense<T><<<1, 256, 0, st>>>(G.ncoarse, G.cinv, b, x);
 }
+template <class T>
+void gmg_sten_cheb(const Gmg<T> &G, int l, const T *din, T *dout, T *x, T *r, cudaStream_t st) {
+  const double rho0 = 9.0 / 11.0, rho1 = 99.0 / 161.0;
+  const GmgLevel<T> &L = G.lv[l];
+  if (G.B == 2)
+    k_sten_cheb<T, 2><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.lmax, rho1 * rho0,
+                                                  2.0 * rho1, din, dout, x, r);
+  else
+    k_sten_cheb<T, 1><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.lmax, rho1 * rho0,
+                                                  2.0 * rho1, din, dout, x, r);
+}
+template <class T>
+void gmg_coarse_cycle(const Gmg<T> &G, int lc, const T *b0, T *x0, cudaStream_t st) {
+  CoarseArgs<T> a;
+  a.nlev = G.nl - lc;
+  for (int l = lc; l < G.nl; ++l) {
+    const GmgLevel<T> &L = G.lv[l];
+    a.L[l - lc] = CoarseLevel<T>{L.nx, L.ny, L.S, L.invd, L.x, L.b, L.r, L.dv, L.y, L.fm, L.lmax};
+  }
+  a.b0 = b0;
+  a.x0 = x0;
+  a.cinv = G.cinv;
+  a.ncoarse = G.ncoarse;
+  if (G.B == 2)
+    k_coarse_cycle<T, 2><<<1, 1024, 0, st>>>(a);
+  else
+    k_coarse_cycle<T, 1><<<1, 1024, 0, st>>>(a);
+}
 
 #define GMG_INST(T)                                                                            \
   template cudaError_t gmg_alloc<T>(Gmg<T> &, int, int, int, const RedWs &);                   \
@@ -682,7 +906,9 @@ void gmg_dense(const Gmg<T> &G, const T *b, T *x, cudaStream_t st) {
   template void gmg_sub<T>(size_t, const T *, const T *, T *, cudaStream_t);                    \
   template void gmg_restrict<T>(const Gmg<T> &, int, const T *, T *, cudaStream_t);             \
   template void gmg_prolong_add<T>(const Gmg<T> &, int, const T *, T *, cudaStream_t);          \
-  template void gmg_dense<T>(const Gmg<T> &, const T *, T *, cudaStream_t);
+  template void gmg_dense<T>(const Gmg<T> &, const T *, T *, cudaStream_t);                     \
+  template void gmg_sten_cheb<T>(const Gmg<T> &, int, const T *, T *, T *, T *, cudaStream_t);  \
+  template void gmg_coarse_cycle<T>(const Gmg<T> &, int, const T *, T *, cudaStream_t);
 GMG_INST(double)
 GMG_INST(float)
 

@@ -18,6 +18,7 @@ namespace pf {
 constexpr int GMG_MAX_LEVELS = 16;
 constexpr int GMG_COARSE_MAX = 8;   // coarsen while max(nx, ny) > this
 constexpr int CHEB_DEGREE = 2;
+constexpr int GMG_CTA_NODES = 4500;  // levels with at most this many nodes run in one CTA
 
 template <class T>
 struct GmgLevel {
@@ -25,7 +26,7 @@ struct GmgLevel {
   size_t nn = 0;
   T *S = nullptr;       // 9*B*B*nn stencil (SoA: entry-major), levels >= 0
   T *invd = nullptr;    // B*nn inverse diagonal (0 on constrained / empty DOFs)
-  T *x = nullptr, *b = nullptr, *r = nullptr, *dv = nullptr, *y = nullptr;  // B*nn work
+  T *x = nullptr, *b = nullptr, *r = nullptr, *dv = nullptr, *dv2 = nullptr, *y = nullptr;
   uint8_t *fm = nullptr;   // nn bytes, bit c: component c free on this level
   double *lmax = nullptr;  // device scalar
 };
@@ -34,6 +35,7 @@ template <class T>
 struct Gmg {
   int B = 1;
   int nl = 0;
+  int lc = 0;               // first level handled by the single-CTA coarse cycle
   GmgLevel<T> lv[GMG_MAX_LEVELS];
   int ncoarse = 0;          // DOFs of the coarsest level
   T *cinv = nullptr;        // ncoarse^2 dense inverse
@@ -78,54 +80,61 @@ template <class T>
 void gmg_prolong_add(const Gmg<T> &G, int l, const T *xc, T *xf, cudaStream_t st);
 template <class T>
 void gmg_dense(const Gmg<T> &G, const T *b, T *x, cudaStream_t st);
+template <class T>
+void gmg_sten_cheb(const Gmg<T> &G, int l, const T *din, T *dout, T *x, T *r, cudaStream_t st);
+template <class T>
+void gmg_coarse_cycle(const Gmg<T> &G, int lc, const T *b0, T *x0, cudaStream_t st);
 
 // z = V(r): one V-cycle (Chebyshev degree 2 pre and post) on the fine residual r.
-// fine_apply(x, y) must compute y = A_0 x with constrained rows/columns zeroed.
-// Returns the number of kernel launches issued.
+// fine_apply(x, y) must compute y = A_0 x with constrained rows/columns zeroed.  Levels
+// below G.lc run as separate grid-wide kernels; levels from G.lc down to the dense
+// solve run in one single-CTA kernel.  Returns the number of kernel launches issued.
 template <class T, class FineApply>
 int gmg_vcycle(Gmg<T> &G, FineApply fine_apply, const T *r, T *z, cudaStream_t st) {
   int launches = 0;
-  auto apply = [&](int l, const T *x, T *y) {
-    if (l == 0) fine_apply(x, y);
-    else gmg_sten_apply<T>(G, l, x, nullptr, y, 0, st);
-    ++launches;
-  };
-  const int last = G.nl - 1;
-  for (int l = 0; l < last; ++l) {
+  const int lc = G.lc;
+  for (int l = 0; l < lc; ++l) {
     GmgLevel<T> &L = G.lv[l];
     const T *b = (l == 0) ? r : L.b;
     T *x = (l == 0) ? z : L.x;
     gmg_cheb_first<T>(G, l, b, x, L.dv, L.r, st);
-    apply(l, L.dv, L.y);
-    gmg_cheb_step<T>(G, l, L.y, x, L.dv, L.r, st);
     if (l == 0) {
-      apply(0, x, L.y);
+      fine_apply(L.dv, L.y);
+      gmg_cheb_step<T>(G, 0, L.y, x, L.dv, L.r, st);
+      fine_apply(x, L.y);
       gmg_sub<T>((size_t)G.B * L.nn, b, L.y, L.r, st);
-      ++launches;
+      launches += 5;
     } else {
+      gmg_sten_cheb<T>(G, l, L.dv, L.dv2, x, L.r, st);
       gmg_sten_apply<T>(G, l, x, b, L.r, 1, st);
-      ++launches;
+      launches += 3;
     }
     gmg_restrict<T>(G, l, L.r, G.lv[l + 1].b, st);
-    launches += 3;
-  }
-  {
-    GmgLevel<T> &C = G.lv[last];
-    T *xc = (last == 0) ? z : C.x;
-    const T *bc = (last == 0) ? r : C.b;
-    gmg_dense<T>(G, bc, xc, st);
     ++launches;
   }
-  for (int l = last - 1; l >= 0; --l) {
+  {
+    const T *b0 = lc == 0 ? r : G.lv[lc].b;
+    T *x0 = lc == 0 ? z : G.lv[lc].x;
+    gmg_coarse_cycle<T>(G, lc, b0, x0, st);
+    ++launches;
+  }
+  for (int l = lc - 1; l >= 0; --l) {
     GmgLevel<T> &L = G.lv[l];
     const T *b = (l == 0) ? r : L.b;
     T *x = (l == 0) ? z : L.x;
     gmg_prolong_add<T>(G, l, G.lv[l + 1].x, x, st);
-    apply(l, x, L.y);
-    gmg_cheb_first_x<T>(G, l, b, L.y, x, L.dv, L.r, st);
-    apply(l, L.dv, L.y);
-    gmg_cheb_step<T>(G, l, L.y, x, L.dv, L.r, st);
-    launches += 3;
+    if (l == 0) {
+      fine_apply(x, L.y);
+      gmg_cheb_first_x<T>(G, 0, b, L.y, x, L.dv, L.r, st);
+      fine_apply(L.dv, L.y);
+      gmg_cheb_step<T>(G, 0, L.y, x, L.dv, L.r, st);
+      launches += 5;
+    } else {
+      gmg_sten_apply<T>(G, l, x, nullptr, L.y, 0, st);
+      gmg_cheb_first_x<T>(G, l, b, L.y, x, L.dv, L.r, st);
+      gmg_sten_cheb<T>(G, l, L.dv, L.dv2, x, L.r, st);
+      launches += 4;
+    }
   }
   return launches;
 }

@@ -48,6 +48,10 @@ struct RedWs {
   int max_blocks;
 };
 
+// CTAs of a grid-wide reduction: two per SM of the current device (set once per
+// process from the device attributes).
+int red_blocks();
+
 inline unsigned tile_blocks_x(int nx) { return (unsigned)((nx + 1 + TX - 1) / TX); }
 inline unsigned tile_blocks_y(int ny) { return (unsigned)((ny + 1 + TY - 1) / TY); }
 

@@ -122,7 +122,10 @@ k_elas(GridD g, MatD mt, const T *__restrict__ d, const uint8_t *__restrict__ te
   __shared__ T sd[PY * PX];
   __shared__ T ef[8][NE];
   const int nx = g.nx, ny = g.ny, ld = nx + 1;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int tbx = (nx + 1 + TX - 1) / TX, ntiles = tbx * ((ny + 1 + TY - 1) / TY);
+  double dot = 0.0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  const int i0 = (tile % tbx) * TX, j0 = (tile / tbx) * TY;
 
   for (int t = threadIdx.x; t < PX * PY; t += TILE_THREADS) {
     const int li = t % PX, lj = t / PX;
@@ -229,7 +232,6 @@ k_elas(GridD g, MatD mt, const T *__restrict__ d, const uint8_t *__restrict__ te
 
   const int li = threadIdx.x % TX, lj = threadIdx.x / TX;
   const int gi = i0 + li, gj = j0 + lj;
-  double dot = 0.0;
   if (gi <= nx && gj <= ny) {
     const int e00 = lj * EX + li, e10 = e00 + 1, e01 = e00 + EX, e11 = e01 + 1;
     T fx = ef[6][e00] + ef[4][e10] + ef[2][e01] + ef[0][e11];
@@ -244,9 +246,11 @@ k_elas(GridD g, MatD mt, const T *__restrict__ d, const uint8_t *__restrict__ te
     y[2 * n + 1] = fy;
     if (MODE == EL_APPLY && epi != EPI_NONE) {
       const int p = (lj + 1) * PX + li + 1;
-      dot = (double)sx[0][p] * (double)fx + (double)sx[1][p] * (double)fy;
+      dot += (double)sx[0][p] * (double)fx + (double)sx[1][p] * (double)fy;
     }
   }
+  __syncthreads();
+  }  // tiles
   if (MODE == EL_APPLY && epi != EPI_NONE) {
     double v[1] = {dot}, tot[1];
     if (grid_reduce<1>(v, ws, tot)) krylov_epilogue(epi, sc, tot[0]);
@@ -266,7 +270,10 @@ k_damage(GridD g, const C *__restrict__ c, double kappa_d, const T *__restrict__
   __shared__ T sxv[PY * PX];
   __shared__ T ef[4][NE];
   const int nx = g.nx, ny = g.ny, ld = nx + 1;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int tbx = (nx + 1 + TX - 1) / TX, ntiles = tbx * ((ny + 1 + TY - 1) / TY);
+  double dot = 0.0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  const int i0 = (tile % tbx) * TX, j0 = (tile / tbx) * TY;
   if (MODE == DM_APPLY) {
     for (int t = threadIdx.x; t < PX * PY; t += TILE_THREADS) {
       const int li = t % PX, lj = t / PX;
@@ -334,15 +341,16 @@ k_damage(GridD g, const C *__restrict__ c, double kappa_d, const T *__restrict__
   __syncthreads();
   const int li = threadIdx.x % TX, lj = threadIdx.x / TX;
   const int gi = i0 + li, gj = j0 + lj;
-  double dot = 0.0;
   if (gi <= nx && gj <= ny) {
     const int e00 = lj * EX + li, e10 = e00 + 1, e01 = e00 + EX, e11 = e01 + 1;
     T v = ef[3][e00] + ef[2][e10] + ef[1][e01] + ef[0][e11];
     const size_t n = (size_t)gj * ld + gi;
     if (MODE != DM_RHS && g.dofm && (ldg(g.dofm + n) & 4)) v = T(0);
     y[n] = v;
-    if (MODE == DM_APPLY && epi != EPI_NONE) dot = (double)sxv[(lj + 1) * PX + li + 1] * (double)v;
+    if (MODE == DM_APPLY && epi != EPI_NONE) dot += (double)sxv[(lj + 1) * PX + li + 1] * (double)v;
   }
+  __syncthreads();
+  }  // tiles
   if (MODE == DM_APPLY && epi != EPI_NONE) {
     double vv[1] = {dot}, tot[1];
     if (grid_reduce<1>(vv, ws, tot)) krylov_epilogue(epi, sc, tot[0]);
@@ -557,7 +565,14 @@ __global__ void k_dof_mask(int nx, int ny, const uint8_t *__restrict__ flags,
 // ------------------------------------------------------------------------------------
 // Host launch wrappers.
 // ------------------------------------------------------------------------------------
-static inline dim3 tile_grid(const GridD &g) { return dim3(tile_blocks_x(g.nx), tile_blocks_y(g.ny)); }
+static inline unsigned tile_count(const GridD &g) { return tile_blocks_x(g.nx) * tile_blocks_y(g.ny); }
+static inline dim3 tile_grid(const GridD &g) { return dim3(tile_count(g)); }
+// Fused-reduction launches use at most red_blocks() CTAs (each loops over tiles): one
+// arrival atomic per CTA on a single counter is what limits the reduction tail.
+static inline dim3 tile_grid_red(const GridD &g) {
+  const unsigned t = tile_count(g), cap = (unsigned)red_blocks();
+  return dim3(t < cap ? t : cap);
+}
 static inline unsigned elem_blocks(size_t n) {
   size_t b = (n + VEC_THREADS - 1) / VEC_THREADS;
   return (unsigned)(b < 1 ? 1 : (b > 65535u * 8u ? 65535u * 8u : b));
@@ -567,8 +582,9 @@ template <class T>
 void elas_apply(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, const T *x,
                 T *y, cudaStream_t st, KrylovScal *sc, const RedWs *ws, int epi) {
   RedWs w = ws ? *ws : RedWs{nullptr, nullptr, 0};
-  k_elas<T, EL_APPLY><<<tile_grid(g), TILE_THREADS, 0, st>>>(g, m, d, tens, x, y, nullptr, sc,
-                                                             w, ws ? epi : EPI_NONE);
+  const int e = ws ? epi : EPI_NONE;
+  k_elas<T, EL_APPLY><<<e == EPI_NONE ? tile_grid(g) : tile_grid_red(g), TILE_THREADS, 0, st>>>(
+      g, m, d, tens, x, y, nullptr, sc, w, e);
 }
 template <class T>
 void elas_diag(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, T *diag,
@@ -585,8 +601,9 @@ template <class T>
 void damage_apply(const GridD &g, const T *c, double kappa, const T *x, T *y, cudaStream_t st,
                   KrylovScal *sc, const RedWs *ws, int epi) {
   RedWs w = ws ? *ws : RedWs{nullptr, nullptr, 0};
-  k_damage<T, T, DM_APPLY><<<tile_grid(g), TILE_THREADS, 0, st>>>(g, c, kappa, x, y, sc, w,
-                                                                   ws ? epi : EPI_NONE);
+  const int e = ws ? epi : EPI_NONE;
+  k_damage<T, T, DM_APPLY><<<e == EPI_NONE ? tile_grid(g) : tile_grid_red(g), TILE_THREADS, 0, st>>>(
+      g, c, kappa, x, y, sc, w, e);
 }
 template <class T>
 void damage_diag(const GridD &g, const T *c, double kappa, T *diag, cudaStream_t st) {

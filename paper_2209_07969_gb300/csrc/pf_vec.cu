@@ -314,22 +314,39 @@ __global__ void k_project(size_t n, const uint8_t *__restrict__ dofm,
 }
 
 // ---- launchers -----------------------------------------------------------------------
+int red_blocks() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 64;
+    cached = 2 * sms;
+  }
+  return cached;
+}
+
 static inline unsigned vblocks(size_t n, int cap) {
   size_t b = (n + VEC_THREADS - 1) / VEC_THREADS;
   if (b < 1) b = 1;
   if (b > (size_t)cap) b = cap;
   return (unsigned)b;
 }
+// reduction kernels: at most red_blocks() CTAs (and never more than the partial slots)
+static inline unsigned rblocks(size_t n, int max_blocks) {
+  const int cap = red_blocks() < max_blocks ? red_blocks() : max_blocks;
+  return vblocks(n, cap);
+}
 
 template <class T>
 void cg_init(size_t n, const T *b, T *x, T *r, T *z, T *p, const T *invd, KrylovScal *sc,
              const RedWs &ws, cudaStream_t st) {
-  k_cg_init<T><<<vblocks(n, ws.max_blocks), VEC_THREADS, 0, st>>>(n, b, x, r, z, p, invd, sc, ws);
+  k_cg_init<T><<<rblocks(n, ws.max_blocks), VEC_THREADS, 0, st>>>(n, b, x, r, z, p, invd, sc, ws);
 }
 template <class T>
 void cg_update(size_t n, T *x, T *r, T *z, const T *p, const T *q, const T *invd,
                KrylovScal *sc, const RedWs &ws, cudaStream_t st) {
-  k_cg_update<T><<<vblocks(n, ws.max_blocks), VEC_THREADS, 0, st>>>(n, x, r, z, p, q, invd, sc, ws);
+  k_cg_update<T><<<rblocks(n, ws.max_blocks), VEC_THREADS, 0, st>>>(n, x, r, z, p, q, invd, sc, ws);
 }
 template <class T>
 void cg_dir(size_t n, const T *z, T *p, const KrylovScal *sc, cudaStream_t st) {
@@ -337,17 +354,17 @@ void cg_dir(size_t n, const T *z, T *p, const KrylovScal *sc, cudaStream_t st) {
 }
 template <class T>
 void pcg_init(size_t n, const T *b, T *x, T *r, KrylovScal *sc, const RedWs &ws, cudaStream_t st) {
-  k_pcg_init<T><<<vblocks(n, ws.max_blocks), VEC_THREADS, 0, st>>>(n, b, x, r, sc, ws);
+  k_pcg_init<T><<<rblocks(n, ws.max_blocks), VEC_THREADS, 0, st>>>(n, b, x, r, sc, ws);
 }
 template <class T>
 void pcg_update(size_t n, T *x, T *r, const T *p, const T *q, KrylovScal *sc, const RedWs &ws,
                 cudaStream_t st) {
-  k_pcg_update<T><<<vblocks(n, ws.max_blocks), VEC_THREADS, 0, st>>>(n, x, r, p, q, sc, ws);
+  k_pcg_update<T><<<rblocks(n, ws.max_blocks), VEC_THREADS, 0, st>>>(n, x, r, p, q, sc, ws);
 }
 template <class T>
 void pcg_rz(size_t n, const T *r, const T *z, T *p, int first, KrylovScal *sc, const RedWs &ws,
             cudaStream_t st) {
-  k_pcg_rz<T><<<vblocks(n, ws.max_blocks), VEC_THREADS, 0, st>>>(n, r, z, p, first, sc, ws);
+  k_pcg_rz<T><<<rblocks(n, ws.max_blocks), VEC_THREADS, 0, st>>>(n, r, z, p, first, sc, ws);
 }
 template <class T>
 void invert(size_t n, const T *diag, T *inv, cudaStream_t st) {
@@ -374,15 +391,15 @@ void lift(size_t nn, const uint8_t *flags, const uint8_t *dofm, double ubar, dou
 }
 void norms(size_t n, int ncomp, const uint8_t *dofm, const double *v, double *out,
            const RedWs &ws, cudaStream_t st) {
-  k_norms<<<vblocks(n, ws.max_blocks), VEC_THREADS, 0, st>>>(n, ncomp, dofm, v, out, ws);
+  k_norms<<<rblocks(n, ws.max_blocks), VEC_THREADS, 0, st>>>(n, ncomp, dofm, v, out, ws);
 }
 void stag_max(size_t n, const uint8_t *dofm, const double *Kd, const double *b,
               const double *diag, double *out, const RedWs &ws, cudaStream_t st) {
-  k_stag_max<<<vblocks(n, ws.max_blocks), VEC_THREADS, 0, st>>>(n, dofm, Kd, b, diag, out, ws);
+  k_stag_max<<<rblocks(n, ws.max_blocks), VEC_THREADS, 0, st>>>(n, dofm, Kd, b, diag, out, ws);
 }
 void reaction(size_t nn, const uint8_t *flags, int dir, const double *F, double *out,
               const RedWs &ws, cudaStream_t st) {
-  k_reaction<<<vblocks(nn, ws.max_blocks), VEC_THREADS, 0, st>>>(nn, flags, dir, F, out, ws);
+  k_reaction<<<rblocks(nn, ws.max_blocks), VEC_THREADS, 0, st>>>(nn, flags, dir, F, out, ws);
 }
 void project(size_t n, const uint8_t *dofm, const double *dlo, double *d, cudaStream_t st) {
   k_project<<<vblocks(n, 1 << 16), VEC_THREADS, 0, st>>>(n, dofm, dlo, d);
