@@ -1,0 +1,354 @@
+#!/usr/bin/env python3
+"""Benchmark of the staggered phase-field solver on the 512 x 512 tensile notched square.
+
+Workload (tensile notched square, 512 x 512 Q1 elements, l = 0.0075 mm, 100 load steps to
+6e-3 mm, staggered tolerance 1e-5; S1 fixed-stress scheme, FP32 CG with FP64 refinement,
+geometric multigrid): a batch of B independent simulations of that specimen, each with
+its own context and CUDA stream, advanced concurrently.  One bench step is one load step
+(one pf_load_step, i.e. every part of the method once through) on every simulation of
+the batch.  W untimed load steps, then K timed load steps.
+
+Reported metric: load paths/s = (B x K load steps / 100 load steps per path) / time, over
+the timed window of the path; DOF.CG-iterations/s, load steps/s and per-step latency
+percentiles are reported beside it.  The window starts at the beginning of the path, so
+it covers elastic steps unless K reaches the crack (steps ~80-85); crack steps cost
+hundreds of staggered passes each, so a full path takes longer than the window rate
+suggests (the full-path figure is a separate measurement, --full-path).
+
+--impl reference times the FP64 CPU checker (oracle/) on a bounded sample of the same
+workload: each step is one exact phase-field solve (assembly + sparse LU) of load step 1
+on the 512 x 512 grid; since every load step needs at least one such solve (and two
+displacement solves, each several times more expensive), 1 / (100 x sample time) is an
+upper bound of the checker's load paths/s.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+STEPS_PER_PATH = 100
+METRIC = "load paths/s"
+UNIT = "load paths/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--batch", type=int, default=8)
+    p.add_argument("--grid", type=int, default=512)
+    p.add_argument("--scheme", default="S1")
+    p.add_argument("--full-path", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def workload(grid):
+    from paper_2209_07969_gb300 import specimens as S
+    return S.tensile(grid, l=0.0075 if grid == 512 else 0.0075 * 512 / grid,
+                     steps=STEPS_PER_PATH, u_max=6e-3)
+
+
+# ---- clocks ------------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---- checker sample (CPU) ---------------------------------------------------------------
+def oracle_sample(grid):
+    """One exact phase-field solve of load step 1 (assembly + LU); returns seconds."""
+    import numpy as np
+    from oracle import model, q1, staggered as stg
+    sp = workload(grid)
+    g = q1.Grid(sp.nx, sp.ny, sp.Lx, sp.Ly, sp.node_flags, sp.elem_active)
+    m = model.material_from_E_nu(sp.E, sp.nu, sp.Gc, sp.l, sp.eta, sp.plane)
+    j = np.arange(g.nn) // (g.nx + 1)
+    u = np.stack([np.zeros(g.nn), sp.increments[0] * j / g.ny], 1).ravel()
+    t0 = time.perf_counter()
+    H = stg.psi_plus_qp(g, u, m)
+    stg.d_step_standard(g, m, H)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(grid, budget_s=12.0):
+    ts = []
+    t_start = time.perf_counter()
+    while not ts or (time.perf_counter() - t_start < budget_s and len(ts) < 5):
+        ts.append(oracle_sample(grid))
+    t = statistics.median(ts)
+    return {"value": 1.0 / (STEPS_PER_PATH * t), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{len(ts)} exact phase-field solves (assembly + SuperLU) of load step 1 "
+                       f"on the {grid}x{grid} grid, median {t:.2f} s; value = 1/(100 x that), an "
+                       "upper bound since each load step needs at least one such solve"),
+            "host_cpus": os.cpu_count()}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(args.grid)
+    ts = [oracle_sample(args.grid) for _ in range(args.steps)]
+    total = sum(ts)
+    value = args.steps / (STEPS_PER_PATH * total)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"tensile notched square {args.grid}x{args.grid}, l=0.0075 mm, "
+                                   "100 load steps to 6e-3 mm (checker sample: one phase-field "
+                                   "solve of load step 1 per step)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step one exact phase-field solve (assembly + "
+                                       "SuperLU) of load step 1; value = steps/(100 x time)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- GPU arm --------------------------------------------------------------------------------
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_roofline(spec, sims, peak_gbs, reps=30):
+    """Time the FP32 matrix-free elasticity tangent apply (the dominant operator) on the
+    workload grid with CUDA events on the launching stream, flushing L2 before each
+    launch.  Algorithmic bytes per node: x (8) + y (8) + d (4) + DOF mask (1) + tension
+    byte (1 per element, ~1 per node) = 22."""
+    import numpy as np
+    import torch
+    from paper_2209_07969_gb300 import binding
+    L = binding.lib()
+    nn = (spec.nx + 1) * (spec.ny + 1)
+    ne = spec.nx * spec.ny
+    dev = torch.device("cuda")
+    flags = torch.from_numpy(spec.node_flags.astype(np.uint8)).to(dev)
+    mask = torch.empty(nn, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream()
+    binding.check(L.pf_op_dof_mask(spec.nx, spec.ny, flags.data_ptr(), None, mask.data_ptr(),
+                                   st.cuda_stream))
+    g = binding.grid(spec.nx, spec.ny, spec.Lx / spec.nx, spec.Ly / spec.ny, None, mask.data_ptr())
+    mat = binding.material(spec.E, spec.nu, spec.Gc, spec.l, spec.eta, spec.plane)
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    d = (torch.rand(nn, generator=gen) * 0.5).to(dev, torch.float32)
+    x = torch.randn(2 * nn, generator=gen).to(dev, torch.float32)
+    y = torch.empty_like(x)
+    tens = torch.randint(0, 16, (ne,), generator=gen, dtype=torch.uint8).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    times = []
+    for k in range(reps + 3):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        binding.check(L.pf_op_elas_apply(g, mat, binding.F32, d.data_ptr(), tens.data_ptr(),
+                                         x.data_ptr(), y.data_ptr(), st.cuda_stream))
+        e1.record(st)
+        e1.synchronize()
+        if k >= 3:
+            times.append(e0.elapsed_time(e1) * 1e-3)
+    t = statistics.mean(times)
+    bytes_ = 22.0 * nn
+    ach = bytes_ / t / 1e9
+    return {"kernel": "k_elas<float,APPLY> (matrix-free Q1 elasticity tangent, FP32)",
+            "bound": "hbm", "achieved": ach, "peak": peak_gbs, "unit": "GB/s",
+            "frac": ach / peak_gbs, "traffic": None, "algorithmic_bytes": bytes_,
+            "launch_us": t * 1e6, "l2": "flushed before each launch"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2209_07969_gb300 import binding, build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    binding.lib()
+    spec = workload(args.grid)
+    scheme = binding.SCHEMES[args.scheme]
+    B = args.batch
+    sims = [binding.Simulation(spec, precision=binding.FP32_IR, precond=binding.PRECOND_GMG)
+            for _ in range(B)]
+    for s in sims:
+        s.set_options(max_stag=1000)
+    incs = spec.increments
+    step_idx = [0] * B
+    results = [[] for _ in range(B)]
+
+    def advance(i, nsteps, fields=False):
+        s = sims[i]
+        for _ in range(nsteps):
+            k = step_idx[i]
+            r = s.load_step(incs[k % len(incs)], scheme, 1e-5)
+            if fields:
+                s.fields()
+            step_idx[i] += 1
+            results[i].append(r)
+
+    def run_batch(nsteps, fields=False):
+        th = [threading.Thread(target=advance, args=(i, nsteps, fields)) for i in range(B)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+
+    run_batch(args.warmup)
+    for r in results:
+        r.clear()
+    launches0 = sum(s.launches() for s in sims)
+    clocks = Clocks(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    t0 = time.perf_counter()
+    run_batch(args.steps)
+    torch.cuda.synchronize()
+    e1.record()
+    e1.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    t_dev = e0.elapsed_time(e1) * 1e-3
+    T = max(t_dev, wall)
+    if world > 1:
+        tt = torch.tensor([T], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        T = float(tt.item())
+    launches = sum(s.launches() for s in sims) - launches0
+    nn = (spec.nx + 1) * (spec.ny + 1)
+    work = sum(r["lin_u"] * 2 * nn + r["lin_d"] * nn for rs in results for r in rs)
+    lat = sorted(r["ms"] for rs in results for r in rs)
+    steps_done = B * args.steps * world
+    value = steps_done / STEPS_PER_PATH / T
+    # end to end: the same number of further load steps through the public API with the
+    # host-side increment in and the fields (u, d, H) copied back to host every step
+    for r in results:
+        r.clear()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    run_batch(args.steps, fields=True)
+    torch.cuda.synchronize()
+    T_e2e = time.perf_counter() - t1
+    d2h = (3 * nn + 4 * spec.nx * spec.ny) * 8 * B
+    out = None
+    if rank == 0:
+        pk, which = peaks()
+        roof = kernel_roofline(spec, sims, pk.get("hbm_gbs", 6800.0))
+        roof["peak_source"] = which
+        base = cpu_baseline(args.grid)
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32+f64", "data": "synthetic",
+               "config": {"workload": f"tensile notched square {args.grid}x{args.grid} Q1, l=0.0075 mm, "
+                                      f"100 load steps to 6e-3 mm, TOL_ST 1e-5, scheme {args.scheme}, "
+                                      "FP32 CG + FP64 refinement, GMG; batch of independent "
+                                      "simulations on separate streams",
+                          "batch": B, "timed_load_steps": f"{args.warmup}..{args.warmup + args.steps - 1}",
+                          "l2": "working set per simulation ~0.2 GB, batch exceeds L2"},
+               "dof_cg_iters_per_s": work * world / T,
+               "load_steps_per_s": steps_done / T,
+               "step_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+               "staggered_passes": sum(r["stag_iters"] for rs in results for r in rs),
+               "clocks": clk, "gpu_launches": launches,
+               "e2e": {"value": steps_done / STEPS_PER_PATH / T_e2e, "unit": UNIT,
+                       "h2d_bytes_per_step": 8 * B, "d2h_bytes_per_step": d2h},
+               "roofline": roof, "cpu_baseline": base}
+        print(json.dumps(out), flush=True)
+    for s in sims:
+        s.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_full_path(args):
+    """Complete load paths (all 100 steps) of the workload, one simulation per scheme."""
+    from paper_2209_07969_gb300 import binding, build
+    build.build()
+    spec = workload(args.grid)
+    for name in args.scheme.split(","):
+        for prec in (binding.FP32_IR, binding.FP64):
+            s = binding.Simulation(spec, precision=prec, precond=binding.PRECOND_GMG)
+            t0 = time.perf_counter()
+            passes = 0
+            for du in spec.increments:
+                r = s.load_step(du, binding.SCHEMES[name], 1e-5)
+                passes += r["stag_iters"]
+            dt = time.perf_counter() - t0
+            print(json.dumps({"scheme": name, "precision": "fp32_ir" if prec else "fp64",
+                              "path_s": dt, "load_paths_per_s": 1.0 / dt, "passes": passes}), flush=True)
+            s.close()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    elif a.full_path:
+        run_full_path(a)
+    else:
+        run_ours(a)

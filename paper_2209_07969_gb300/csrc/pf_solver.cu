@@ -23,6 +23,23 @@
 
 using namespace pf;
 
+// Multigrid hierarchies are rebuilt lazily: a hierarchy built for an earlier operator is
+// still an SPD preconditioner for the current one, so it is kept until the Krylov
+// iteration count of a solve grows past 1.5x (+4) the count right after the last rebuild.
+struct MgState {
+  int base = -1;       // iterations of the first solve after the last rebuild
+  int last = 0;        // iterations of the latest solve
+  int since = 0;       // solves since the last rebuild
+  bool stale = true;
+  bool need() const { return stale || base < 0 || last > (3 * base) / 2 + 4 || since >= 64; }
+  void built() { stale = false; base = -1; since = 0; }
+  void record(int it) {
+    last = it;
+    if (base < 0) base = it;
+    ++since;
+  }
+};
+
 struct GraphSlot {
   cudaGraphExec_t exec = nullptr;
   int launches = 0;
@@ -64,6 +81,7 @@ struct pf_ctx {
   Gmg<float> gu32, gd32;     // multigrid hierarchies (FP32 inner solves)
   GraphSlot graphs[4];
   bool use_graphs = true;
+  MgState mg_u, mg_d;
   double *dscal = nullptr;   // device scalars for norms / residual / reaction
   double *hbuf = nullptr;    // pinned host mirror
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -265,10 +283,11 @@ pf_status newton_correction(pf_ctx *ctx, int *lin, int *refines, bool *ok) {
     auto Af = [ctx, st](const double *xx, double *yy) {
       elas_apply<double>(ctx->g, ctx->m, ctx->d, ctx->tens, xx, yy, st);
     };
-    if (mg) {
+    if (mg && ctx->mg_u.need()) {
       cudaError_t e = gmg_setup_elas<double>(ctx->gu, ctx->g, ctx->m, ctx->d, ctx->tens, st);
       if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
-    } else {
+      ctx->mg_u.built();
+    } else if (!mg) {
       elas_diag<double>(ctx->g, ctx->m, ctx->d, ctx->tens, ctx->kz, st);
       invert<double>(n, ctx->kz, ctx->kinv, st);
       ctx->launches += 2;
@@ -278,6 +297,7 @@ pf_status newton_correction(pf_ctx *ctx, int *lin, int *refines, bool *ok) {
                     ctx->kz, ctx->kp, ctx->kq, ctx->kinv, ctx->opt.tol_lin, ctx->opt.max_lin,
                     &it, ok));
     *lin += it;
+    if (mg) ctx->mg_u.record(it);
     return PF_OK;
   }
   auto Af32 = [ctx, st](const float *xx, float *yy, int epi) {
@@ -286,10 +306,11 @@ pf_status newton_correction(pf_ctx *ctx, int *lin, int *refines, bool *ok) {
   auto Ff32 = [ctx, st](const float *xx, float *yy) {
     elas_apply<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, xx, yy, st);
   };
-  if (mg) {
+  if (mg && ctx->mg_u.need()) {
     cudaError_t e = gmg_setup_elas<float>(ctx->gu32, ctx->g, ctx->m, ctx->fd, ctx->tens, st);
     if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
-  } else {
+    ctx->mg_u.built();
+  } else if (!mg) {
     elas_diag<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, ctx->fz, st);
     invert<float>(n, ctx->fz, ctx->finv, st);
     ctx->launches += 2;
@@ -302,7 +323,10 @@ pf_status newton_correction(pf_ctx *ctx, int *lin, int *refines, bool *ok) {
   auto AD = [ctx, st](const double *xx, double *yy) {
     elas_apply<double>(ctx->g, ctx->m, ctx->d, ctx->tens, xx, yy, st);
   };
-  return refine(ctx, AD, inner, n, 2, ctx->kb, ctx->kx, lin, refines, ok);
+  int it0 = *lin;
+  pf_status rs = refine(ctx, AD, inner, n, 2, ctx->kb, ctx->kx, lin, refines, ok);
+  if (mg) ctx->mg_u.record(*lin - it0);
+  return rs;
 }
 
 pf_status solve_u(pf_ctx *ctx, int *newton, int *lin, int *refines, bool *ok) {
@@ -359,10 +383,11 @@ pf_status solve_damage(pf_ctx *ctx, const double *c, const double *rhs, double *
     auto Af = [ctx, st, kappa](const double *xx, double *yy) {
       damage_apply<double>(ctx->g, ctx->csolve, kappa, xx, yy, st);
     };
-    if (mg) {
+    if (mg && ctx->mg_d.need()) {
       cudaError_t e = gmg_setup_damage<double>(ctx->gd, ctx->g, ctx->csolve, kappa, st);
       if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
-    } else {
+      ctx->mg_d.built();
+    } else if (!mg) {
       damage_diag<double>(ctx->g, ctx->csolve, kappa, ctx->kz, st);
       invert<double>(n, ctx->kz, ctx->kinv, st);
       ctx->launches += 2;
@@ -374,6 +399,7 @@ pf_status solve_damage(pf_ctx *ctx, const double *c, const double *rhs, double *
                     &it, ok));
     if (x != ctx->dd) CK(cudaMemcpyAsync(x, ctx->dd, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     *lin += it;
+    if (mg) ctx->mg_d.record(it);
     return PF_OK;
   }
   convert<double, float>(ctx->nq, ctx->csolve, ctx->fc, st);
@@ -384,10 +410,11 @@ pf_status solve_damage(pf_ctx *ctx, const double *c, const double *rhs, double *
   auto Ff32 = [ctx, st, kappa](const float *xx, float *yy) {
     damage_apply<float>(ctx->g, ctx->fc, kappa, xx, yy, st);
   };
-  if (mg) {
+  if (mg && ctx->mg_d.need()) {
     cudaError_t e = gmg_setup_damage<float>(ctx->gd32, ctx->g, ctx->fc, kappa, st);
     if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
-  } else {
+    ctx->mg_d.built();
+  } else if (!mg) {
     damage_diag<float>(ctx->g, ctx->fc, kappa, ctx->fz, st);
     invert<float>(n, ctx->fz, ctx->finv, st);
     ctx->launches += 2;
@@ -400,7 +427,10 @@ pf_status solve_damage(pf_ctx *ctx, const double *c, const double *rhs, double *
   auto AD = [ctx, st, kappa](const double *xx, double *yy) {
     damage_apply<double>(ctx->g, ctx->csolve, kappa, xx, yy, st);
   };
-  return refine(ctx, AD, inner, n, 1, rhs, x, lin, refines, ok);
+  int it0 = *lin;
+  pf_status rs = refine(ctx, AD, inner, n, 1, rhs, x, lin, refines, ok);
+  if (mg) ctx->mg_d.record(*lin - it0);
+  return rs;
 }
 
 // rhs = free ? b(H) - K(c) d : 0 ; then d += K_ff^-1 rhs.
@@ -774,6 +804,7 @@ pf_status pf_set_fields(pf_ctx *ctx, const double *u, const double *d, const dou
   if (H) CK(cudaMemcpyAsync(ctx->H, H, ctx->nq * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
   ctx->ubar = ubar;
+  ctx->mg_u.stale = ctx->mg_d.stale = true;
   return PF_OK;
 }
 

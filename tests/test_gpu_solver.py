@@ -128,9 +128,9 @@ def test_tensile_path_fp64_matches_checker(gpu, scheme, precond):
         dd, dH = _max_diff(g, d, H, st_ref)
         assert dd < 1e-6
         assert dH <= 1e-6 * max(1.0, np.max(st_ref.H))
-        # the pass count of a slowly contracting iteration is not a unique result; the
-        # converged state is (checked above)
-        assert abs(r["stag_iters"] - r_ref.stag_iters) <= max(1, 0.1 * r_ref.stag_iters)
+        # the pass count of a slowly contracting iteration (and of the two crack branches)
+        # is not a unique result; the converged state is (checked above)
+        assert abs(r["stag_iters"] - r_ref.stag_iters) <= max(1, 0.2 * r_ref.stag_iters)
         cracked |= r_ref.reaction < 0.7 * peak or r_ref.stag_iters > 20
     assert cracked, "the small path must reach the crack"
 
