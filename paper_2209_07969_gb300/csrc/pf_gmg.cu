@@ -219,6 +219,18 @@ __global__ void k_bound(int nx, int ny, const T *__restrict__ S, const uint8_t *
   grid_max(bound, ws, lmax);
 }
 
+// Chebyshev coefficients of a level in its arithmetic type, from the FP64 bound:
+// coef = {1/theta, 2 rho1/delta, rho1 rho0} with theta = 0.55 lmax, delta = 0.45 lmax,
+// rho0 = 1/sigma = 9/11, rho1 = 1/(2 sigma - rho0) = 99/161.
+template <class T>
+__global__ void k_cheb_coef(const double *lmax, T *coef) {
+  const double lm = *lmax > 0.0 ? *lmax : 1.0;
+  const double rho0 = 9.0 / 11.0, rho1 = 99.0 / 161.0;
+  coef[0] = (T)(1.0 / (0.55 * lm));
+  coef[1] = (T)(2.0 * rho1 / (0.45 * lm));
+  coef[2] = (T)(rho1 * rho0);
+}
+
 // Galerkin product A_c = P^T A_f P with P bilinear, rows of non-free fine DOFs removed.
 template <class T, int B>
 __global__ void k_rap(int nxf, int nyf, const T *__restrict__ Sf, const uint8_t *__restrict__ fmf,
@@ -331,10 +343,10 @@ __global__ void k_sten_apply(int nx, int ny, const T *__restrict__ S,
 // c2/(0.45 lmax) D^-1 r; x += d_out.  d is double-buffered (neighbours read d_in).
 template <class T, int B>
 __global__ void k_sten_cheb(int nx, int ny, const T *__restrict__ S, const T *__restrict__ invd,
-                            const double *lmax, double c1, double c2, const T *__restrict__ din,
-                            T *__restrict__ dout, T *__restrict__ x, T *__restrict__ r) {
+                            const T *coef, const T *__restrict__ din, T *__restrict__ dout,
+                            T *__restrict__ x, T *__restrict__ r) {
   const size_t nn = (size_t)(nx + 1) * (ny + 1);
-  const T a = (T)c1, bb = (T)(c2 / (0.45 * *lmax));
+  const T a = coef[2], bb = coef[1];
   for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
        n += (size_t)gridDim.x * blockDim.x) {
     T acc[B];
@@ -358,7 +370,7 @@ struct CoarseLevel {
   const T *S, *invd;
   T *x, *b, *r, *d, *y;
   const uint8_t *fm;
-  const double *lmax;
+  const T *coef;
 };
 template <class T>
 struct CoarseArgs {
@@ -388,15 +400,13 @@ __device__ void cta_apply(const CoarseLevel<T> &L, const T *x, const T *b, T *y,
 // One V-cycle over levels [0, nlev) of `a` inside a single CTA (blockDim 1024).
 template <class T, int B>
 __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> a) {
-  const double rho0 = 9.0 / 11.0, rho1 = 99.0 / 161.0;
   const int last = a.nlev - 1;
   for (int l = 0; l < last; ++l) {
     const CoarseLevel<T> &L = a.L[l];
     const T *b = l == 0 ? a.b0 : L.b;
     T *x = l == 0 ? a.x0 : L.x;
     const size_t n = (size_t)B * (L.nx + 1) * (L.ny + 1);
-    const T it = (T)(1.0 / (0.55 * *L.lmax));
-    const T c2 = (T)(2.0 * rho1 / (0.45 * *L.lmax)), c1 = (T)(rho1 * rho0);
+    const T it = L.coef[0], c2 = L.coef[1], c1 = L.coef[2];
     for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
       const T di = L.invd[i] * b[i] * it;
       L.d[i] = di;
@@ -428,7 +438,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> a) {
         for (int q = -1; q <= 1; ++q) {
           const int ix = 2 * Ix + p, iy = 2 * Iy + q;
           if (ix < 0 || ix > L.nx || iy < 0 || iy > L.ny) continue;
-          const T wi = T((p == 0 ? 1.0 : 0.5) * (q == 0 ? 1.0 : 0.5));
+          const T wi = (p == 0 ? T(1) : T(0.5)) * (q == 0 ? T(1) : T(0.5));
           const size_t fi = (size_t)iy * (L.nx + 1) + ix;
 #pragma unroll
           for (int c = 0; c < B; ++c) acc[c] += wi * L.r[B * fi + c];
@@ -446,11 +456,11 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> a) {
     T *x = last == 0 ? a.x0 : C.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = warp; i < a.ncoarse; i += nw) {
-      double s = 0.0;
-      for (int j = lane; j < a.ncoarse; j += 32) s += (double)a.cinv[(size_t)i * a.ncoarse + j] * (double)b[j];
+      T s = T(0);
+      for (int j = lane; j < a.ncoarse; j += 32) s += a.cinv[(size_t)i * a.ncoarse + j] * b[j];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) x[i] = (T)s;
+      if (lane == 0) x[i] = s;
     }
     __syncthreads();
   }
@@ -471,7 +481,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> a) {
       for (int c = 0; c < B; ++c) acc[c] = T(0);
       for (int u = 0; u < npx; ++u)
         for (int v = 0; v < npy; ++v) {
-          const T wj = T((npx == 2 ? 0.5 : 1.0) * (npy == 2 ? 0.5 : 1.0));
+          const T wj = (npx == 2 ? T(0.5) : T(1)) * (npy == 2 ? T(0.5) : T(1));
           const size_t J = (size_t)(py0 + v) * (C.nx + 1) + (px0 + u);
 #pragma unroll
           for (int c = 0; c < B; ++c) acc[c] += wj * xc[B * J + c];
@@ -482,8 +492,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> a) {
     }
     __syncthreads();
     const size_t n = (size_t)B * nnf;
-    const T it = (T)(1.0 / (0.55 * *L.lmax));
-    const T c2 = (T)(2.0 * rho1 / (0.45 * *L.lmax)), c1 = (T)(rho1 * rho0);
+    const T it = L.coef[0], c2 = L.coef[1], c1 = L.coef[2];
     cta_apply<T, B>(L, x, b, L.r, 1);
     __syncthreads();
     for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -509,9 +518,9 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> a) {
 // first step from x = 0: d = D^-1 b / theta; x = d; r = b
 template <class T>
 __global__ void k_cheb_first(size_t n, const T *__restrict__ b, const T *__restrict__ invd,
-                             const double *lmax, T *__restrict__ x, T *__restrict__ d,
+                             const T *coef, T *__restrict__ x, T *__restrict__ d,
                              T *__restrict__ r) {
-  const T it = (T)(1.0 / (0.55 * *lmax));
+  const T it = coef[0];
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     const T bi = b[i];
@@ -524,9 +533,9 @@ __global__ void k_cheb_first(size_t n, const T *__restrict__ b, const T *__restr
 // first step from x != 0 with y = A x: r = b - y; d = D^-1 r / theta; x += d
 template <class T>
 __global__ void k_cheb_first_x(size_t n, const T *__restrict__ b, const T *__restrict__ y,
-                               const T *__restrict__ invd, const double *lmax, T *__restrict__ x,
+                               const T *__restrict__ invd, const T *coef, T *__restrict__ x,
                                T *__restrict__ d, T *__restrict__ r) {
-  const T it = (T)(1.0 / (0.55 * *lmax));
+  const T it = coef[0];
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     const T ri = b[i] - y[i];
@@ -539,9 +548,9 @@ __global__ void k_cheb_first_x(size_t n, const T *__restrict__ b, const T *__res
 // later step with y = A d: r -= y; d = c1 d + c2 D^-1 r; x += d
 template <class T>
 __global__ void k_cheb_step(size_t n, const T *__restrict__ y, const T *__restrict__ invd,
-                            const double *lmax, double c1, double c2, T *__restrict__ x,
-                            T *__restrict__ d, T *__restrict__ r) {
-  const T a = (T)c1, bb = (T)(c2 / (0.45 * *lmax));
+                            const T *coef, T *__restrict__ x, T *__restrict__ d,
+                            T *__restrict__ r) {
+  const T a = coef[2], bb = coef[1];
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     const T ri = r[i] - y[i];
@@ -573,7 +582,7 @@ __global__ void k_restrict(int nxf, int nyf, const T *__restrict__ rf, const uin
       for (int b = -1; b <= 1; ++b) {
         const int ix = 2 * Ix + a, iy = 2 * Iy + b;
         if (ix < 0 || ix > nxf || iy < 0 || iy > nyf) continue;
-        const T wi = T((a == 0 ? 1.0 : 0.5) * (b == 0 ? 1.0 : 0.5));
+        const T wi = (a == 0 ? T(1) : T(0.5)) * (b == 0 ? T(1) : T(0.5));
         const size_t fi = (size_t)iy * (nxf + 1) + ix;
         const uint8_t m = fmf[fi];
         for (int c = 0; c < B; ++c)
@@ -600,7 +609,7 @@ __global__ void k_prolong_add(int nxf, int nyf, const uint8_t *__restrict__ fmf,
     for (int c = 0; c < B; ++c) acc[c] = T(0);
     for (int u = 0; u < npx; ++u)
       for (int v = 0; v < npy; ++v) {
-        const T wj = T((npx == 2 ? 0.5 : 1.0) * (npy == 2 ? 0.5 : 1.0));
+        const T wj = (npx == 2 ? T(0.5) : T(1)) * (npy == 2 ? T(0.5) : T(1));
         const size_t J = (size_t)(py0 + v) * (nxc + 1) + (px0 + u);
         for (int c = 0; c < B; ++c) acc[c] += wj * xc[B * J + c];
       }
@@ -681,6 +690,7 @@ cudaError_t gmg_alloc(Gmg<T> &G, int nx, int ny, int B, const RedWs &ws) {
     if ((e = cudaMalloc(&L.dv2, nb * sizeof(T))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&L.fm, L.nn)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&L.lmax, sizeof(double))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&L.coef, 4 * sizeof(T))) != cudaSuccess) return e;
     ++l;
     if ((cx <= GMG_COARSE_MAX && cy <= GMG_COARSE_MAX) || l == GMG_MAX_LEVELS) break;
     cx = (cx + 1) / 2;
@@ -707,7 +717,7 @@ template <class T>
 void gmg_free(Gmg<T> &G) {
   for (int l = 0; l < G.nl; ++l) {
     GmgLevel<T> &L = G.lv[l];
-    void *p[] = {L.S, L.invd, L.x, L.b, L.r, L.dv, L.dv2, L.y, L.fm, L.lmax};
+    void *p[] = {L.S, L.invd, L.x, L.b, L.r, L.dv, L.dv2, L.y, L.fm, L.lmax, L.coef};
     for (void *q : p)
       if (q) cudaFree(q);
     L = GmgLevel<T>();
@@ -737,6 +747,7 @@ static cudaError_t gmg_setup_common(Gmg<T> &G, const GridD &g, cudaStream_t st) 
     }
     k_diag_bound<T, B><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.fm, L.invd);
     k_bound<T, B><<<nblk(L.nn, red_blocks()), 256, 0, st>>>(L.nx, L.ny, L.S, L.fm, G.ws, L.lmax);
+    k_cheb_coef<T><<<1, 1, 0, st>>>(L.lmax, L.coef);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -820,22 +831,20 @@ template <class T>
 void gmg_cheb_first(const Gmg<T> &G, int l, const T *b, T *x, T *d, T *r, cudaStream_t st) {
   const GmgLevel<T> &L = G.lv[l];
   const size_t n = (size_t)G.B * L.nn;
-  k_cheb_first<T><<<nblk(n), 256, 0, st>>>(n, b, L.invd, L.lmax, x, d, r);
+  k_cheb_first<T><<<nblk(n), 256, 0, st>>>(n, b, L.invd, L.coef, x, d, r);
 }
 template <class T>
 void gmg_cheb_first_x(const Gmg<T> &G, int l, const T *b, const T *y, T *x, T *d, T *r,
                       cudaStream_t st) {
   const GmgLevel<T> &L = G.lv[l];
   const size_t n = (size_t)G.B * L.nn;
-  k_cheb_first_x<T><<<nblk(n), 256, 0, st>>>(n, b, y, L.invd, L.lmax, x, d, r);
+  k_cheb_first_x<T><<<nblk(n), 256, 0, st>>>(n, b, y, L.invd, L.coef, x, d, r);
 }
 template <class T>
 void gmg_cheb_step(const Gmg<T> &G, int l, const T *y, T *x, T *d, T *r, cudaStream_t st) {
-  // rho0 = 1/sigma = 9/11, rho1 = 1/(2 sigma - rho0) = 99/161
-  const double rho0 = 9.0 / 11.0, rho1 = 99.0 / 161.0;
   const GmgLevel<T> &L = G.lv[l];
   const size_t n = (size_t)G.B * L.nn;
-  k_cheb_step<T><<<nblk(n), 256, 0, st>>>(n, y, L.invd, L.lmax, rho1 * rho0, 2.0 * rho1, x, d, r);
+  k_cheb_step<T><<<nblk(n), 256, 0, st>>>(n, y, L.invd, L.coef, x, d, r);
 }
 template <class T>
 void gmg_sub(size_t n, const T *b, const T *y, T *r, cudaStream_t st) {
@@ -863,14 +872,11 @@ void gmg_dense(const Gmg<T> &G, const T *b, T *x, cudaStream_t st) {
 }
 template <class T>
 void gmg_sten_cheb(const Gmg<T> &G, int l, const T *din, T *dout, T *x, T *r, cudaStream_t st) {
-  const double rho0 = 9.0 / 11.0, rho1 = 99.0 / 161.0;
   const GmgLevel<T> &L = G.lv[l];
   if (G.B == 2)
-    k_sten_cheb<T, 2><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.lmax, rho1 * rho0,
-                                                  2.0 * rho1, din, dout, x, r);
+    k_sten_cheb<T, 2><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.coef, din, dout, x, r);
   else
-    k_sten_cheb<T, 1><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.lmax, rho1 * rho0,
-                                                  2.0 * rho1, din, dout, x, r);
+    k_sten_cheb<T, 1><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.coef, din, dout, x, r);
 }
 template <class T>
 void gmg_coarse_cycle(const Gmg<T> &G, int lc, const T *b0, T *x0, cudaStream_t st) {
@@ -878,7 +884,7 @@ void gmg_coarse_cycle(const Gmg<T> &G, int lc, const T *b0, T *x0, cudaStream_t 
   a.nlev = G.nl - lc;
   for (int l = lc; l < G.nl; ++l) {
     const GmgLevel<T> &L = G.lv[l];
-    a.L[l - lc] = CoarseLevel<T>{L.nx, L.ny, L.S, L.invd, L.x, L.b, L.r, L.dv, L.y, L.fm, L.lmax};
+    a.L[l - lc] = CoarseLevel<T>{L.nx, L.ny, L.S, L.invd, L.x, L.b, L.r, L.dv, L.y, L.fm, L.coef};
   }
   a.b0 = b0;
   a.x0 = x0;

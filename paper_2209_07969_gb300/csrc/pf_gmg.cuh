@@ -29,6 +29,7 @@ struct GmgLevel {
   T *x = nullptr, *b = nullptr, *r = nullptr, *dv = nullptr, *dv2 = nullptr, *y = nullptr;
   uint8_t *fm = nullptr;   // nn bytes, bit c: component c free on this level
   double *lmax = nullptr;  // device scalar
+  T *coef = nullptr;       // Chebyshev coefficients in T (see k_cheb_coef)
 };
 
 template <class T>

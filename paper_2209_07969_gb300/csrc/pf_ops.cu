@@ -108,13 +108,28 @@ __device__ __forceinline__ void krylov_epilogue(int epi, KrylovScal *sc, double 
 }
 
 // ------------------------------------------------------------------------------------
+// Per-launch constants in the kernel's arithmetic type, computed on the host: GB300 runs
+// FP64 at 1/64 of the FP32 rate, so a float kernel must not touch a double.
+// ------------------------------------------------------------------------------------
+template <class T>
+struct ElemConst {
+  T ihx, ihy, w, mu, K, cd, eta, G0, G1, kappa;
+};
+template <class T>
+static ElemConst<T> elem_const(const GridD &g, const MatD &m, double kappa = 0.0) {
+  const double a = 0.5 * (1.0 - 1.0 / sqrt(3.0)), b = 0.5 * (1.0 + 1.0 / sqrt(3.0));
+  return ElemConst<T>{T(1.0 / g.hx), T(1.0 / g.hy), T(0.25 * g.hx * g.hy), T(m.mu), T(m.K),
+                      T(m.cdim), T(m.eta), T(a), T(b), T(kappa)};
+}
+
+// ------------------------------------------------------------------------------------
 // Elasticity: tangent apply, tangent diagonal, nonlinear internal force.
 // ------------------------------------------------------------------------------------
 enum { EL_APPLY = 0, EL_DIAG = 1, EL_RESID = 2 };
 
 template <class T, int MODE>
 __global__ void __launch_bounds__(TILE_THREADS)
-k_elas(GridD g, MatD mt, const T *__restrict__ d, const uint8_t *__restrict__ tens_in,
+k_elas(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restrict__ tens_in,
        const T *__restrict__ x, T *__restrict__ y, uint8_t *__restrict__ tens_out,
        KrylovScal *sc, RedWs ws, int epi) {
   constexpr int PX = TX + 2, PY = TY + 2, EX = TX + 1, EY = TY + 1, NE = EX * EY;
@@ -123,7 +138,7 @@ k_elas(GridD g, MatD mt, const T *__restrict__ d, const uint8_t *__restrict__ te
   __shared__ T ef[8][NE];
   const int nx = g.nx, ny = g.ny, ld = nx + 1;
   const int tbx = (nx + 1 + TX - 1) / TX, ntiles = tbx * ((ny + 1 + TY - 1) / TY);
-  double dot = 0.0;
+  T dot = T(0);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
   const int i0 = (tile % tbx) * TX, j0 = (tile / tbx) * TY;
 
@@ -151,9 +166,9 @@ k_elas(GridD g, MatD mt, const T *__restrict__ d, const uint8_t *__restrict__ te
   }
   __syncthreads();
 
-  const T ihx = T(1.0 / g.hx), ihy = T(1.0 / g.hy), w = T(0.25 * g.hx * g.hy);
-  const T mu = T(mt.mu), K = T(mt.K), cd = T(mt.cdim), eta = T(mt.eta);
-  const T G0 = T(gp_lo()), G1 = T(gp_hi());
+  const T ihx = kc.ihx, ihy = kc.ihy, w = kc.w;
+  const T mu = kc.mu, K = kc.K, cd = kc.cd, eta = kc.eta;
+  const T G0 = kc.G0, G1 = kc.G1;
   for (int t = threadIdx.x; t < NE; t += TILE_THREADS) {
     const int le = t % EX, me = t / EX;
     const int ei = i0 - 1 + le, ej = j0 - 1 + me;
@@ -246,13 +261,13 @@ k_elas(GridD g, MatD mt, const T *__restrict__ d, const uint8_t *__restrict__ te
     y[2 * n + 1] = fy;
     if (MODE == EL_APPLY && epi != EPI_NONE) {
       const int p = (lj + 1) * PX + li + 1;
-      dot += (double)sx[0][p] * (double)fx + (double)sx[1][p] * (double)fy;
+      dot += sx[0][p] * fx + sx[1][p] * fy;
     }
   }
   __syncthreads();
   }  // tiles
   if (MODE == EL_APPLY && epi != EPI_NONE) {
-    double v[1] = {dot}, tot[1];
+    double v[1] = {(double)dot}, tot[1];
     if (grid_reduce<1>(v, ws, tot)) krylov_epilogue(epi, sc, tot[0]);
   }
 }
@@ -264,14 +279,14 @@ enum { DM_APPLY = 0, DM_DIAG = 1, DM_RHS = 2 };
 
 template <class T, class C, int MODE>
 __global__ void __launch_bounds__(TILE_THREADS)
-k_damage(GridD g, const C *__restrict__ c, double kappa_d, const T *__restrict__ x,
+k_damage(GridD g, ElemConst<T> kc, const C *__restrict__ c, const T *__restrict__ x,
          T *__restrict__ y, KrylovScal *sc, RedWs ws, int epi) {
   constexpr int PX = TX + 2, PY = TY + 2, EX = TX + 1, EY = TY + 1, NE = EX * EY;
   __shared__ T sxv[PY * PX];
   __shared__ T ef[4][NE];
   const int nx = g.nx, ny = g.ny, ld = nx + 1;
   const int tbx = (nx + 1 + TX - 1) / TX, ntiles = tbx * ((ny + 1 + TY - 1) / TY);
-  double dot = 0.0;
+  T dot = T(0);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
   const int i0 = (tile % tbx) * TX, j0 = (tile / tbx) * TY;
   if (MODE == DM_APPLY) {
@@ -288,9 +303,9 @@ k_damage(GridD g, const C *__restrict__ c, double kappa_d, const T *__restrict__
     }
     __syncthreads();
   }
-  const T ihx = T(1.0 / g.hx), ihy = T(1.0 / g.hy), w = T(0.25 * g.hx * g.hy);
-  const T kappa = T(kappa_d);
-  const T G0 = T(gp_lo()), G1 = T(gp_hi());
+  const T ihx = kc.ihx, ihy = kc.ihy, w = kc.w;
+  const T kappa = kc.kappa;
+  const T G0 = kc.G0, G1 = kc.G1;
   for (int t = threadIdx.x; t < NE; t += TILE_THREADS) {
     const int le = t % EX, me = t / EX;
     const int ei = i0 - 1 + le, ej = j0 - 1 + me;
@@ -347,12 +362,12 @@ k_damage(GridD g, const C *__restrict__ c, double kappa_d, const T *__restrict__
     const size_t n = (size_t)gj * ld + gi;
     if (MODE != DM_RHS && g.dofm && (ldg(g.dofm + n) & 4)) v = T(0);
     y[n] = v;
-    if (MODE == DM_APPLY && epi != EPI_NONE) dot += (double)sxv[(lj + 1) * PX + li + 1] * (double)v;
+    if (MODE == DM_APPLY && epi != EPI_NONE) dot += sxv[(lj + 1) * PX + li + 1] * v;
   }
   __syncthreads();
   }  // tiles
   if (MODE == DM_APPLY && epi != EPI_NONE) {
-    double vv[1] = {dot}, tot[1];
+    double vv[1] = {(double)dot}, tot[1];
     if (grid_reduce<1>(vv, ws, tot)) krylov_epilogue(epi, sc, tot[0]);
   }
 }
@@ -584,18 +599,19 @@ void elas_apply(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, 
   RedWs w = ws ? *ws : RedWs{nullptr, nullptr, 0};
   const int e = ws ? epi : EPI_NONE;
   k_elas<T, EL_APPLY><<<e == EPI_NONE ? tile_grid(g) : tile_grid_red(g), TILE_THREADS, 0, st>>>(
-      g, m, d, tens, x, y, nullptr, sc, w, e);
+      g, elem_const<T>(g, m), d, tens, x, y, nullptr, sc, w, e);
 }
 template <class T>
 void elas_diag(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, T *diag,
                cudaStream_t st) {
-  k_elas<T, EL_DIAG><<<tile_grid(g), TILE_THREADS, 0, st>>>(g, m, d, tens, nullptr, diag,
-                                                            nullptr, nullptr, RedWs{}, EPI_NONE);
+  k_elas<T, EL_DIAG><<<tile_grid(g), TILE_THREADS, 0, st>>>(g, elem_const<T>(g, m), d, tens,
+                                                            nullptr, diag, nullptr, nullptr,
+                                                            RedWs{}, EPI_NONE);
 }
 void elas_residual(const GridD &g, const MatD &m, const double *u, const double *d, double *F,
                    uint8_t *tens, cudaStream_t st) {
-  k_elas<double, EL_RESID><<<tile_grid(g), TILE_THREADS, 0, st>>>(g, m, d, nullptr, u, F, tens,
-                                                                  nullptr, RedWs{}, EPI_NONE);
+  k_elas<double, EL_RESID><<<tile_grid(g), TILE_THREADS, 0, st>>>(
+      g, elem_const<double>(g, m), d, nullptr, u, F, tens, nullptr, RedWs{}, EPI_NONE);
 }
 template <class T>
 void damage_apply(const GridD &g, const T *c, double kappa, const T *x, T *y, cudaStream_t st,
@@ -603,16 +619,16 @@ void damage_apply(const GridD &g, const T *c, double kappa, const T *x, T *y, cu
   RedWs w = ws ? *ws : RedWs{nullptr, nullptr, 0};
   const int e = ws ? epi : EPI_NONE;
   k_damage<T, T, DM_APPLY><<<e == EPI_NONE ? tile_grid(g) : tile_grid_red(g), TILE_THREADS, 0, st>>>(
-      g, c, kappa, x, y, sc, w, e);
+      g, elem_const<T>(g, MatD{}, kappa), c, x, y, sc, w, e);
 }
 template <class T>
 void damage_diag(const GridD &g, const T *c, double kappa, T *diag, cudaStream_t st) {
-  k_damage<T, T, DM_DIAG><<<tile_grid(g), TILE_THREADS, 0, st>>>(g, c, kappa, nullptr, diag,
-                                                                 nullptr, RedWs{}, EPI_NONE);
+  k_damage<T, T, DM_DIAG><<<tile_grid(g), TILE_THREADS, 0, st>>>(
+      g, elem_const<T>(g, MatD{}, kappa), c, nullptr, diag, nullptr, RedWs{}, EPI_NONE);
 }
 void damage_rhs(const GridD &g, const double *H, double *b, cudaStream_t st) {
   k_damage<double, double, DM_RHS><<<tile_grid(g), TILE_THREADS, 0, st>>>(
-      g, H, 0.0, nullptr, b, nullptr, RedWs{}, EPI_NONE);
+      g, elem_const<double>(g, MatD{}, 0.0), H, nullptr, b, nullptr, RedWs{}, EPI_NONE);
 }
 void qp_energy(const GridD &g, const MatD &m, const double *u, const double *Hprev,
                double *psi, double *Hout, cudaStream_t st) {

@@ -78,12 +78,14 @@ __device__ __forceinline__ bool constrained(const uint8_t *dofm, size_t i, int n
 }
 
 // ---- CG ------------------------------------------------------------------------------
+// Each thread sums its few entries in the vector type; the cross-thread tree (warp,
+// CTA, grid) runs in FP64.
 // x = 0, r = b, z = M^-1 r, p = z; rz = r.z, rr = r.r -> sc.
 template <class T>
 __global__ void k_cg_init(size_t n, const T *__restrict__ b, T *__restrict__ x,
                           T *__restrict__ r, T *__restrict__ z, T *__restrict__ p,
                           const T *__restrict__ invd, KrylovScal *sc, RedWs ws) {
-  double rz = 0.0, rr = 0.0;
+  T rz = T(0), rr = T(0);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     const T ri = b[i];
@@ -92,10 +94,10 @@ __global__ void k_cg_init(size_t n, const T *__restrict__ b, T *__restrict__ x,
     r[i] = ri;
     z[i] = zi;
     p[i] = zi;
-    rz += (double)ri * (double)zi;
-    rr += (double)ri * (double)ri;
+    rz += ri * zi;
+    rr += ri * ri;
   }
-  double v[2] = {rz, rr}, tot[2];
+  double v[2] = {(double)rz, (double)rr}, tot[2];
   if (vgrid_reduce<2>(v, ws, tot, false)) {
     sc->rz = tot[0];
     sc->rr = tot[1];
@@ -111,7 +113,7 @@ __global__ void k_cg_update(size_t n, T *__restrict__ x, T *__restrict__ r, T *_
                             const T *__restrict__ p, const T *__restrict__ q,
                             const T *__restrict__ invd, KrylovScal *sc, RedWs ws) {
   const T a = (T)sc->alpha;
-  double rz = 0.0, rr = 0.0;
+  T rz = T(0), rr = T(0);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     x[i] += a * p[i];
@@ -119,10 +121,10 @@ __global__ void k_cg_update(size_t n, T *__restrict__ x, T *__restrict__ r, T *_
     r[i] = ri;
     const T zi = invd[i] * ri;
     z[i] = zi;
-    rz += (double)ri * (double)zi;
-    rr += (double)ri * (double)ri;
+    rz += ri * zi;
+    rr += ri * ri;
   }
-  double v[2] = {rz, rr}, tot[2];
+  double v[2] = {(double)rz, (double)rr}, tot[2];
   if (vgrid_reduce<2>(v, ws, tot, false)) {
     const double old = sc->rz;
     sc->beta = (old > 0.0 && isfinite(tot[0])) ? tot[0] / old : 0.0;
@@ -146,15 +148,15 @@ __global__ void k_cg_dir(size_t n, const T *__restrict__ z, T *__restrict__ p,
 template <class T>
 __global__ void k_pcg_init(size_t n, const T *__restrict__ b, T *__restrict__ x,
                            T *__restrict__ r, KrylovScal *sc, RedWs ws) {
-  double rr = 0.0;
+  T rr = T(0);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     const T ri = b[i];
     x[i] = T(0);
     r[i] = ri;
-    rr += (double)ri * (double)ri;
+    rr += ri * ri;
   }
-  double v[1] = {rr}, tot[1];
+  double v[1] = {(double)rr}, tot[1];
   if (vgrid_reduce<1>(v, ws, tot, false)) {
     sc->rr = tot[0];
     sc->rz = 0.0;
@@ -170,15 +172,15 @@ __global__ void k_pcg_update(size_t n, T *__restrict__ x, T *__restrict__ r,
                              const T *__restrict__ p, const T *__restrict__ q, KrylovScal *sc,
                              RedWs ws) {
   const T a = (T)sc->alpha;
-  double rr = 0.0;
+  T rr = T(0);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     x[i] += a * p[i];
     const T ri = r[i] - a * q[i];
     r[i] = ri;
-    rr += (double)ri * (double)ri;
+    rr += ri * ri;
   }
-  double v[1] = {rr}, tot[1];
+  double v[1] = {(double)rr}, tot[1];
   if (vgrid_reduce<1>(v, ws, tot, false)) sc->rr = tot[0];
 }
 
@@ -187,14 +189,14 @@ __global__ void k_pcg_update(size_t n, T *__restrict__ x, T *__restrict__ r,
 template <class T>
 __global__ void k_pcg_rz(size_t n, const T *__restrict__ r, const T *__restrict__ z,
                          T *__restrict__ p, int first, KrylovScal *sc, RedWs ws) {
-  double rz = 0.0;
+  T rz = T(0);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     const T zi = z[i];
-    rz += (double)r[i] * (double)zi;
+    rz += r[i] * zi;
     if (first) p[i] = zi;
   }
-  double v[1] = {rz}, tot[1];
+  double v[1] = {(double)rz}, tot[1];
   if (vgrid_reduce<1>(v, ws, tot, false)) {
     const double old = sc->rz;
     sc->beta = (!first && old > 0.0 && isfinite(tot[0])) ? tot[0] / old : 0.0;
