@@ -18,7 +18,7 @@ namespace pf {
 constexpr int GMG_MAX_LEVELS = 16;
 constexpr int GMG_COARSE_MAX = 8;   // coarsen while max(nx, ny) > this
 constexpr int CHEB_DEGREE = 2;
-constexpr int GMG_CTA_NODES = 4500;  // levels with at most this many nodes run in one CTA
+constexpr int GMG_CTA_NODES = 300;  // levels with at most this many nodes run in one CTA
 
 template <class T>
 struct GmgLevel {

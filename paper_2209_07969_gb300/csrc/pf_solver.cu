@@ -270,6 +270,39 @@ pf_status refine(pf_ctx *ctx, ApplyD applyd, Inner inner, size_t n, int ncomp, c
   return PF_OK;
 }
 
+// ---- lagged multigrid -----------------------------------------------------------------
+// Solve with the current hierarchy; a lagged hierarchy gets a soft iteration cap, and when
+// the solve misses it the hierarchy is rebuilt for the current operator and the solve
+// restarted.  setup() rebuilds; solve(maxit, &it, &ok) runs one Krylov solve.
+template <class Setup, class Solve>
+pf_status mg_solve(pf_ctx *ctx, MgState &S, bool mg, Setup setup, Solve solve, int *lin,
+                   bool *ok) {
+  bool fresh = false;
+  if (mg && S.need()) {
+    CKS(setup());
+    S.built();
+    fresh = true;
+  }
+  const int full = ctx->opt.max_lin;
+  int cap = full;
+  if (mg && !fresh) {
+    const int soft = 3 * (S.base > 0 ? S.base : 10) + 10;
+    cap = soft < full ? soft : full;
+  }
+  int it = 0;
+  CKS(solve(cap, &it, ok));
+  *lin += it;
+  if (mg && !fresh && !*ok && cap < full) {
+    CKS(setup());
+    S.built();
+    it = 0;
+    CKS(solve(full, &it, ok));
+    *lin += it;
+  }
+  if (mg) S.record(it);
+  return PF_OK;
+}
+
 // ---- u-solve ---------------------------------------------------------------------------
 // One Newton correction: K_t(d, tension) kx = kb on free DOFs.
 pf_status newton_correction(pf_ctx *ctx, int *lin, int *refines, bool *ok) {
@@ -283,22 +316,21 @@ pf_status newton_correction(pf_ctx *ctx, int *lin, int *refines, bool *ok) {
     auto Af = [ctx, st](const double *xx, double *yy) {
       elas_apply<double>(ctx->g, ctx->m, ctx->d, ctx->tens, xx, yy, st);
     };
-    if (mg && ctx->mg_u.need()) {
-      cudaError_t e = gmg_setup_elas<double>(ctx->gu, ctx->g, ctx->m, ctx->d, ctx->tens, st);
-      if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
-      ctx->mg_u.built();
-    } else if (!mg) {
+    if (!mg) {
       elas_diag<double>(ctx->g, ctx->m, ctx->d, ctx->tens, ctx->kz, st);
       invert<double>(n, ctx->kz, ctx->kinv, st);
       ctx->launches += 2;
     }
-    int it = 0;
-    CKS(pcg<double>(ctx, SL_U, A, Af, mg ? &ctx->gu : nullptr, n, ctx->kb, ctx->kx, ctx->kr,
-                    ctx->kz, ctx->kp, ctx->kq, ctx->kinv, ctx->opt.tol_lin, ctx->opt.max_lin,
-                    &it, ok));
-    *lin += it;
-    if (mg) ctx->mg_u.record(it);
-    return PF_OK;
+    auto setup = [&]() -> pf_status {
+      cudaError_t e = gmg_setup_elas<double>(ctx->gu, ctx->g, ctx->m, ctx->d, ctx->tens, st);
+      if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
+      return PF_OK;
+    };
+    auto solve = [&](int maxit, int *it, bool *sok) {
+      return pcg<double>(ctx, SL_U, A, Af, mg ? &ctx->gu : nullptr, n, ctx->kb, ctx->kx, ctx->kr,
+                         ctx->kz, ctx->kp, ctx->kq, ctx->kinv, ctx->opt.tol_lin, maxit, it, sok);
+    };
+    return mg_solve(ctx, ctx->mg_u, mg, setup, solve, lin, ok);
   }
   auto Af32 = [ctx, st](const float *xx, float *yy, int epi) {
     elas_apply<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, xx, yy, st, ctx->sc, &ctx->ws, epi);
@@ -306,27 +338,31 @@ pf_status newton_correction(pf_ctx *ctx, int *lin, int *refines, bool *ok) {
   auto Ff32 = [ctx, st](const float *xx, float *yy) {
     elas_apply<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, xx, yy, st);
   };
-  if (mg && ctx->mg_u.need()) {
-    cudaError_t e = gmg_setup_elas<float>(ctx->gu32, ctx->g, ctx->m, ctx->fd, ctx->tens, st);
-    if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
-    ctx->mg_u.built();
-  } else if (!mg) {
+  if (!mg) {
     elas_diag<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, ctx->fz, st);
     invert<float>(n, ctx->fz, ctx->finv, st);
     ctx->launches += 2;
   }
-  auto inner = [&](int *it, bool *iok) {
+  auto setup = [&]() -> pf_status {
+    cudaError_t e = gmg_setup_elas<float>(ctx->gu32, ctx->g, ctx->m, ctx->fd, ctx->tens, st);
+    if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
+    return PF_OK;
+  };
+  auto solve = [&](int maxit, int *it, bool *iok) {
     return pcg<float>(ctx, SL_U, Af32, Ff32, mg ? &ctx->gu32 : nullptr, n, ctx->fb, ctx->fx,
-                      ctx->fr, ctx->fz, ctx->fp, ctx->fq, ctx->finv, ctx->opt.tol_inner,
-                      ctx->opt.max_lin, it, iok);
+                      ctx->fr, ctx->fz, ctx->fp, ctx->fq, ctx->finv, ctx->opt.tol_inner, maxit,
+                      it, iok);
+  };
+  auto inner = [&](int *it, bool *iok) {
+    int cnt = 0;
+    pf_status s2 = mg_solve(ctx, ctx->mg_u, mg, setup, solve, &cnt, iok);
+    *it = cnt;
+    return s2;
   };
   auto AD = [ctx, st](const double *xx, double *yy) {
     elas_apply<double>(ctx->g, ctx->m, ctx->d, ctx->tens, xx, yy, st);
   };
-  int it0 = *lin;
-  pf_status rs = refine(ctx, AD, inner, n, 2, ctx->kb, ctx->kx, lin, refines, ok);
-  if (mg) ctx->mg_u.record(*lin - it0);
-  return rs;
+  return refine(ctx, AD, inner, n, 2, ctx->kb, ctx->kx, lin, refines, ok);
 }
 
 pf_status solve_u(pf_ctx *ctx, int *newton, int *lin, int *refines, bool *ok) {
@@ -383,23 +419,23 @@ pf_status solve_damage(pf_ctx *ctx, const double *c, const double *rhs, double *
     auto Af = [ctx, st, kappa](const double *xx, double *yy) {
       damage_apply<double>(ctx->g, ctx->csolve, kappa, xx, yy, st);
     };
-    if (mg && ctx->mg_d.need()) {
-      cudaError_t e = gmg_setup_damage<double>(ctx->gd, ctx->g, ctx->csolve, kappa, st);
-      if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
-      ctx->mg_d.built();
-    } else if (!mg) {
+    if (!mg) {
       damage_diag<double>(ctx->g, ctx->csolve, kappa, ctx->kz, st);
       invert<double>(n, ctx->kz, ctx->kinv, st);
       ctx->launches += 2;
     }
     CK(cudaMemcpyAsync(ctx->kb, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    int it = 0;
-    CKS(pcg<double>(ctx, SL_D, A, Af, mg ? &ctx->gd : nullptr, n, ctx->kb, ctx->dd, ctx->kr,
-                    ctx->kz, ctx->kp, ctx->kq, ctx->kinv, ctx->opt.tol_lin, ctx->opt.max_lin,
-                    &it, ok));
+    auto setup = [&]() -> pf_status {
+      cudaError_t e = gmg_setup_damage<double>(ctx->gd, ctx->g, ctx->csolve, kappa, st);
+      if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
+      return PF_OK;
+    };
+    auto solve = [&](int maxit, int *it, bool *sok) {
+      return pcg<double>(ctx, SL_D, A, Af, mg ? &ctx->gd : nullptr, n, ctx->kb, ctx->dd, ctx->kr,
+                         ctx->kz, ctx->kp, ctx->kq, ctx->kinv, ctx->opt.tol_lin, maxit, it, sok);
+    };
+    CKS(mg_solve(ctx, ctx->mg_d, mg, setup, solve, lin, ok));
     if (x != ctx->dd) CK(cudaMemcpyAsync(x, ctx->dd, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    *lin += it;
-    if (mg) ctx->mg_d.record(it);
     return PF_OK;
   }
   convert<double, float>(ctx->nq, ctx->csolve, ctx->fc, st);
@@ -410,27 +446,31 @@ pf_status solve_damage(pf_ctx *ctx, const double *c, const double *rhs, double *
   auto Ff32 = [ctx, st, kappa](const float *xx, float *yy) {
     damage_apply<float>(ctx->g, ctx->fc, kappa, xx, yy, st);
   };
-  if (mg && ctx->mg_d.need()) {
-    cudaError_t e = gmg_setup_damage<float>(ctx->gd32, ctx->g, ctx->fc, kappa, st);
-    if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
-    ctx->mg_d.built();
-  } else if (!mg) {
+  if (!mg) {
     damage_diag<float>(ctx->g, ctx->fc, kappa, ctx->fz, st);
     invert<float>(n, ctx->fz, ctx->finv, st);
     ctx->launches += 2;
   }
-  auto inner = [&](int *it, bool *iok) {
+  auto setup = [&]() -> pf_status {
+    cudaError_t e = gmg_setup_damage<float>(ctx->gd32, ctx->g, ctx->fc, kappa, st);
+    if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
+    return PF_OK;
+  };
+  auto solve = [&](int maxit, int *it, bool *iok) {
     return pcg<float>(ctx, SL_D, Af32, Ff32, mg ? &ctx->gd32 : nullptr, n, ctx->fb, ctx->fx,
-                      ctx->fr, ctx->fz, ctx->fp, ctx->fq, ctx->finv, ctx->opt.tol_inner,
-                      ctx->opt.max_lin, it, iok);
+                      ctx->fr, ctx->fz, ctx->fp, ctx->fq, ctx->finv, ctx->opt.tol_inner, maxit,
+                      it, iok);
+  };
+  auto inner = [&](int *it, bool *iok) {
+    int cnt = 0;
+    pf_status s2 = mg_solve(ctx, ctx->mg_d, mg, setup, solve, &cnt, iok);
+    *it = cnt;
+    return s2;
   };
   auto AD = [ctx, st, kappa](const double *xx, double *yy) {
     damage_apply<double>(ctx->g, ctx->csolve, kappa, xx, yy, st);
   };
-  int it0 = *lin;
-  pf_status rs = refine(ctx, AD, inner, n, 1, rhs, x, lin, refines, ok);
-  if (mg) ctx->mg_d.record(*lin - it0);
-  return rs;
+  return refine(ctx, AD, inner, n, 1, rhs, x, lin, refines, ok);
 }
 
 // rhs = free ? b(H) - K(c) d : 0 ; then d += K_ff^-1 rhs.
