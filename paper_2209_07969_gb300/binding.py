@@ -184,6 +184,15 @@ class Simulation:
               "pf_get_fields", self.ctx)
         return u, d, H.reshape(-1, 4)
 
+    def fields_into(self, u=None, d=None, H=None):
+        """Copy the committed fields into caller-owned float64 arrays (any may be None);
+        pinned host arrays make the copy asynchronous-capable."""
+        ptr = lambda a: None if a is None else a.ctypes.data
+        for a, n in ((u, 2 * self.nn), (d, self.nn), (H, self.nq)):
+            if a is not None and (a.dtype != np.float64 or a.size != n or not a.flags.c_contiguous):
+                raise ValueError("field buffer has the wrong size or type")
+        check(lib().pf_get_fields(self.ctx, ptr(u), ptr(d), ptr(H)), "pf_get_fields", self.ctx)
+
     def set_fields(self, u, d, H, ubar):
         u = np.ascontiguousarray(u, dtype=np.float64)
         d = np.ascontiguousarray(d, dtype=np.float64)

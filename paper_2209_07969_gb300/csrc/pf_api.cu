@@ -27,12 +27,13 @@ struct Scratch {
   void *base = nullptr;
   pf_status alloc(int blocks) {
     ws.max_blocks = blocks;
-    size_t bytes = (size_t)4 * blocks * sizeof(double) + 64;
-    if (cudaMalloc(&base, bytes) != cudaSuccess) return PF_ENOMEM;
+    const size_t pbytes = (size_t)4 * blocks * sizeof(double);
+    const size_t cbytes = red_counters(blocks) * sizeof(unsigned);
+    if (cudaMalloc(&base, pbytes + cbytes + 64) != cudaSuccess) return PF_ENOMEM;
     ws.partials = (double *)base;
-    ws.counter = (unsigned *)((char *)base + (size_t)4 * blocks * sizeof(double));
-    res = (double *)((char *)base + (size_t)4 * blocks * sizeof(double) + 16);
-    return cudaMemset(ws.counter, 0, sizeof(unsigned)) == cudaSuccess ? PF_OK : PF_ECUDA;
+    ws.counter = (unsigned *)((char *)base + pbytes);
+    res = (double *)((char *)base + pbytes + ((cbytes + 15) / 16) * 16);
+    return cudaMemset(ws.counter, 0, cbytes) == cudaSuccess ? PF_OK : PF_ECUDA;
   }
   ~Scratch() {
     if (base) cudaFree(base);

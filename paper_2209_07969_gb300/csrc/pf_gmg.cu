@@ -33,8 +33,7 @@ __device__ void grid_max(double v, const RedWs ws, double *out) {
     double s = sh[0];
     for (int w = 1; w < nw; ++w) s = fmax(s, sh[w]);
     ws.partials[blockIdx.x] = s;
-    __threadfence();
-    am_last = atomicAdd(ws.counter, 1u) == gridDim.x - 1;
+    am_last = red_arrive(ws.counter, blockIdx.x, gridDim.x);
   }
   __syncthreads();
   if (!am_last) return;
@@ -49,7 +48,6 @@ __device__ void grid_max(double v, const RedWs ws, double *out) {
     double t = sh[0];
     for (int w = 1; w < nw; ++w) t = fmax(t, sh[w]);
     *out = t;
-    *ws.counter = 0u;
   }
 }
 
@@ -300,24 +298,33 @@ __global__ void k_fm_coarse(int nxf, int nyf, const uint8_t *__restrict__ fmf, i
 
 // (A x)_n for one node: vectors are zero on non-free DOFs at every level, so the
 // neighbours' masks are not needed; out-of-grid neighbours have no stencil entry.
-template <class T, int B>
+// NC: x is not written while the kernel runs, so the read-only data path may be used
+// (false inside the single-CTA coarse cycle, which rewrites its vectors between phases).
+template <class T, int B, bool NC = true>
 __device__ __forceinline__ void sten_row(int nx, int ny, size_t nn, const T *__restrict__ S,
                                          const T *__restrict__ x, size_t n, T (&acc)[B]) {
+  // Stencil entries towards neighbours outside the grid are zero, so neighbour indices are
+  // clamped into the grid instead of branched on: all loads issue back to back.
   const int i = (int)(n % (nx + 1)), j = (int)(n / (nx + 1));
+  const int im = i > 0 ? i - 1 : 0, ip = i < nx ? i + 1 : nx;
+  const int jm = j > 0 ? j - 1 : 0, jp = j < ny ? j + 1 : ny;
+  const int ld = nx + 1;
+  const size_t m[9] = {(size_t)jm * ld + im, (size_t)jm * ld + i, (size_t)jm * ld + ip,
+                       (size_t)j * ld + im,  (size_t)j * ld + i,  (size_t)j * ld + ip,
+                       (size_t)jp * ld + im, (size_t)jp * ld + i, (size_t)jp * ld + ip};
+  T xv[9][B];
+#pragma unroll
+  for (int k = 0; k < 9; ++k)
+#pragma unroll
+    for (int c = 0; c < B; ++c) xv[k][c] = NC ? __ldg(x + B * m[k] + c) : x[B * m[k] + c];
 #pragma unroll
   for (int r = 0; r < B; ++r) acc[r] = T(0);
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const int ii = i + k % 3 - 1, jj = j + k / 3 - 1;
-    if (ii < 0 || ii > nx || jj < 0 || jj > ny) continue;
-    const size_t m = (size_t)jj * (nx + 1) + ii;
+  for (int k = 0; k < 9; ++k)
 #pragma unroll
-    for (int c = 0; c < B; ++c) {
-      const T xv = x[B * m + c];
+    for (int c = 0; c < B; ++c)
 #pragma unroll
-      for (int r = 0; r < B; ++r) acc[r] += S[sidx<B>(k, r, c, n, nn)] * xv;
-    }
-  }
+      for (int r = 0; r < B; ++r) acc[r] += __ldg(S + sidx<B>(k, r, c, n, nn)) * xv[k][c];
 }
 
 // y = A x  (mode 0) or y = b - A x (mode 1), rows of non-free DOFs zero.
@@ -387,7 +394,7 @@ __device__ void cta_apply(const CoarseLevel<T> &L, const T *x, const T *b, T *y,
   const size_t nn = (size_t)(L.nx + 1) * (L.ny + 1);
   for (size_t n = threadIdx.x; n < nn; n += blockDim.x) {
     T acc[B];
-    sten_row<T, B>(L.nx, L.ny, nn, L.S, x, n, acc);
+    sten_row<T, B, false>(L.nx, L.ny, nn, L.S, x, n, acc);
     const uint8_t f = L.fm[n];
 #pragma unroll
     for (int r = 0; r < B; ++r) {
@@ -568,7 +575,7 @@ __global__ void k_sub(size_t n, const T *__restrict__ b, const T *__restrict__ y
     r[i] = b[i] - y[i];
 }
 
-// b_c = P^T r_f over free DOFs.
+// b_c = P^T r_f over free DOFs (out-of-grid fine neighbours: clamped index, weight 0).
 template <class T, int B>
 __global__ void k_restrict(int nxf, int nyf, const T *__restrict__ rf, const uint8_t *__restrict__ fmf,
                            int nxc, int nyc, const uint8_t *__restrict__ fmc, T *__restrict__ bc) {
@@ -577,44 +584,57 @@ __global__ void k_restrict(int nxf, int nyf, const T *__restrict__ rf, const uin
        I += (size_t)gridDim.x * blockDim.x) {
     const int Ix = (int)(I % (nxc + 1)), Iy = (int)(I / (nxc + 1));
     T acc[B];
+#pragma unroll
     for (int c = 0; c < B; ++c) acc[c] = T(0);
-    for (int a = -1; a <= 1; ++a)
-      for (int b = -1; b <= 1; ++b) {
-        const int ix = 2 * Ix + a, iy = 2 * Iy + b;
-        if (ix < 0 || ix > nxf || iy < 0 || iy > nyf) continue;
-        const T wi = (a == 0 ? T(1) : T(0.5)) * (b == 0 ? T(1) : T(0.5));
-        const size_t fi = (size_t)iy * (nxf + 1) + ix;
-        const uint8_t m = fmf[fi];
-        for (int c = 0; c < B; ++c)
-          if ((m >> c) & 1) acc[c] += wi * rf[B * fi + c];
+#pragma unroll
+    for (int b = -1; b <= 1; ++b) {
+      const int iy = 2 * Iy + b;
+      const bool vy = iy >= 0 && iy <= nyf;
+      const int iyc = iy < 0 ? 0 : (iy > nyf ? nyf : iy);
+#pragma unroll
+      for (int a = -1; a <= 1; ++a) {
+        const int ix = 2 * Ix + a;
+        const bool v = vy && ix >= 0 && ix <= nxf;
+        const int ixc = ix < 0 ? 0 : (ix > nxf ? nxf : ix);
+        const T wi = v ? (a == 0 ? T(1) : T(0.5)) * (b == 0 ? T(1) : T(0.5)) : T(0);
+        const size_t fi = (size_t)iyc * (nxf + 1) + ixc;
+        const uint8_t m = __ldg(fmf + fi);
+#pragma unroll
+        for (int c = 0; c < B; ++c) {
+          const T rv = __ldg(rf + B * fi + c);
+          acc[c] += ((m >> c) & 1) ? wi * rv : T(0);
+        }
       }
+    }
     const uint8_t mc = fmc[I];
+#pragma unroll
     for (int c = 0; c < B; ++c) bc[B * I + c] = ((mc >> c) & 1) ? acc[c] : T(0);
   }
 }
 
-// x_f += P x_c over free fine DOFs.
+// x_f += P x_c over free fine DOFs (always four parents, out-of-grid ones weighted 0).
 template <class T, int B>
 __global__ void k_prolong_add(int nxf, int nyf, const uint8_t *__restrict__ fmf, int nxc,
                               const T *__restrict__ xc, T *__restrict__ xf) {
   const size_t nnf = (size_t)(nxf + 1) * (nyf + 1);
+  const int nyc = (nyf + 1) / 2;
   for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nnf;
        n += (size_t)gridDim.x * blockDim.x) {
     const uint8_t m = fmf[n];
     if (!m) continue;
     const int ix = (int)(n % (nxf + 1)), iy = (int)(n / (nxf + 1));
     const int px0 = ix >> 1, py0 = iy >> 1;
-    const int npx = (ix & 1) ? 2 : 1, npy = (iy & 1) ? 2 : 1;
-    T acc[B];
-    for (int c = 0; c < B; ++c) acc[c] = T(0);
-    for (int u = 0; u < npx; ++u)
-      for (int v = 0; v < npy; ++v) {
-        const T wj = (npx == 2 ? T(0.5) : T(1)) * (npy == 2 ? T(0.5) : T(1));
-        const size_t J = (size_t)(py0 + v) * (nxc + 1) + (px0 + u);
-        for (int c = 0; c < B; ++c) acc[c] += wj * xc[B * J + c];
-      }
-    for (int c = 0; c < B; ++c)
-      if ((m >> c) & 1) xf[B * n + c] += acc[c];
+    const int px1 = px0 + 1 <= nxc ? px0 + 1 : nxc, py1 = py0 + 1 <= nyc ? py0 + 1 : nyc;
+    const T wx1 = (ix & 1) ? T(0.5) : T(0), wx0 = T(1) - wx1;
+    const T wy1 = (iy & 1) ? T(0.5) : T(0), wy0 = T(1) - wy1;
+    const size_t J00 = (size_t)py0 * (nxc + 1) + px0, J01 = (size_t)py0 * (nxc + 1) + px1;
+    const size_t J10 = (size_t)py1 * (nxc + 1) + px0, J11 = (size_t)py1 * (nxc + 1) + px1;
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      const T v = wy0 * (wx0 * __ldg(xc + B * J00 + c) + wx1 * __ldg(xc + B * J01 + c)) +
+                  wy1 * (wx0 * __ldg(xc + B * J10 + c) + wx1 * __ldg(xc + B * J11 + c));
+      if ((m >> c) & 1) xf[B * n + c] += v;
+    }
   }
 }
 

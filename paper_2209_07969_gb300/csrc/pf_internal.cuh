@@ -41,12 +41,35 @@ struct KrylovScal {
   int pad;
 };
 
-// Reduction workspace: per-CTA partials (up to 4 values each) and the arrival counter.
+// Reduction workspace: per-CTA partials (up to 4 values each) and arrival counters
+// (counter[0] for groups, counter[1 + g] for the CTAs of group g), all kept at zero
+// between launches.
 struct RedWs {
   double *partials;   // 4 * max_blocks doubles
-  unsigned *counter;  // one counter, kept at zero between launches
+  unsigned *counter;  // red_counters(max_blocks) counters
   int max_blocks;
 };
+constexpr int RED_GROUP = 64;
+inline size_t red_counters(int max_blocks) { return 2 + (size_t)max_blocks / RED_GROUP; }
+
+#ifdef __CUDACC__
+// Arrival of CTA `bid` of `nblk` after it published its partials (thread 0 only).  CTAs
+// arrive in groups of RED_GROUP; the last CTA of a group arrives at the top counter, so
+// no single counter takes more than RED_GROUP atomics.  Returns true in exactly one CTA,
+// the last to arrive overall; counters are reset for the next launch.
+__device__ __forceinline__ bool red_arrive(unsigned *counter, unsigned bid, unsigned nblk) {
+  const unsigned g = bid / RED_GROUP;
+  const unsigned ng = (nblk + RED_GROUP - 1) / RED_GROUP;
+  const unsigned gsize = (g + 1) * RED_GROUP <= nblk ? RED_GROUP : nblk - g * RED_GROUP;
+  __threadfence();
+  if (atomicAdd(counter + 1 + g, 1u) != gsize - 1) return false;
+  counter[1 + g] = 0u;
+  __threadfence();
+  if (atomicAdd(counter, 1u) != ng - 1) return false;
+  counter[0] = 0u;
+  return true;
+}
+#endif
 
 // CTAs of a grid-wide reduction: two per SM of the current device (set once per
 // process from the device attributes).

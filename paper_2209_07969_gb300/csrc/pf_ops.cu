@@ -62,9 +62,7 @@ __device__ bool grid_reduce(double (&v)[NV], const RedWs ws, double (&tot)[NV],
       for (int w = 1; w < nw; ++w) s = is_max ? fmax(s, sh[k][w]) : s + sh[k][w];
       ws.partials[k * ws.max_blocks + bid] = s;
     }
-    __threadfence();
-    unsigned prev = atomicAdd(ws.counter, 1u);
-    am_last = (prev == nblk - 1);
+    am_last = red_arrive(ws.counter, bid, nblk);
   }
   __syncthreads();
   if (!am_last) return false;
@@ -88,7 +86,6 @@ __device__ bool grid_reduce(double (&v)[NV], const RedWs ws, double (&tot)[NV],
     for (int w = 1; w < nw; ++w) s = is_max ? fmax(s, sh[k][w]) : s + sh[k][w];
     tot[k] = s;
   }
-  *ws.counter = 0u;
   return true;
 }
 
@@ -598,7 +595,7 @@ void elas_apply(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, 
                 T *y, cudaStream_t st, KrylovScal *sc, const RedWs *ws, int epi) {
   RedWs w = ws ? *ws : RedWs{nullptr, nullptr, 0};
   const int e = ws ? epi : EPI_NONE;
-  k_elas<T, EL_APPLY><<<e == EPI_NONE ? tile_grid(g) : tile_grid_red(g), TILE_THREADS, 0, st>>>(
+  k_elas<T, EL_APPLY><<<tile_grid(g), TILE_THREADS, 0, st>>>(
       g, elem_const<T>(g, m), d, tens, x, y, nullptr, sc, w, e);
 }
 template <class T>
@@ -618,7 +615,7 @@ void damage_apply(const GridD &g, const T *c, double kappa, const T *x, T *y, cu
                   KrylovScal *sc, const RedWs *ws, int epi) {
   RedWs w = ws ? *ws : RedWs{nullptr, nullptr, 0};
   const int e = ws ? epi : EPI_NONE;
-  k_damage<T, T, DM_APPLY><<<e == EPI_NONE ? tile_grid(g) : tile_grid_red(g), TILE_THREADS, 0, st>>>(
+  k_damage<T, T, DM_APPLY><<<tile_grid(g), TILE_THREADS, 0, st>>>(
       g, elem_const<T>(g, MatD{}, kappa), c, x, y, sc, w, e);
 }
 template <class T>

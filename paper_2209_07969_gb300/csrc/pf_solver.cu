@@ -682,7 +682,7 @@ pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double 
     ctx->ws.max_blocks = (int)(tiles > 4096 ? tiles : 4096);
   }
   AL(ws.partials, 4 * ctx->ws.max_blocks);
-  AL(ws.counter, 1);
+  AL(ws.counter, red_counters(ctx->ws.max_blocks));
 #undef AL
   if (ctx->precond == PF_PRECOND_GMG) {
     cudaError_t e1, e2;
@@ -699,7 +699,8 @@ pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double 
   if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess)
     return fail(PF_ECUDA);
   cudaStream_t st = ctx->st;
-  bool okc = cudaMemsetAsync(ctx->ws.counter, 0, sizeof(unsigned), st) == cudaSuccess &&
+  bool okc = cudaMemsetAsync(ctx->ws.counter, 0, red_counters(ctx->ws.max_blocks) * sizeof(unsigned),
+                             st) == cudaSuccess &&
              cudaMemsetAsync(ctx->sc, 0, sizeof(KrylovScal), st) == cudaSuccess &&
              cudaMemcpyAsync(ctx->flags, mesh->node_flags, nn, cudaMemcpyHostToDevice, st) ==
                  cudaSuccess &&

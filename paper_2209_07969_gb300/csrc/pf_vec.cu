@@ -40,9 +40,7 @@ __device__ bool vgrid_reduce(double (&v)[NV], const RedWs ws, double (&tot)[NV],
       for (int w = 1; w < nw; ++w) s = is_max ? fmax(s, sh[k][w]) : s + sh[k][w];
       ws.partials[k * ws.max_blocks + bid] = s;
     }
-    __threadfence();
-    unsigned prev = atomicAdd(ws.counter, 1u);
-    am_last = (prev == nblk - 1);
+    am_last = red_arrive(ws.counter, bid, nblk);
   }
   __syncthreads();
   if (!am_last) return false;
@@ -66,7 +64,6 @@ __device__ bool vgrid_reduce(double (&v)[NV], const RedWs ws, double (&tot)[NV],
     for (int w = 1; w < nw; ++w) s = is_max ? fmax(s, sh[k][w]) : s + sh[k][w];
     tot[k] = s;
   }
-  *ws.counter = 0u;
   return true;
 }
 
