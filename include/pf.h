@@ -150,6 +150,21 @@ pf_status pf_sizes(const pf_ctx *ctx, int64_t *n_nodes, int64_t *n_elems, int64_
 /* Kernel launches issued by this context since creation (for accounting). */
 int64_t pf_launch_count(const pf_ctx *ctx);
 
+/* Host milliseconds accumulated per phase of pf_load_step since creation or the last
+ * reset: each phase ends in a stream synchronisation, so these are device-bound times
+ * plus launch gaps.  ms[i] for i < n (n <= PF_PROF_PHASES); reset != 0 zeroes them. */
+enum {
+  PF_PROF_U_SETUP = 0,  /* multigrid hierarchy builds for u */
+  PF_PROF_U_SOLVE = 1,  /* Newton corrections for u (Krylov + refinement), incl. setups */
+  PF_PROF_U_RESID = 2,  /* internal-force residual + norms per Newton iterate */
+  PF_PROF_D_SETUP = 3,  /* multigrid hierarchy builds for d */
+  PF_PROF_D_SOLVE = 4,  /* d linear solves (ST, augmented and frozen S-solves), incl. setups */
+  PF_PROF_STAG = 5,     /* staggered residual checks */
+  PF_PROF_TOTAL = 6,    /* whole load steps */
+  PF_PROF_PHASES = 8
+};
+pf_status pf_profile(pf_ctx *ctx, double *ms, int n, int reset);
+
 const char *pf_last_error(const pf_ctx *ctx);
 const char *pf_status_string(pf_status s);
 void pf_destroy(pf_ctx *ctx);

@@ -83,6 +83,7 @@ _PROTOS = {
     "pf_set_state": (S, [P, P, C.c_size_t]),
     "pf_sizes": (S, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "pf_launch_count": (C.c_int64, [P]),
+    "pf_profile": (S, [P, P, I, I]),
     "pf_last_error": (C.c_char_p, [P]),
     "pf_destroy": (None, [P]),
     "pf_op_dof_mask": (S, [I, I, P, P, P, P]),
@@ -209,6 +210,13 @@ class Simulation:
     def set_state(self, buf):
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         check(lib().pf_set_state(self.ctx, buf.ctypes.data, buf.size), "pf_set_state", self.ctx)
+
+    PHASES = ("u_setup", "u_solve", "u_resid", "d_setup", "d_solve", "stag", "total")
+
+    def profile(self, reset=False):
+        ms = np.zeros(8)
+        check(lib().pf_profile(self.ctx, ms.ctypes.data, 8, int(reset)), "pf_profile", self.ctx)
+        return dict(zip(self.PHASES, ms[:7].tolist()))
 
     def launches(self):
         return int(lib().pf_launch_count(self.ctx))

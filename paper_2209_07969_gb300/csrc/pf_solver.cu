@@ -14,6 +14,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <chrono>
 #include <new>
 #include <vector>
 
@@ -82,12 +83,24 @@ struct pf_ctx {
   GraphSlot graphs[4];
   bool use_graphs = true;
   MgState mg_u, mg_d;
+  double prof[PF_PROF_PHASES] = {0};   // host milliseconds per phase (pf_profile)
   double *dscal = nullptr;   // device scalars for norms / residual / reaction
   double *hbuf = nullptr;    // pinned host mirror
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 namespace {
+
+// Host time of a phase; every phase ends in a stream synchronisation (a scalar read or a
+// setup's host step), so host time equals device time of the phase plus launch gaps.
+struct PhaseTimer {
+  double *slot;
+  std::chrono::steady_clock::time_point t0;
+  explicit PhaseTimer(double *s) : slot(s), t0(std::chrono::steady_clock::now()) {}
+  ~PhaseTimer() {
+    *slot += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
 
 pf_status set_err(pf_ctx *c, pf_status s, const char *fmt, ...) {
   if (c) {
@@ -275,8 +288,13 @@ pf_status refine(pf_ctx *ctx, ApplyD applyd, Inner inner, size_t n, int ncomp, c
 // the solve misses it the hierarchy is rebuilt for the current operator and the solve
 // restarted.  setup() rebuilds; solve(maxit, &it, &ok) runs one Krylov solve.
 template <class Setup, class Solve>
-pf_status mg_solve(pf_ctx *ctx, MgState &S, bool mg, Setup setup, Solve solve, int *lin,
+pf_status mg_solve(pf_ctx *ctx, MgState &S, bool mg, Setup setup0, Solve solve, int *lin,
                    bool *ok) {
+  double *slot = (&S == &ctx->mg_u) ? &ctx->prof[PF_PROF_U_SETUP] : &ctx->prof[PF_PROF_D_SETUP];
+  auto setup = [&]() -> pf_status {
+    PhaseTimer tm(slot);
+    return setup0();
+  };
   bool fresh = false;
   if (mg && S.need()) {
     CKS(setup());
@@ -306,6 +324,7 @@ pf_status mg_solve(pf_ctx *ctx, MgState &S, bool mg, Setup setup, Solve solve, i
 // ---- u-solve ---------------------------------------------------------------------------
 // One Newton correction: K_t(d, tension) kx = kb on free DOFs.
 pf_status newton_correction(pf_ctx *ctx, int *lin, int *refines, bool *ok) {
+  PhaseTimer tm(&ctx->prof[PF_PROF_U_SOLVE]);
   cudaStream_t st = ctx->st;
   const size_t n = 2 * ctx->nn;
   const bool mg = ctx->precond == PF_PRECOND_GMG;
@@ -375,11 +394,14 @@ pf_status solve_u(pf_ctx *ctx, int *newton, int *lin, int *refines, bool *ok) {
     ctx->launches++;
   }
   for (int it = 0; it <= ctx->opt.max_newton; ++it) {
-    elas_residual(ctx->g, ctx->m, ctx->u, ctx->d, ctx->F, ctx->tens, st);
-    norms(n, 2, ctx->g.dofm, ctx->F, ctx->dscal, ctx->ws, st);
-    ctx->launches += 2;
-    CKS(check_launch(ctx));
-    CKS(read_scalars(ctx, ctx->dscal, 2 * sizeof(double)));
+    {
+      PhaseTimer tm(&ctx->prof[PF_PROF_U_RESID]);
+      elas_residual(ctx->g, ctx->m, ctx->u, ctx->d, ctx->F, ctx->tens, st);
+      norms(n, 2, ctx->g.dofm, ctx->F, ctx->dscal, ctx->ws, st);
+      ctx->launches += 2;
+      CKS(check_launch(ctx));
+      CKS(read_scalars(ctx, ctx->dscal, 2 * sizeof(double)));
+    }
     const double rn = sqrt(ctx->hbuf[0]), fref = sqrt(ctx->hbuf[1]);
     if (r0 < 0.0) r0 = rn;
     if (rn == 0.0 || rn <= ctx->opt.tol_nr * fmax(r0, fref)) {
@@ -406,6 +428,7 @@ pf_status solve_u(pf_ctx *ctx, int *newton, int *lin, int *refines, bool *ok) {
 // point, copied into the fixed coefficient buffer the captured graphs read.
 pf_status solve_damage(pf_ctx *ctx, const double *c, const double *rhs, double *x, int *lin,
                        int *refines, bool *ok) {
+  PhaseTimer tm(&ctx->prof[PF_PROF_D_SOLVE]);
   cudaStream_t st = ctx->st;
   const size_t n = ctx->nn;
   const double kappa = ctx->m.Gc * ctx->m.l;
@@ -526,6 +549,7 @@ pf_status d_step(pf_ctx *ctx, int scheme, int *lin, int *refines, int *dsolves, 
 }
 
 pf_status stag_residual(pf_ctx *ctx, double *out) {
+  PhaseTimer tm(&ctx->prof[PF_PROF_STAG]);
   cudaStream_t st = ctx->st;
   const double gcl = ctx->m.Gc / ctx->m.l;
   const double kappa = ctx->m.Gc * ctx->m.l;
@@ -765,6 +789,7 @@ pf_status pf_load_step(pf_ctx *ctx, double d_ubar, int scheme, double tol,
   if (scheme < PF_ST || scheme > PF_S3 || !(tol > 0) || !isfinite(d_ubar))
     return set_err(ctx, PF_EINVAL, "invalid scheme/tol/d_ubar");
   CK(cudaSetDevice(ctx->device));
+  PhaseTimer tm_all(&ctx->prof[PF_PROF_TOTAL]);
   pf_step_result r;
   memset(&r, 0, sizeof(r));
   cudaStream_t st = ctx->st;
@@ -890,6 +915,14 @@ pf_status pf_sizes(const pf_ctx *ctx, int64_t *n_nodes, int64_t *n_elems, int64_
 }
 
 int64_t pf_launch_count(const pf_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+pf_status pf_profile(pf_ctx *ctx, double *ms, int n, int reset) {
+  if (!ctx || (n > 0 && !ms) || n < 0) return PF_EINVAL;
+  for (int i = 0; i < n && i < PF_PROF_PHASES; ++i) ms[i] = ctx->prof[i];
+  if (reset)
+    for (double &v : ctx->prof) v = 0.0;
+  return PF_OK;
+}
 
 const char *pf_last_error(const pf_ctx *ctx) { return ctx ? ctx->err : "null context"; }
 
