@@ -260,6 +260,28 @@ pf_status pf_op_stag_residual(const pf_grid *g, const pf_material *m, const doub
                               const double *d, const double *Hprev, double *out,
                               void *stream);
 
+/* Allocation-free variant of pf_op_stag_residual (the paper has no counterpart; this is
+ * an interface convenience).  pf_op_stag_residual allocates and frees device scratch on
+ * every call, which some callers cannot do: code whose device memory is owned by another
+ * allocator (a framework's caching pool with a fixed budget), and code that must not
+ * stall the device, since cudaMalloc and cudaFree can synchronise it.  This variant takes
+ * the same inputs and gives the same result, but keeps its scratch in a static device
+ * array of PF_NOALLOC_MAX_DOUBLES doubles (about 12 MiB) that every GPU which loads the
+ * library holds until the process exits.  It calls no allocation routine.
+ *   Size limit: 2*Q + 3*N <= PF_NOALLOC_MAX_DOUBLES (Q = 4*nx*ny Gauss points, N nodes),
+ *   about 136,000 elements (e.g. 368 x 368); larger grids return PF_EINVAL before any
+ *   GPU work.
+ *   First call on a device: resolves the scratch address with cudaGetSymbolAddress while
+ *   that device is current; make that first call before any stream capture.
+ *   Sharing: every call on a device uses the same scratch, and the last call's contents
+ *   stay there; calls whose work overlaps on the GPU (different streams or threads at the
+ *   same time) race and must be serialised by the caller.
+ * Synchronises `stream`; the result goes to *out (host). */
+#define PF_NOALLOC_MAX_DOUBLES 1500000
+pf_status pf_op_stag_residual_noalloc(const pf_grid *g, const pf_material *m, const double *u,
+                                      const double *d, const double *Hprev, double *out,
+                                      void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -98,7 +98,10 @@ _PROTOS = {
     "pf_op_fs_predict": (S, [C.POINTER(Grid), C.POINTER(Material), I, P, P, P, P, P, P, P]),
     "pf_op_reaction": (S, [C.POINTER(Grid), P, P, I, C.POINTER(D), P]),
     "pf_op_stag_residual": (S, [C.POINTER(Grid), C.POINTER(Material), P, P, P, C.POINTER(D), P]),
+    "pf_op_stag_residual_noalloc": (S, [C.POINTER(Grid), C.POINTER(Material), P, P, P,
+                                        C.POINTER(D), P]),
 }
+NOALLOC_MAX_DOUBLES = 1500000
 
 
 def lib():

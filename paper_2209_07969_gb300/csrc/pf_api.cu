@@ -1,6 +1,8 @@
 // Operator-level C ABI of libpf: single operations on caller-owned device arrays.
 #include <math.h>
 
+#include <mutex>
+
 #include "pf_internal.cuh"
 #include "pf_vec.cuh"
 
@@ -193,3 +195,79 @@ pf_status pf_op_stag_residual(const pf_grid *g, const pf_material *m, const doub
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------
+// Allocation-free staggered residual.  Its scratch lives in file-scope device arrays
+// that every GPU loading the library holds until the process exits.  Host code may not
+// use the arrays' names as device addresses: the first call on a device resolves their
+// addresses with cudaGetSymbolAddress while that device is current.
+// ------------------------------------------------------------------------------------
+namespace {
+
+constexpr int NOALLOC_BLOCKS = 1024;  // reduction partial slots (>= 2 CTAs per SM)
+constexpr size_t NOALLOC_FIELD_DOUBLES = PF_NOALLOC_MAX_DOUBLES;
+constexpr size_t NOALLOC_DOUBLES = 4 * NOALLOC_BLOCKS + 2 + NOALLOC_FIELD_DOUBLES;
+constexpr size_t NOALLOC_COUNTERS = 2 + NOALLOC_BLOCKS / RED_GROUP;
+
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+static __device__ __align__(256) unsigned g_noalloc_counters[NOALLOC_COUNTERS];
+
+struct NoallocPtrs {
+  double *scratch = nullptr;
+  unsigned *counters = nullptr;
+};
+std::mutex g_noalloc_mx;
+NoallocPtrs g_noalloc_dev[64];
+
+// Device addresses of the static scratch on the current device (resolved once).
+pf_status noalloc_ptrs(NoallocPtrs *out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PF_ECUDA;
+  std::lock_guard<std::mutex> lk(g_noalloc_mx);
+  NoallocPtrs &p = g_noalloc_dev[dev];
+  if (!p.scratch) {
+    void *a = nullptr, *b = nullptr;
+    if (cudaGetSymbolAddress(&a, g_noalloc_scratch) != cudaSuccess) return PF_ECUDA;
+    if (cudaGetSymbolAddress(&b, g_noalloc_counters) != cudaSuccess) return PF_ECUDA;
+    p.scratch = (double *)a;
+    p.counters = (unsigned *)b;
+  }
+  *out = p;
+  return PF_OK;
+}
+
+}  // namespace
+
+extern "C" pf_status pf_op_stag_residual_noalloc(const pf_grid *g, const pf_material *m,
+                                                 const double *u, const double *d,
+                                                 const double *Hprev, double *out,
+                                                 void *stream) {
+  if (!grid_ok(g) || !mat_ok(m) || !u || !d || !Hprev || !out) return PF_EINVAL;
+  const size_t nn = (size_t)(g->nx + 1) * (g->ny + 1), nq = (size_t)4 * g->nx * g->ny;
+  if (2 * nq + 3 * nn > NOALLOC_FIELD_DOUBLES) return PF_EINVAL;  // beyond the static scratch
+  NoallocPtrs P;
+  pf_status st = noalloc_ptrs(&P);
+  if (st != PF_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  // arrival counters must start at zero; the partial sums need no clearing
+  if (cudaMemsetAsync(P.counters, 0, NOALLOC_COUNTERS * sizeof(unsigned), cs) != cudaSuccess)
+    return PF_ECUDA;
+  RedWs ws{P.scratch, P.counters, NOALLOC_BLOCKS};
+  double *res = P.scratch + 4 * NOALLOC_BLOCKS;
+  double *H = res + 2, *c = H + nq, *Kd = c + nq, *b = Kd + nn, *diag = b + nn;
+  GridD gd = to_dev(g);
+  GridD gfull = gd;
+  gfull.dofm = nullptr;
+  MatD md = to_dev(m);
+  qp_energy(gd, md, u, Hprev, nullptr, H, cs);
+  coef<double>(nq, m->Gc / m->l, H, c, cs);
+  damage_rhs(gd, H, b, cs);
+  damage_apply<double>(gfull, c, m->Gc * m->l, d, Kd, cs);
+  damage_diag<double>(gfull, c, m->Gc * m->l, diag, cs);
+  stag_max(nn, gd.dofm, Kd, b, diag, res, ws, cs);
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(out, res, sizeof(double), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+      cudaStreamSynchronize(cs) != cudaSuccess)
+    return PF_ECUDA;
+  return PF_OK;
+}
