@@ -1,11 +1,12 @@
 // Matrix-free Q1 operators and per-Gauss-point kernels of the staggered phase-field
 // method (arXiv 2209.07969), written for sm_103a.
 //
-// Operator kernels use one 256-thread CTA per tile of TX x TY nodes.  The CTA stages
-// the (TX+2) x (TY+2) node patch in shared memory, computes the element vectors of the
-// (TX+1) x (TY+1) elements that touch its nodes (the one-element halo is recomputed by
-// the neighbouring CTA as well), and sums the four element contributions of every
-// owned node.  No atomics: results are deterministic and independent of the launch.
+// Operator kernels use one 256-thread CTA per tile of TX x TY = 31 x 7 nodes.  The CTA
+// stages the (TX+2) x (TY+2) node patch in shared memory, computes the element vectors
+// of the (TX+1) x (TY+1) = 256 elements that touch its nodes, one per thread (the
+// one-element halo is recomputed by the neighbouring CTA as well), and sums the four
+// element contributions of every owned node.  No atomics: results are deterministic and
+// independent of the launch.
 //
 // Element quantities (Sec. 2 and 3.2): 2x2 Gauss points at unit coordinates
 // s, t in {G0, G1} = {(1 - 1/sqrt3)/2, (1 + 1/sqrt3)/2}; N_a bilinear; weight hx hy/4.
@@ -21,6 +22,18 @@ __device__ __forceinline__ double gp_hi() { return 0.78867513459481288225; }  //
 
 template <class T>
 __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+// Both displacement components of node n (interleaved storage) in one vector load.
+__device__ __forceinline__ void ld_pair(const float *x, size_t n, float &a, float &b) {
+  const float2 v = __ldg(reinterpret_cast<const float2 *>(x) + n);
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void ld_pair(const double *x, size_t n, double &a, double &b) {
+  const double2 v = __ldg(reinterpret_cast<const double2 *>(x) + n);
+  a = v.x;
+  b = v.y;
+}
 
 // ------------------------------------------------------------------------------------
 // Reductions: warp shuffle -> CTA -> per-CTA partials -> last-arriving CTA sums the
@@ -148,8 +161,7 @@ k_elas(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restr
     if (in) {
       vd = ldg(d + n);
       if (MODE != EL_DIAG) {
-        vx = ldg(x + 2 * n);
-        vy = ldg(x + 2 * n + 1);
+        ld_pair(x, n, vx, vy);
         if (MODE == EL_APPLY && g.dofm) {
           const uint8_t mk = ldg(g.dofm + n);
           if (mk & 1) vx = T(0);
@@ -244,7 +256,7 @@ k_elas(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restr
 
   const int li = threadIdx.x % TX, lj = threadIdx.x / TX;
   const int gi = i0 + li, gj = j0 + lj;
-  if (gi <= nx && gj <= ny) {
+  if (lj < TY && gi <= nx && gj <= ny) {
     const int e00 = lj * EX + li, e10 = e00 + 1, e01 = e00 + EX, e11 = e01 + 1;
     T fx = ef[6][e00] + ef[4][e10] + ef[2][e01] + ef[0][e11];
     T fy = ef[7][e00] + ef[5][e10] + ef[3][e01] + ef[1][e11];
@@ -353,7 +365,7 @@ k_damage(GridD g, ElemConst<T> kc, const C *__restrict__ c, const T *__restrict_
   __syncthreads();
   const int li = threadIdx.x % TX, lj = threadIdx.x / TX;
   const int gi = i0 + li, gj = j0 + lj;
-  if (gi <= nx && gj <= ny) {
+  if (lj < TY && gi <= nx && gj <= ny) {
     const int e00 = lj * EX + li, e10 = e00 + 1, e01 = e00 + EX, e11 = e01 + 1;
     T v = ef[3][e00] + ef[2][e10] + ef[1][e01] + ef[0][e11];
     const size_t n = (size_t)gj * ld + gi;

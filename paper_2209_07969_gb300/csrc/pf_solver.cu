@@ -45,6 +45,7 @@ struct GraphSlot {
   cudaGraphExec_t exec = nullptr;
   int launches = 0;
   size_t n = 0;
+  int every = 0;
 };
 
 struct pf_ctx {
@@ -192,12 +193,24 @@ pf_status pcg(pf_ctx *ctx, int slot, Apply apply, Fine fine, Gmg<T> *G, size_t n
     }
     return nl;
   };
+  // One graph holds `every` iterations followed by the read-back of ||r||^2 and the
+  // breakdown flag, so the host launches once and synchronises once per check.
+  const int every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 8;
+  auto batch = [&]() -> int {
+    int nl = 0;
+    for (int k = 0; k < every; ++k) nl += body();
+    cudaMemcpyAsync(ctx->hbuf, &ctx->sc->rr, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(ctx->hbuf + 1, &ctx->sc->breakdown, sizeof(int), cudaMemcpyDeviceToHost, st);
+    return nl;
+  };
   const int sidx = slot * 2 + (G ? 1 : 0);
   GraphSlot &S = ctx->graphs[sidx];
-  if (ctx->use_graphs && !S.exec) {
+  if (ctx->use_graphs && (!S.exec || S.every != every)) {
+    if (S.exec) cudaGraphExecDestroy(S.exec);
+    S.exec = nullptr;
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    S.launches = body();
+    S.launches = batch();
     cudaError_t e = cudaStreamEndCapture(st, &graph);
     if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
     e = cudaGraphInstantiate(&S.exec, graph, 0);
@@ -207,34 +220,29 @@ pf_status pcg(pf_ctx *ctx, int slot, Apply apply, Fine fine, Gmg<T> *G, size_t n
       return set_err(ctx, PF_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
     }
     S.n = n;
+    S.every = every;
   }
   const double target = rtol * rtol * rr0;
-  const int every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 8;
   int it = 0;
   *ok = false;
   while (it < maxit) {
     if (S.exec) {
       CK(cudaGraphLaunch(S.exec, st));
-      ctx->launches += S.launches;
     } else {
-      ctx->launches += body();
+      S.launches = batch();
     }
-    ++it;
-    if (it % every == 0 || it == maxit) {
-      CKS(check_launch(ctx));
-      CK(cudaMemcpyAsync(ctx->hbuf, &ctx->sc->rr, sizeof(double), cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(ctx->hbuf + 1, &ctx->sc->breakdown, sizeof(int), cudaMemcpyDeviceToHost,
-                         st));
-      CK(cudaStreamSynchronize(st));
-      const double rr = ctx->hbuf[0];
-      int bd;
-      memcpy(&bd, ctx->hbuf + 1, sizeof(int));
-      if (rr <= target) {
-        *ok = true;
-        break;
-      }
-      if (bd || !isfinite(rr)) break;
+    ctx->launches += S.launches;
+    it += every;
+    CKS(check_launch(ctx));
+    CK(cudaStreamSynchronize(st));
+    const double rr = ctx->hbuf[0];
+    int bd;
+    memcpy(&bd, ctx->hbuf + 1, sizeof(int));
+    if (rr <= target) {
+      *ok = true;
+      break;
     }
+    if (bd || !isfinite(rr)) break;
   }
   *iters = it;
   return PF_OK;
