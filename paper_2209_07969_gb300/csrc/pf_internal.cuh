@@ -8,11 +8,11 @@
 namespace pf {
 
 // Element tile owned by one 256-thread CTA: TX x TY nodes; the CTA computes the
-// (TX+1) x (TY+1) = 256 elements touching them, one per thread (the one-element halo is
-// recomputed by the neighbouring CTA as well), so the nodal gather needs no atomics.
-constexpr int TX = 31;
-constexpr int TY = 7;
-constexpr int TILE_THREADS = (TX + 1) * (TY + 1);
+// (TX+1) x (TY+1) elements touching them (the one-element halo is recomputed by the
+// neighbouring CTA as well), so the nodal gather needs no atomics.
+constexpr int TX = 32;
+constexpr int TY = 8;
+constexpr int TILE_THREADS = 256;
 // Thread count of the element-wise and vector kernels.
 constexpr int VEC_THREADS = 256;
 

@@ -1,12 +1,13 @@
 // Matrix-free Q1 operators and per-Gauss-point kernels of the staggered phase-field
 // method (arXiv 2209.07969), written for sm_103a.
 //
-// Operator kernels use one 256-thread CTA per tile of TX x TY = 31 x 7 nodes.  The CTA
+// Operator kernels use one 256-thread CTA per tile of TX x TY = 32 x 8 nodes.  The CTA
 // stages the (TX+2) x (TY+2) node patch in shared memory, computes the element vectors
-// of the (TX+1) x (TY+1) = 256 elements that touch its nodes, one per thread (the
-// one-element halo is recomputed by the neighbouring CTA as well), and sums the four
-// element contributions of every owned node.  No atomics: results are deterministic and
-// independent of the launch.
+// of the (TX+1) x (TY+1) elements that touch its nodes (the one-element halo is
+// recomputed by the neighbouring CTA as well), and sums the four element contributions
+// of every owned node.  No atomics: results are deterministic and independent of the
+// launch.  The CTAs are register-limited to fill the GPU in one wave at the 512 x 512
+// size (8 CTAs of 256 threads per SM).
 //
 // Element quantities (Sec. 2 and 3.2): 2x2 Gauss points at unit coordinates
 // s, t in {G0, G1} = {(1 - 1/sqrt3)/2, (1 + 1/sqrt3)/2}; N_a bilinear; weight hx hy/4.
@@ -138,7 +139,7 @@ static ElemConst<T> elem_const(const GridD &g, const MatD &m, double kappa = 0.0
 enum { EL_APPLY = 0, EL_DIAG = 1, EL_RESID = 2 };
 
 template <class T, int MODE>
-__global__ void __launch_bounds__(TILE_THREADS)
+__global__ void __launch_bounds__(TILE_THREADS, sizeof(T) == 4 ? 8 : 4)
 k_elas(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restrict__ tens_in,
        const T *__restrict__ x, T *__restrict__ y, uint8_t *__restrict__ tens_out,
        KrylovScal *sc, RedWs ws, int epi) {
@@ -199,14 +200,14 @@ k_elas(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restr
         uy0 = sx[1][p0]; uy1 = sx[1][p1]; uy2 = sx[1][p2]; uy3 = sx[1][p3];
       }
       uint8_t tb = (MODE == EL_RESID) ? 0 : ldg(tens_in + e);
+      if (MODE == EL_DIAG) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const T s = (q & 1) ? G1 : G0, tt = (q & 2) ? G1 : G0;
-        const T s1 = T(1) - s, t1 = T(1) - tt;
-        const T dq = s1 * t1 * d0 + s * t1 * d1 + s1 * tt * d2 + s * tt * d3;
-        const T om = T(1) - dq;
-        const T gq = om * om + eta;
-        if (MODE == EL_DIAG) {
+        for (int q = 0; q < 4; ++q) {
+          const T s = (q & 1) ? G1 : G0, tt = (q & 2) ? G1 : G0;
+          const T s1 = T(1) - s, t1 = T(1) - tt;
+          const T dq = s1 * t1 * d0 + s * t1 * d1 + s1 * tt * d2 + s * tt * d3;
+          const T om = T(1) - dq;
+          const T gq = om * om + eta;
           const T kv = ((tb >> q) & 1) ? gq * K : K;
           const T Dn = gq * T(2) * mu * (T(1) - cd) + kv;  // D00 = D11
           const T Ds = gq * mu;                              // D22
@@ -218,12 +219,31 @@ k_elas(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restr
             f[2 * a] += w * (Dn * ax[a] * ax[a] + Ds * ay[a] * ay[a]);
             f[2 * a + 1] += w * (Dn * ay[a] * ay[a] + Ds * ax[a] * ax[a]);
           }
-        } else {
-          const T exx = (t1 * (ux1 - ux0) + tt * (ux3 - ux2)) * ihx;
-          const T eyy = (s1 * (uy2 - uy0) + s * (uy3 - uy1)) * ihy;
-          const T gxy = (s1 * (ux2 - ux0) + s * (ux3 - ux1)) * ihy +
-                        (t1 * (uy1 - uy0) + tt * (uy3 - uy2)) * ihx;
-          const T tr = exx + eyy;
+        }
+      } else {
+        // Gauss point q has s = G[q & 1], t = G[q >> 1] with G0 + G1 = 1, so the strain
+        // components and the interpolated d separate into values per s and per t, and
+        // the element force into sums over the two points of equal s or equal t.
+        const T dxb = ux1 - ux0, dxt = ux3 - ux2, dyl = uy2 - uy0, dyr = uy3 - uy1;
+        const T uyb = uy1 - uy0, uyt = uy3 - uy2, uxl = ux2 - ux0, uxr = ux3 - ux1;
+        const T exx_lo = (G1 * dxb + G0 * dxt) * ihx, exx_hi = (G0 * dxb + G1 * dxt) * ihx;
+        const T eyy_l = (G1 * dyl + G0 * dyr) * ihy, eyy_r = (G0 * dyl + G1 * dyr) * ihy;
+        const T uxy_l = (G1 * uxl + G0 * uxr) * ihy, uxy_r = (G0 * uxl + G1 * uxr) * ihy;
+        const T uyx_lo = (G1 * uyb + G0 * uyt) * ihx, uyx_hi = (G0 * uyb + G1 * uyt) * ihx;
+        const T dbl = G1 * d0 + G0 * d1, dbr = G0 * d0 + G1 * d1;
+        const T dtl = G1 * d2 + G0 * d3, dtr = G0 * d2 + G1 * d3;
+        const T dqv[4] = {G1 * dbl + G0 * dtl, G1 * dbr + G0 * dtr, G0 * dbl + G1 * dtl,
+                          G0 * dbr + G1 * dtr};
+        const T exv[4] = {exx_lo, exx_lo, exx_hi, exx_hi};
+        const T eyv[4] = {eyy_l, eyy_r, eyy_l, eyy_r};
+        const T gxv[4] = {uxy_l + uyx_lo, uxy_r + uyx_lo, uxy_l + uyx_hi, uxy_r + uyx_hi};
+        T P[4], Q[4], R[4], U[4];
+        const T wx = w * ihx, wy = w * ihy;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const T om = T(1) - dqv[q];
+          const T gq = om * om + eta;
+          const T exx = exv[q], eyy = eyv[q], tr = exx + eyy;
           T vol;
           if (MODE == EL_RESID) {
             vol = tr > T(0) ? gq * K * tr : K * tr;
@@ -232,20 +252,27 @@ k_elas(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restr
             vol = ((tb >> q) & 1) ? gq * K * tr : K * tr;
           }
           const T gm2 = gq * T(2) * mu;
-          const T sxx = gm2 * (exx - cd * tr) + vol;
-          const T syy = gm2 * (eyy - cd * tr) + vol;
-          const T sxy = gq * mu * gxy;
-          const T Ax = w * ihx * sxx, Ay = w * ihy * sxy;
-          const T Bx = w * ihx * sxy, By = w * ihy * syy;
-          f[0] += -t1 * Ax - s1 * Ay;
-          f[1] += -t1 * Bx - s1 * By;
-          f[2] += t1 * Ax - s * Ay;
-          f[3] += t1 * Bx - s * By;
-          f[4] += -tt * Ax + s1 * Ay;
-          f[5] += -tt * Bx + s1 * By;
-          f[6] += tt * Ax + s * Ay;
-          f[7] += tt * Bx + s * By;
+          const T sxy = gq * mu * gxv[q];
+          P[q] = wx * (gm2 * (exx - cd * tr) + vol);   // w dN/dx-weight * sxx
+          U[q] = wy * (gm2 * (eyy - cd * tr) + vol);   // w dN/dy-weight * syy
+          Q[q] = wy * sxy;
+          R[q] = wx * sxy;
         }
+        // t-sums (points 0,1 have t = G0; 2,3 have t = G1), s-sums (0,2: G0; 1,3: G1)
+        const T Plo = P[0] + P[1], Phi = P[2] + P[3], Rlo = R[0] + R[1], Rhi = R[2] + R[3];
+        const T Ql = Q[0] + Q[2], Qr = Q[1] + Q[3], Ul = U[0] + U[2], Ur = U[1] + U[3];
+        const T P1 = G1 * Plo + G0 * Phi, P2 = G0 * Plo + G1 * Phi;   // sum (1-t) P, sum t P
+        const T R1 = G1 * Rlo + G0 * Rhi, R2 = G0 * Rlo + G1 * Rhi;
+        const T Q1 = G1 * Ql + G0 * Qr, Q2 = G0 * Ql + G1 * Qr;       // sum (1-s) Q, sum s Q
+        const T U1 = G1 * Ul + G0 * Ur, U2 = G0 * Ul + G1 * Ur;
+        f[0] = -P1 - Q1;
+        f[1] = -R1 - U1;
+        f[2] = P1 - Q2;
+        f[3] = R1 - U2;
+        f[4] = -P2 + Q1;
+        f[5] = -R2 + U1;
+        f[6] = P2 + Q2;
+        f[7] = R2 + U2;
       }
       if (MODE == EL_RESID && tens_out) tens_out[e] = tb;
     }
@@ -287,7 +314,7 @@ k_elas(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restr
 enum { DM_APPLY = 0, DM_DIAG = 1, DM_RHS = 2 };
 
 template <class T, class C, int MODE>
-__global__ void __launch_bounds__(TILE_THREADS)
+__global__ void __launch_bounds__(TILE_THREADS, sizeof(T) == 4 ? 8 : 4)
 k_damage(GridD g, ElemConst<T> kc, const C *__restrict__ c, const T *__restrict__ x,
          T *__restrict__ y, KrylovScal *sc, RedWs ws, int epi) {
   constexpr int PX = TX + 2, PY = TY + 2, EX = TX + 1, EY = TY + 1, NE = EX * EY;
@@ -331,32 +358,45 @@ k_damage(GridD g, ElemConst<T> kc, const C *__restrict__ c, const T *__restrict_
         const int p0 = me * PX + le;
         x0 = sxv[p0]; x1 = sxv[p0 + 1]; x2 = sxv[p0 + PX]; x3 = sxv[p0 + PX + 1];
       }
+      if (MODE != DM_APPLY) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const T s = (q & 1) ? G1 : G0, tt = (q & 2) ? G1 : G0;
-        const T s1 = T(1) - s, t1 = T(1) - tt;
-        const T N[4] = {s1 * t1, s * t1, s1 * tt, s * tt};
-        const T cq = T(ldg(c + 4 * e + q));
-        if (MODE == DM_RHS) {
+        for (int q = 0; q < 4; ++q) {
+          const T s = (q & 1) ? G1 : G0, tt = (q & 2) ? G1 : G0;
+          const T s1 = T(1) - s, t1 = T(1) - tt;
+          const T N[4] = {s1 * t1, s * t1, s1 * tt, s * tt};
+          const T cq = T(ldg(c + 4 * e + q));
+          if (MODE == DM_RHS) {
 #pragma unroll
-          for (int a = 0; a < 4; ++a) f[a] += w * T(2) * cq * N[a];
-        } else if (MODE == DM_DIAG) {
-          const T ax[4] = {t1 * ihx, t1 * ihx, tt * ihx, tt * ihx};
-          const T ay[4] = {s1 * ihy, s * ihy, s1 * ihy, s * ihy};
+            for (int a = 0; a < 4; ++a) f[a] += w * T(2) * cq * N[a];
+          } else {
+            const T ax[4] = {t1 * ihx, t1 * ihx, tt * ihx, tt * ihx};
+            const T ay[4] = {s1 * ihy, s * ihy, s1 * ihy, s * ihy};
 #pragma unroll
-          for (int a = 0; a < 4; ++a)
-            f[a] += w * (cq * N[a] * N[a] + kappa * (ax[a] * ax[a] + ay[a] * ay[a]));
-        } else {
-          const T xq = N[0] * x0 + N[1] * x1 + N[2] * x2 + N[3] * x3;
-          const T gx = (t1 * (x1 - x0) + tt * (x3 - x2)) * ihx;
-          const T gy = (s1 * (x2 - x0) + s * (x3 - x1)) * ihy;
-          const T m = w * cq * xq, kx = w * kappa * gx * ihx, ky = w * kappa * gy * ihy;
-          // dN/dx * ihx^-1: (-t1, t1, -tt, tt); dN/dy * ihy^-1: (-s1, -s, s1, s)
-          f[0] += m * N[0] - t1 * kx - s1 * ky;
-          f[1] += m * N[1] + t1 * kx - s * ky;
-          f[2] += m * N[2] - tt * kx + s1 * ky;
-          f[3] += m * N[3] + tt * kx + s * ky;
+            for (int a = 0; a < 4; ++a)
+              f[a] += w * (cq * N[a] * N[a] + kappa * (ax[a] * ax[a] + ay[a] * ay[a]));
+          }
         }
+      } else {
+        // separable form over the Gauss points (s = G[q & 1], t = G[q >> 1], G0 + G1 = 1)
+        const T xbl = G1 * x0 + G0 * x1, xbr = G0 * x0 + G1 * x1;
+        const T xtl = G1 * x2 + G0 * x3, xtr = G0 * x2 + G1 * x3;
+        const T xq[4] = {G1 * xbl + G0 * xtl, G1 * xbr + G0 * xtr, G0 * xbl + G1 * xtl,
+                         G0 * xbr + G1 * xtr};
+        T m[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) m[q] = w * T(ldg(c + 4 * e + q)) * xq[q];
+        const T ml_lo = G1 * m[0] + G0 * m[1], mr_lo = G0 * m[0] + G1 * m[1];
+        const T ml_hi = G1 * m[2] + G0 * m[3], mr_hi = G0 * m[2] + G1 * m[3];
+        const T bx = x1 - x0, tx = x3 - x2, ly = x2 - x0, ry = x3 - x1;
+        const T gx_lo = G1 * bx + G0 * tx, gx_hi = G0 * bx + G1 * tx;   // times ihx
+        const T gy_l = G1 * ly + G0 * ry, gy_r = G0 * ly + G1 * ry;     // times ihy
+        const T cxx = T(2) * w * kappa * ihx * ihx, cyy = T(2) * w * kappa * ihy * ihy;
+        const T kx1 = cxx * (G1 * gx_lo + G0 * gx_hi), kx2 = cxx * (G0 * gx_lo + G1 * gx_hi);
+        const T ky1 = cyy * (G1 * gy_l + G0 * gy_r), ky2 = cyy * (G0 * gy_l + G1 * gy_r);
+        f[0] = G1 * ml_lo + G0 * ml_hi - kx1 - ky1;
+        f[1] = G1 * mr_lo + G0 * mr_hi + kx1 - ky2;
+        f[2] = G0 * ml_lo + G1 * ml_hi - kx2 + ky1;
+        f[3] = G0 * mr_lo + G1 * mr_hi + kx2 + ky2;
       }
     }
 #pragma unroll
