@@ -136,6 +136,69 @@ static ElemConst<T> elem_const(const GridD &g, const MatD &m, double kappa = 0.0
 // ------------------------------------------------------------------------------------
 // Elasticity: tangent apply, tangent diagonal, nonlinear internal force.
 // ------------------------------------------------------------------------------------
+// Element force of the Q1 elasticity element with nodal values (a0..a3 = (i,j), (i+1,j),
+// (i,j+1), (i+1,j+1)): f[2a] / f[2a+1] = x / y force on node a.  RESID: nonlinear
+// stress, tension bits written to tb; otherwise the frozen-indicator tangent with bits tb.
+// Gauss point q has s = G[q & 1], t = G[q >> 1] with G0 + G1 = 1, so strains and the
+// interpolated d separate into values per s and per t, and the force into sums over the
+// two points of equal s or equal t.
+template <class T, bool RESID>
+__device__ __forceinline__ void elas_element(const ElemConst<T> &kc, T ux0, T ux1, T ux2, T ux3,
+                                             T uy0, T uy1, T uy2, T uy3, T d0, T d1, T d2, T d3,
+                                             uint8_t &tb, T (&f)[8]) {
+  const T G0 = kc.G0, G1 = kc.G1, ihx = kc.ihx, ihy = kc.ihy;
+  const T mu = kc.mu, K = kc.K, cd = kc.cd, eta = kc.eta;
+  const T dxb = ux1 - ux0, dxt = ux3 - ux2, dyl = uy2 - uy0, dyr = uy3 - uy1;
+  const T uyb = uy1 - uy0, uyt = uy3 - uy2, uxl = ux2 - ux0, uxr = ux3 - ux1;
+  const T exx_lo = (G1 * dxb + G0 * dxt) * ihx, exx_hi = (G0 * dxb + G1 * dxt) * ihx;
+  const T eyy_l = (G1 * dyl + G0 * dyr) * ihy, eyy_r = (G0 * dyl + G1 * dyr) * ihy;
+  const T uxy_l = (G1 * uxl + G0 * uxr) * ihy, uxy_r = (G0 * uxl + G1 * uxr) * ihy;
+  const T uyx_lo = (G1 * uyb + G0 * uyt) * ihx, uyx_hi = (G0 * uyb + G1 * uyt) * ihx;
+  const T dbl = G1 * d0 + G0 * d1, dbr = G0 * d0 + G1 * d1;
+  const T dtl = G1 * d2 + G0 * d3, dtr = G0 * d2 + G1 * d3;
+  const T dqv[4] = {G1 * dbl + G0 * dtl, G1 * dbr + G0 * dtr, G0 * dbl + G1 * dtl,
+                    G0 * dbr + G1 * dtr};
+  const T exv[4] = {exx_lo, exx_lo, exx_hi, exx_hi};
+  const T eyv[4] = {eyy_l, eyy_r, eyy_l, eyy_r};
+  const T gxv[4] = {uxy_l + uyx_lo, uxy_r + uyx_lo, uxy_l + uyx_hi, uxy_r + uyx_hi};
+  T P[4], Q[4], R[4], U[4];
+  const T wx = kc.w * ihx, wy = kc.w * ihy;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const T om = T(1) - dqv[q];
+    const T gq = om * om + eta;
+    const T exx = exv[q], eyy = eyv[q], tr = exx + eyy;
+    T vol;
+    if (RESID) {
+      vol = tr > T(0) ? gq * K * tr : K * tr;
+      if (tr > T(0)) tb |= (uint8_t)(1u << q);
+    } else {
+      vol = ((tb >> q) & 1) ? gq * K * tr : K * tr;
+    }
+    const T gm2 = gq * T(2) * mu;
+    const T sxy = gq * mu * gxv[q];
+    P[q] = wx * (gm2 * (exx - cd * tr) + vol);
+    U[q] = wy * (gm2 * (eyy - cd * tr) + vol);
+    Q[q] = wy * sxy;
+    R[q] = wx * sxy;
+  }
+  // t-sums (points 0,1 have t = G0; 2,3 have t = G1), s-sums (0,2: G0; 1,3: G1)
+  const T Plo = P[0] + P[1], Phi = P[2] + P[3], Rlo = R[0] + R[1], Rhi = R[2] + R[3];
+  const T Ql = Q[0] + Q[2], Qr = Q[1] + Q[3], Ul = U[0] + U[2], Ur = U[1] + U[3];
+  const T P1 = G1 * Plo + G0 * Phi, P2 = G0 * Plo + G1 * Phi;   // sum (1-t) P, sum t P
+  const T R1 = G1 * Rlo + G0 * Rhi, R2 = G0 * Rlo + G1 * Rhi;
+  const T Q1 = G1 * Ql + G0 * Qr, Q2 = G0 * Ql + G1 * Qr;       // sum (1-s) Q, sum s Q
+  const T U1 = G1 * Ul + G0 * Ur, U2 = G0 * Ul + G1 * Ur;
+  f[0] = -P1 - Q1;
+  f[1] = -R1 - U1;
+  f[2] = P1 - Q2;
+  f[3] = R1 - U2;
+  f[4] = -P2 + Q1;
+  f[5] = -R2 + U1;
+  f[6] = P2 + Q2;
+  f[7] = R2 + U2;
+}
+
 enum { EL_APPLY = 0, EL_DIAG = 1, EL_RESID = 2 };
 
 template <class T, int MODE>
@@ -221,58 +284,8 @@ k_elas(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restr
           }
         }
       } else {
-        // Gauss point q has s = G[q & 1], t = G[q >> 1] with G0 + G1 = 1, so the strain
-        // components and the interpolated d separate into values per s and per t, and
-        // the element force into sums over the two points of equal s or equal t.
-        const T dxb = ux1 - ux0, dxt = ux3 - ux2, dyl = uy2 - uy0, dyr = uy3 - uy1;
-        const T uyb = uy1 - uy0, uyt = uy3 - uy2, uxl = ux2 - ux0, uxr = ux3 - ux1;
-        const T exx_lo = (G1 * dxb + G0 * dxt) * ihx, exx_hi = (G0 * dxb + G1 * dxt) * ihx;
-        const T eyy_l = (G1 * dyl + G0 * dyr) * ihy, eyy_r = (G0 * dyl + G1 * dyr) * ihy;
-        const T uxy_l = (G1 * uxl + G0 * uxr) * ihy, uxy_r = (G0 * uxl + G1 * uxr) * ihy;
-        const T uyx_lo = (G1 * uyb + G0 * uyt) * ihx, uyx_hi = (G0 * uyb + G1 * uyt) * ihx;
-        const T dbl = G1 * d0 + G0 * d1, dbr = G0 * d0 + G1 * d1;
-        const T dtl = G1 * d2 + G0 * d3, dtr = G0 * d2 + G1 * d3;
-        const T dqv[4] = {G1 * dbl + G0 * dtl, G1 * dbr + G0 * dtr, G0 * dbl + G1 * dtl,
-                          G0 * dbr + G1 * dtr};
-        const T exv[4] = {exx_lo, exx_lo, exx_hi, exx_hi};
-        const T eyv[4] = {eyy_l, eyy_r, eyy_l, eyy_r};
-        const T gxv[4] = {uxy_l + uyx_lo, uxy_r + uyx_lo, uxy_l + uyx_hi, uxy_r + uyx_hi};
-        T P[4], Q[4], R[4], U[4];
-        const T wx = w * ihx, wy = w * ihy;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const T om = T(1) - dqv[q];
-          const T gq = om * om + eta;
-          const T exx = exv[q], eyy = eyv[q], tr = exx + eyy;
-          T vol;
-          if (MODE == EL_RESID) {
-            vol = tr > T(0) ? gq * K * tr : K * tr;
-            if (tr > T(0)) tb |= (uint8_t)(1u << q);
-          } else {
-            vol = ((tb >> q) & 1) ? gq * K * tr : K * tr;
-          }
-          const T gm2 = gq * T(2) * mu;
-          const T sxy = gq * mu * gxv[q];
-          P[q] = wx * (gm2 * (exx - cd * tr) + vol);   // w dN/dx-weight * sxx
-          U[q] = wy * (gm2 * (eyy - cd * tr) + vol);   // w dN/dy-weight * syy
-          Q[q] = wy * sxy;
-          R[q] = wx * sxy;
-        }
-        // t-sums (points 0,1 have t = G0; 2,3 have t = G1), s-sums (0,2: G0; 1,3: G1)
-        const T Plo = P[0] + P[1], Phi = P[2] + P[3], Rlo = R[0] + R[1], Rhi = R[2] + R[3];
-        const T Ql = Q[0] + Q[2], Qr = Q[1] + Q[3], Ul = U[0] + U[2], Ur = U[1] + U[3];
-        const T P1 = G1 * Plo + G0 * Phi, P2 = G0 * Plo + G1 * Phi;   // sum (1-t) P, sum t P
-        const T R1 = G1 * Rlo + G0 * Rhi, R2 = G0 * Rlo + G1 * Rhi;
-        const T Q1 = G1 * Ql + G0 * Qr, Q2 = G0 * Ql + G1 * Qr;       // sum (1-s) Q, sum s Q
-        const T U1 = G1 * Ul + G0 * Ur, U2 = G0 * Ul + G1 * Ur;
-        f[0] = -P1 - Q1;
-        f[1] = -R1 - U1;
-        f[2] = P1 - Q2;
-        f[3] = R1 - U2;
-        f[4] = -P2 + Q1;
-        f[5] = -R2 + U1;
-        f[6] = P2 + Q2;
-        f[7] = R2 + U2;
+        elas_element<T, MODE == EL_RESID>(kc, ux0, ux1, ux2, ux3, uy0, uy1, uy2, uy3, d0, d1, d2,
+                                          d3, tb, f);
       }
       if (MODE == EL_RESID && tens_out) tens_out[e] = tb;
     }
@@ -303,6 +316,97 @@ k_elas(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restr
   __syncthreads();
   }  // tiles
   if (MODE == EL_APPLY && epi != EPI_NONE) {
+    double v[1] = {(double)dot}, tot[1];
+    if (grid_reduce<1>(v, ws, tot)) krylov_epilogue(epi, sc, tot[0]);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Strip form of the elasticity tangent apply (the Krylov hot loop).  A warp owns 32 node
+// columns and marches up SR node rows, keeping the row below in registers; the right
+// neighbour's column comes by warp shuffle.  Lane k computes element (c0 + k, j) for
+// k < 31 and outputs node column c0 + k for 1 <= k <= 30, so a node is read ~1.07 times
+// and an element computed ~1.03 times per row step, with no shared memory or CTA
+// barrier.  Node (i, j) sums a0 of its own element, a1 of the left lane's element (same
+// row) and, carried from the previous row step, a2 of its own and a3 of the left lane's.
+// ------------------------------------------------------------------------------------
+constexpr int SR = 8;           // node rows per warp
+constexpr int SW = 30;          // output node columns per warp
+constexpr int STRIP_WARPS = 4;  // warps per CTA
+
+template <class T>
+__global__ void __launch_bounds__(32 * STRIP_WARPS)
+k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restrict__ tens,
+             const T *__restrict__ x, T *__restrict__ y, KrylovScal *sc, RedWs ws, int epi) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int nx = g.nx, ny = g.ny, ld = nx + 1;
+  const int nstrips = (nx + 1 + SW - 1) / SW, nchunks = (ny + 1 + SR - 1) / SR;
+  const int gw = blockIdx.x * STRIP_WARPS + (threadIdx.x >> 5);
+  const int strip = gw % nstrips, chunk = gw / nstrips;
+  T dot = T(0);
+  if (chunk < nchunks) {
+    const int i = strip * SW - 1 + lane;
+    const int r0 = chunk * SR;
+    const bool col_ok = i >= 0 && i <= nx;
+    auto load = [&](int j, T &vx, T &vy, T &vd) {
+      vx = vy = vd = T(0);
+      if (col_ok && j >= 0 && j <= ny) {
+        const size_t n = (size_t)j * ld + i;
+        ld_pair(x, n, vx, vy);
+        vd = ldg(d + n);
+        if (g.dofm) {
+          const uint8_t mk = ldg(g.dofm + n);
+          if (mk & 1) vx = T(0);
+          if (mk & 2) vy = T(0);
+        }
+      }
+    };
+    T cx, cy, cdv;
+    load(r0 - 1, cx, cy, cdv);
+    T carry_x = T(0), carry_y = T(0);
+    for (int j = r0 - 1; j < r0 + SR; ++j) {
+      T nxv, nyv, ndv;
+      load(j + 1, nxv, nyv, ndv);
+      const T rx0 = __shfl_down_sync(FULL, cx, 1), ry0 = __shfl_down_sync(FULL, cy, 1);
+      const T rd0 = __shfl_down_sync(FULL, cdv, 1);
+      const T rx1 = __shfl_down_sync(FULL, nxv, 1), ry1 = __shfl_down_sync(FULL, nyv, 1);
+      const T rd1 = __shfl_down_sync(FULL, ndv, 1);
+      T f[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) f[k] = T(0);
+      if (lane < 31 && i >= 0 && i < nx && j >= 0 && j < ny) {
+        const size_t e = (size_t)j * nx + i;
+        if (!g.active || ldg(g.active + e)) {
+          uint8_t tb = ldg(tens + e);
+          elas_element<T, false>(kc, cx, rx0, nxv, rx1, cy, ry0, nyv, ry1, cdv, rd0, ndv, rd1, tb, f);
+        }
+      }
+      const T lx1 = __shfl_up_sync(FULL, f[2], 1), ly1 = __shfl_up_sync(FULL, f[3], 1);
+      const T lx3 = __shfl_up_sync(FULL, f[6], 1), ly3 = __shfl_up_sync(FULL, f[7], 1);
+      if (j >= r0 && j <= ny && lane >= 1 && lane <= SW && col_ok) {
+        T ox = f[0] + lx1 + carry_x, oy = f[1] + ly1 + carry_y;
+        const size_t n = (size_t)j * ld + i;
+        if (g.dofm) {
+          const uint8_t mk = ldg(g.dofm + n);
+          if (mk & 1) ox = T(0);
+          if (mk & 2) oy = T(0);
+        }
+        if (sizeof(T) == 4) {
+          reinterpret_cast<float2 *>(y)[n] = make_float2((float)ox, (float)oy);
+        } else {
+          reinterpret_cast<double2 *>(y)[n] = make_double2((double)ox, (double)oy);
+        }
+        dot += cx * ox + cy * oy;
+      }
+      carry_x = f[4] + lx3;
+      carry_y = f[5] + ly3;
+      cx = nxv;
+      cy = nyv;
+      cdv = ndv;
+    }
+  }
+  if (epi != EPI_NONE) {
     double v[1] = {(double)dot}, tot[1];
     if (grid_reduce<1>(v, ws, tot)) krylov_epilogue(epi, sc, tot[0]);
   }
@@ -647,8 +751,9 @@ void elas_apply(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, 
                 T *y, cudaStream_t st, KrylovScal *sc, const RedWs *ws, int epi) {
   RedWs w = ws ? *ws : RedWs{nullptr, nullptr, 0};
   const int e = ws ? epi : EPI_NONE;
-  k_elas<T, EL_APPLY><<<tile_grid(g), TILE_THREADS, 0, st>>>(
-      g, elem_const<T>(g, m), d, tens, x, y, nullptr, sc, w, e);
+  const unsigned warps = (unsigned)((g.nx + 1 + SW - 1) / SW) * (unsigned)((g.ny + 1 + SR - 1) / SR);
+  k_elas_strip<T><<<(warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, 0, st>>>(
+      g, elem_const<T>(g, m), d, tens, x, y, sc, w, e);
 }
 template <class T>
 void elas_diag(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, T *diag,
