@@ -330,11 +330,12 @@ k_elas(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restr
 // barrier.  Node (i, j) sums a0 of its own element, a1 of the left lane's element (same
 // row) and, carried from the previous row step, a2 of its own and a3 of the left lane's.
 // ------------------------------------------------------------------------------------
-constexpr int SR = 8;           // node rows per warp
 constexpr int SW = 30;          // output node columns per warp
 constexpr int STRIP_WARPS = 4;  // warps per CTA
 
-template <class T>
+// SR node rows per warp: short strips on small grids (more warps to hide latency), long
+// strips on large ones (less halo re-reading).
+template <class T, int SR>
 __global__ void __launch_bounds__(32 * STRIP_WARPS)
 k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restrict__ tens,
              const T *__restrict__ x, T *__restrict__ y, KrylovScal *sc, RedWs ws, int epi) {
@@ -751,9 +752,19 @@ void elas_apply(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, 
                 T *y, cudaStream_t st, KrylovScal *sc, const RedWs *ws, int epi) {
   RedWs w = ws ? *ws : RedWs{nullptr, nullptr, 0};
   const int e = ws ? epi : EPI_NONE;
-  const unsigned warps = (unsigned)((g.nx + 1 + SW - 1) / SW) * (unsigned)((g.ny + 1 + SR - 1) / SR);
-  k_elas_strip<T><<<(warps + STRIP_WARPS - 1) / STRIP_WARPS, 32 * STRIP_WARPS, 0, st>>>(
-      g, elem_const<T>(g, m), d, tens, x, y, sc, w, e);
+  const size_t nn = (size_t)(g.nx + 1) * (g.ny + 1);
+  const unsigned strips = (unsigned)((g.nx + 1 + SW - 1) / SW);
+  auto blocks = [&](int sr) {
+    const unsigned warps = strips * (unsigned)((g.ny + 1 + sr - 1) / sr);
+    return (warps + STRIP_WARPS - 1) / STRIP_WARPS;
+  };
+  const ElemConst<T> kc = elem_const<T>(g, m);
+  if (nn < (size_t)1500000)
+    k_elas_strip<T, 2><<<blocks(2), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, x, y, sc, w, e);
+  else if (nn < (size_t)6000000)
+    k_elas_strip<T, 4><<<blocks(4), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, x, y, sc, w, e);
+  else
+    k_elas_strip<T, 8><<<blocks(8), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, x, y, sc, w, e);
 }
 template <class T>
 void elas_diag(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, T *diag,
