@@ -48,6 +48,10 @@ def parse():
     p.add_argument("--grid", type=int, default=512)
     p.add_argument("--scheme", default="S1")
     p.add_argument("--full-path", action="store_true")
+    p.add_argument("--kernel", default=None, choices=["elas"],
+                   help="time one operator kernel on the --grid tensile mesh and exit")
+    p.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    p.add_argument("--reps", type=int, default=20)
     return p.parse_args()
 
 
@@ -334,6 +338,50 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_kernel(args):
+    """Standalone timing of the matrix-free elasticity tangent apply (pf_op_elas_apply)
+    on the --grid tensile mesh: 2 untimed launches, then --reps launches back to back
+    between CUDA events on the launching stream (inputs resident, L2 not flushed)."""
+    import numpy as np
+    import torch
+    from paper_2209_07969_gb300 import binding, build
+    build.build()
+    L = binding.lib()
+    spec = workload(args.grid)
+    nn, ne = (spec.nx + 1) * (spec.ny + 1), spec.nx * spec.ny
+    dev = torch.device("cuda")
+    st = torch.cuda.current_stream()
+    flags = torch.from_numpy(spec.node_flags.astype(np.uint8)).to(dev)
+    mask = torch.empty(nn, dtype=torch.uint8, device=dev)
+    binding.check(L.pf_op_dof_mask(spec.nx, spec.ny, flags.data_ptr(), None, mask.data_ptr(),
+                                   st.cuda_stream))
+    g = binding.grid(spec.nx, spec.ny, spec.Lx / spec.nx, spec.Ly / spec.ny, None, mask.data_ptr())
+    mat = binding.material(spec.E, spec.nu, spec.Gc, spec.l, spec.eta, spec.plane)
+    T, code = (torch.float32, binding.F32) if args.dtype == "f32" else (torch.float64, binding.F64)
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    d = (torch.rand(nn, generator=gen) * 0.5).to(dev, T)
+    x = torch.randn(2 * nn, generator=gen).to(dev, T)
+    y = torch.empty_like(x)
+    tens = torch.randint(0, 16, (ne,), generator=gen, dtype=torch.uint8).to(dev)
+
+    def launch():
+        binding.check(L.pf_op_elas_apply(g, mat, code, d.data_ptr(), tens.data_ptr(),
+                                         x.data_ptr(), y.data_ptr(), st.cuda_stream))
+    for _ in range(2):
+        launch()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.reps):
+        launch()
+    e1.record(st)
+    e1.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3 / args.reps
+    bpn = 22.0 if args.dtype == "f32" else 42.0
+    print(json.dumps({"kernel": "pf_op_elas_apply", "grid": args.grid, "dtype": args.dtype,
+                      "launch_us": t * 1e6, "algorithmic_GBps": bpn * nn / t / 1e9}), flush=True)
+
+
 def run_full_path(args):
     """Complete load paths (all 100 steps) of the workload, one simulation per scheme."""
     from paper_2209_07969_gb300 import binding, build
@@ -357,6 +405,8 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.kernel:
+        run_kernel(a)
     elif a.full_path:
         run_full_path(a)
     else:
