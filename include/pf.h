@@ -122,6 +122,9 @@ void pf_default_options(pf_options *opt);
  * k_res < 0; NULL pointers), PF_ENOMEM, PF_ECUDA.  *out is NULL on error. */
 pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double l,
                     double k_res, pf_ctx **out);
+/* Device bytes pf_create allocates for this mesh (0 for an invalid mesh); a scheduler
+ * admits simulations by this footprint. */
+size_t pf_footprint_bytes(const pf_mesh *mesh);
 pf_status pf_set_options(pf_ctx *ctx, const pf_options *opt);
 pf_status pf_get_options(const pf_ctx *ctx, pf_options *opt);
 

@@ -73,6 +73,7 @@ _PROTOS = {
     "pf_status_string": (C.c_char_p, [I]),
     "pf_material_make": (S, [D, D, D, D, D, I, C.POINTER(Material)]),
     "pf_create": (S, [C.POINTER(Mesh), D, D, D, D, D, C.POINTER(P)]),
+    "pf_footprint_bytes": (C.c_size_t, [C.POINTER(Mesh)]),
     "pf_set_options": (S, [P, C.POINTER(Options)]),
     "pf_get_options": (S, [P, C.POINTER(Options)]),
     "pf_load_step": (S, [P, D, I, D, C.POINTER(StepResult)]),
@@ -141,6 +142,14 @@ def material(E, nu, Gc, l, k_res, plane=0):
 
 def grid(nx, ny, hx, hy, elem_active_ptr=None, dof_mask_ptr=None):
     return Grid(nx, ny, hx, hy, elem_active_ptr, dof_mask_ptr)
+
+
+def footprint_bytes(spec, precision=FP64, precond=PRECOND_JACOBI):
+    """Device bytes pf_create would allocate for the specimen (admission control)."""
+    active = None if spec.elem_active is None or np.all(spec.elem_active) else 1
+    mesh = Mesh(spec.nx, spec.ny, spec.Lx, spec.Ly, active, 1, spec.plane, precision,
+                spec.reaction_dir, precond)
+    return int(lib().pf_footprint_bytes(C.byref(mesh)))
 
 
 class Simulation:

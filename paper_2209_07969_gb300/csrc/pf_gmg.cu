@@ -733,6 +733,23 @@ cudaError_t gmg_alloc(Gmg<T> &G, int nx, int ny, int B, const RedWs &ws) {
   return cudaSuccess;
 }
 
+size_t gmg_bytes(int nx, int ny, int B, size_t tsize) {
+  size_t total = 0;
+  int cx = nx, cy = ny, l = 0;
+  size_t last_nn = 0;
+  while (true) {
+    const size_t nn = (size_t)(cx + 1) * (cy + 1);
+    total += 9 * B * B * nn * tsize + 6 * B * nn * tsize + nn + sizeof(double) + 4 * tsize;
+    last_nn = nn;
+    ++l;
+    if ((cx <= GMG_COARSE_MAX && cy <= GMG_COARSE_MAX) || l == GMG_MAX_LEVELS) break;
+    cx = (cx + 1) / 2;
+    cy = (cy + 1) / 2;
+  }
+  const size_t nc = B * last_nn;
+  return total + nc * nc * tsize;
+}
+
 template <class T>
 void gmg_free(Gmg<T> &G) {
   for (int l = 0; l < G.nl; ++l) {

@@ -52,6 +52,8 @@ template <class T>
 cudaError_t gmg_alloc(Gmg<T> &G, int nx, int ny, int B, const RedWs &ws);
 template <class T>
 void gmg_free(Gmg<T> &G);
+// Device bytes gmg_alloc takes for an nx x ny grid with B components of tsize bytes.
+size_t gmg_bytes(int nx, int ny, int B, size_t tsize);
 
 // Setup from the fine operator.  Elasticity: fine tangent with d (type T) and tension
 // bits; damage: per-Gauss-point coefficient c (type T), kappa.  dofm: fine mask.

@@ -776,6 +776,26 @@ pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double 
   return PF_OK;
 }
 
+size_t pf_footprint_bytes(const pf_mesh *mesh) {
+  if (!mesh || mesh->nx < 1 || mesh->ny < 1) return 0;
+  const size_t nn = (size_t)(mesh->nx + 1) * (mesh->ny + 1), ne = (size_t)mesh->nx * mesh->ny;
+  const size_t nq = 4 * ne, D = sizeof(double), F = sizeof(float);
+  size_t b = (2 * nn + nn + nq + nn + 2 * nn) * D     // u, d, H, d_prev, F
+             + 4 * nq * D + nq                          // Hk, cq, Hhalf, csolve, act
+             + 3 * nn * D                               // bd, Kd, dd
+             + 2 * nn + ne * (mesh->elem_active ? 2 : 1)  // flags, dofm, tens, active
+             + 8 * 2 * nn * D;                          // Krylov work (FP64)
+  if (mesh->precision == PF_FP32_IR) b += 7 * 2 * nn * F + nn * F + nq * F;
+  const size_t tiles = (size_t)tile_blocks_x(mesh->nx) * tile_blocks_y(mesh->ny);
+  const size_t mb = tiles > 4096 ? tiles : 4096;
+  b += 4 * mb * D + red_counters((int)mb) * sizeof(unsigned) + sizeof(KrylovScal) + 8 * D;
+  if (mesh->precond == PF_PRECOND_GMG) {
+    const size_t ts = mesh->precision == PF_FP64 ? D : F;
+    b += gmg_bytes(mesh->nx, mesh->ny, 2, ts) + gmg_bytes(mesh->nx, mesh->ny, 1, ts);
+  }
+  return b;
+}
+
 pf_status pf_set_options(pf_ctx *ctx, const pf_options *o) {
   if (!ctx || !o) return PF_EINVAL;
   if (!(o->tol_nr > 0) || !(o->tol_lin > 0) || !(o->tol_inner > 0) || o->max_newton < 1 ||

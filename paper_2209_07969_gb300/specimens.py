@@ -175,3 +175,39 @@ def random_state(spec, seed, u_scale=1e-3, h_scale=None):
         h_scale = spec.Gc / spec.l
     H = h_scale * r.random((spec.ne, 4)) * (1.0 + 3.0 * r.random((spec.ne, 1)))
     return u, d, H
+
+
+def served_batch(n_requests=256, seed=0, rate_per_s=1.0, grids=(128, 256, 512, 1024)):
+    """Seeded request mix of the served-batch workload.
+
+    Each request: tensile or shear notched square (50/50) on a grid drawn from ``grids``,
+    E ~ U[20, 210] GPa, nu ~ U[0.15, 0.35], G_c ~ U[1e-4, 3e-3] kN/mm, l ~ U[2h, 4h], scheme
+    from {ST, S1, S2}; 100 (tensile) or 150 (shear) load steps to a final displacement
+    scaled from the benchmark's by the homogeneous critical strain
+    sqrt(G_c / (3 M l)) (M = lambda + 2 mu).  Arrivals are a Poisson process of the given
+    rate.  Returns a list of (arrival_time_s, Specimen, scheme).
+    """
+    r = rng(seed)
+    M0 = MIEHE_LAMBDA + 2 * MIEHE_MU
+    t = 0.0
+    out = []
+    for _ in range(n_requests):
+        t += r.exponential(1.0 / rate_per_s)
+        n = int(r.choice(grids))
+        h = 1.0 / n
+        E = r.uniform(20.0, 210.0)
+        nu = r.uniform(0.15, 0.35)
+        Gc = r.uniform(1e-4, 3e-3)
+        l = r.uniform(2 * h, 4 * h)
+        scheme = int(r.integers(0, 3))
+        tensile_kind = r.random() < 0.5
+        mu = E / (2 * (1 + nu))
+        lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+        scale = np.sqrt((Gc / MIEHE_GC) * (M0 / (lam + 2 * mu)) * (0.0075 / l))
+        if tensile_kind:
+            sp = tensile(n, l=l, steps=100, u_max=6e-3 * scale)
+        else:
+            sp = shear(n, l=l, steps=150, u_max=1.5e-2 * scale)
+        sp.E, sp.nu, sp.Gc = E, nu, Gc
+        out.append((t, sp, scheme))
+    return out

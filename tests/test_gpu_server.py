@@ -1,0 +1,52 @@
+"""A served mix of simulations gives, for every request, the result it gives alone (GPU).
+
+Requests of different grids, materials, specimens and schemes arrive while others run;
+the server admits them by slot and HBM footprint and their kernels overlap on the GPU.
+The kernels are deterministic (no atomics, fixed reduction order), so every request's
+reaction forces and final phase field match its stand-alone run bit for bit.
+"""
+import numpy as np
+import pytest
+
+from paper_2209_07969_gb300 import binding, server, specimens as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests():
+    mix = S.served_batch(8, seed=3, rate_per_s=50.0, grids=(16, 24, 32))
+    reqs = []
+    for k, (t, sp, scheme) in enumerate(mix):
+        sp.increments = sp.increments[:5] * (len(sp.increments) / 5.0)  # 5 coarse steps
+        prec = binding.FP32_IR if k % 2 == 0 else binding.FP64
+        pc = binding.PRECOND_GMG if k % 3 else binding.PRECOND_JACOBI
+        reqs.append((t, server.Request(sp, scheme=scheme, precision=prec, precond=pc,
+                                       tol=1e-6, keep_fields=True)))
+    return reqs
+
+
+def test_results_alone_and_in_the_mix_agree(gpu):
+    reqs = _requests()
+    fps = [binding.footprint_bytes(r.spec, r.precision, r.precond) for _, r in reqs]
+    srv = server.Server(hbm_budget=2 * max(fps), slots=3, device=0)
+    import time
+    t0 = time.perf_counter()
+    for t, r in reqs:                       # Poisson arrivals, compressed in time
+        wait = t0 + 0.01 * t - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        srv.submit(r)
+    assert srv.drain(timeout=600)
+    srv.close()
+    assert srv.peak_in_use <= 2 * max(fps)
+    assert len(srv.results) == len(reqs)
+    for _, r in reqs:
+        mixed = srv.results[r.rid]
+        assert mixed.ok, mixed.error
+        alone = server.run_path(server.Request(r.spec, r.scheme, r.precision, r.precond,
+                                               r.tol, keep_fields=True))
+        assert mixed.reactions == alone.reactions
+        assert mixed.stag_iters == alone.stag_iters
+        assert np.array_equal(mixed.d, alone.d)
+    steps, paths = server.latency_percentiles(srv.results)
+    assert steps["p50"] > 0 and paths["p99"] >= paths["p50"] > 0
