@@ -298,11 +298,12 @@ __global__ void k_fm_coarse(int nxf, int nyf, const uint8_t *__restrict__ fmf, i
 
 // (A x)_n for one node: vectors are zero on non-free DOFs at every level, so the
 // neighbours' masks are not needed; out-of-grid neighbours have no stencil entry.
-// NC: x is not written while the kernel runs, so the read-only data path may be used
-// (false inside the single-CTA coarse cycle, which rewrites its vectors between phases).
-template <class T, int B, bool NC = true>
-__device__ __forceinline__ void sten_row(int nx, int ny, size_t nn, const T *__restrict__ S,
-                                         const T *__restrict__ x, size_t n, T (&acc)[B]) {
+// xat(i) returns entry i of x, so callers choose the load path (read-only cache for
+// vectors no thread rewrites during the kernel, L2 for vectors other CTAs rewrite) or
+// form x on the fly.
+template <class T, int B, class XAt>
+__device__ __forceinline__ void sten_row_by(int nx, int ny, size_t nn, const T *__restrict__ S,
+                                            size_t n, XAt xat, T (&acc)[B]) {
   // Stencil entries towards neighbours outside the grid are zero, so neighbour indices are
   // clamped into the grid instead of branched on: all loads issue back to back.
   const int i = (int)(n % (nx + 1)), j = (int)(n / (nx + 1));
@@ -316,7 +317,7 @@ __device__ __forceinline__ void sten_row(int nx, int ny, size_t nn, const T *__r
 #pragma unroll
   for (int k = 0; k < 9; ++k)
 #pragma unroll
-    for (int c = 0; c < B; ++c) xv[k][c] = NC ? __ldg(x + B * m[k] + c) : x[B * m[k] + c];
+    for (int c = 0; c < B; ++c) xv[k][c] = xat(B * m[k] + c);
 #pragma unroll
   for (int r = 0; r < B; ++r) acc[r] = T(0);
 #pragma unroll
@@ -325,6 +326,13 @@ __device__ __forceinline__ void sten_row(int nx, int ny, size_t nn, const T *__r
     for (int c = 0; c < B; ++c)
 #pragma unroll
       for (int r = 0; r < B; ++r) acc[r] += __ldg(S + sidx<B>(k, r, c, n, nn)) * xv[k][c];
+}
+
+// x is not written while the kernel runs: read-only data path.
+template <class T, int B>
+__device__ __forceinline__ void sten_row(int nx, int ny, size_t nn, const T *__restrict__ S,
+                                         const T *__restrict__ x, size_t n, T (&acc)[B]) {
+  sten_row_by<T, B>(nx, ny, nn, S, n, [x](size_t q) { return __ldg(x + q); }, acc);
 }
 
 // y = A x  (mode 0) or y = b - A x (mode 1), rows of non-free DOFs zero.
@@ -370,7 +378,7 @@ __global__ void k_sten_cheb(int nx, int ny, const T *__restrict__ S, const T *__
   }
 }
 
-// ---- coarse levels in one CTA ------------------------------------------------------------
+// ---- coarse levels in one CTA --------------------------------------------------------------
 template <class T>
 struct CoarseLevel {
   int nx, ny;
@@ -389,54 +397,60 @@ struct CoarseArgs {
   int ncoarse;
 };
 
-template <class T, int B>
-__device__ void cta_apply(const CoarseLevel<T> &L, const T *x, const T *b, T *y, int mode) {
-  const size_t nn = (size_t)(L.nx + 1) * (L.ny + 1);
-  for (size_t n = threadIdx.x; n < nn; n += blockDim.x) {
-    T acc[B];
-    sten_row<T, B, false>(L.nx, L.ny, nn, L.S, x, n, acc);
-    const uint8_t f = L.fm[n];
-#pragma unroll
-    for (int r = 0; r < B; ++r) {
-      T v = mode ? b[B * n + r] - acc[r] : acc[r];
-      y[B * n + r] = ((f >> r) & 1) ? v : T(0);
-    }
-  }
-}
+template <class T>
+__device__ __forceinline__ T ld_(const T *p) { return *p; }
+template <class T>
+__device__ __forceinline__ void st_(T *p, T v) { *p = v; }
 
-// One V-cycle over levels [0, nlev) of `a` inside a single CTA (blockDim 1024).
+// One V-cycle over levels [0, nlev) of `a` in one CTA of COARSE_THREADS threads.  Every
+// phase is a node loop over the CTA followed by a barrier; thread t owns the same nodes in
+// every phase.  Chebyshev steps are fused so that each level costs three barriers on the
+// way down and three on the way up:
+//   down: x = d0 + c1 d0 + c2 D^-1 (b - A d0), d0 = it D^-1 b formed at the neighbours;
+//         r = b - A x;  b_coarse = P^T r
+//   up:   x += P x_coarse;  r = b - A x, d = it D^-1 r;  x = (x + d) + c1 d + c2 D^-1 (r - A d)
 template <class T, int B>
-__global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> a) {
+__global__ void __launch_bounds__(COARSE_THREADS) k_coarse_cycle(CoarseArgs<T> a) {
+  const size_t t0 = threadIdx.x, nt = blockDim.x;
   const int last = a.nlev - 1;
   for (int l = 0; l < last; ++l) {
     const CoarseLevel<T> &L = a.L[l];
     const T *b = l == 0 ? a.b0 : L.b;
     T *x = l == 0 ? a.x0 : L.x;
-    const size_t n = (size_t)B * (L.nx + 1) * (L.ny + 1);
+    const size_t nn = (size_t)(L.nx + 1) * (L.ny + 1);
     const T it = L.coef[0], c2 = L.coef[1], c1 = L.coef[2];
-    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const T di = L.invd[i] * b[i] * it;
-      L.d[i] = di;
-      x[i] = di;
-      L.r[i] = b[i];
+    const T *invd = L.invd;
+    for (size_t n = t0; n < nn; n += nt) {
+      T acc[B];
+      sten_row_by<T, B>(L.nx, L.ny, nn, L.S, n,
+                        [=](size_t q) { return __ldg(invd + q) * ld_(b + q) * it; }, acc);
+      const uint8_t f = __ldg(L.fm + n);
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        const size_t i = B * n + c;
+        const T iv = __ldg(invd + i), bi = ld_(b + i);
+        const T d0 = iv * bi * it;
+        const T d1 = c1 * d0 + c2 * iv * (bi - acc[c]);
+        st_(x + i, ((f >> c) & 1) ? d0 + d1 : T(0));
+      }
     }
     __syncthreads();
-    cta_apply<T, B>(L, L.d, nullptr, L.y, 0);
-    __syncthreads();
-    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const T ri = L.r[i] - L.y[i];
-      const T di = c1 * L.d[i] + c2 * L.invd[i] * ri;
-      L.r[i] = ri;
-      L.d[i] = di;
-      x[i] += di;
+    for (size_t n = t0; n < nn; n += nt) {
+      T acc[B];
+      const T *xr = x;
+      sten_row_by<T, B>(L.nx, L.ny, nn, L.S, n, [=](size_t q) { return ld_(xr + q); }, acc);
+      const uint8_t f = __ldg(L.fm + n);
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        const size_t i = B * n + c;
+        st_(L.r + i, ((f >> c) & 1) ? ld_(b + i) - acc[c] : T(0));
+      }
     }
-    __syncthreads();
-    cta_apply<T, B>(L, x, b, L.r, 1);
     __syncthreads();
     // restrict r -> b of level l+1
     const CoarseLevel<T> &C = a.L[l + 1];
     const size_t nnc = (size_t)(C.nx + 1) * (C.ny + 1);
-    for (size_t I = threadIdx.x; I < nnc; I += blockDim.x) {
+    for (size_t I = t0; I < nnc; I += nt) {
       const int Ix = (int)(I % (C.nx + 1)), Iy = (int)(I / (C.nx + 1));
       T acc[B];
 #pragma unroll
@@ -448,11 +462,11 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> a) {
           const T wi = (p == 0 ? T(1) : T(0.5)) * (q == 0 ? T(1) : T(0.5));
           const size_t fi = (size_t)iy * (L.nx + 1) + ix;
 #pragma unroll
-          for (int c = 0; c < B; ++c) acc[c] += wi * L.r[B * fi + c];
+          for (int c = 0; c < B; ++c) acc[c] += wi * ld_(L.r + B * fi + c);
         }
-      const uint8_t mc = C.fm[I];
+      const uint8_t mc = __ldg(C.fm + I);
 #pragma unroll
-      for (int c = 0; c < B; ++c) C.b[B * I + c] = ((mc >> c) & 1) ? acc[c] : T(0);
+      for (int c = 0; c < B; ++c) st_(C.b + B * I + c, ((mc >> c) & 1) ? acc[c] : T(0));
     }
     __syncthreads();
   }
@@ -461,13 +475,15 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> a) {
     const CoarseLevel<T> &C = a.L[last];
     const T *b = last == 0 ? a.b0 : C.b;
     T *x = last == 0 ? a.x0 : C.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = warp; i < a.ncoarse; i += nw) {
+    const int lane = threadIdx.x & 31;
+    const size_t warp = t0 >> 5, nw = nt >> 5;
+    for (size_t i = warp; i < (size_t)a.ncoarse; i += nw) {
       T s = T(0);
-      for (int j = lane; j < a.ncoarse; j += 32) s += a.cinv[(size_t)i * a.ncoarse + j] * b[j];
+      for (int j = lane; j < a.ncoarse; j += 32)
+        s += __ldg(a.cinv + i * a.ncoarse + j) * ld_(b + j);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) x[i] = s;
+      if (lane == 0) st_(x + i, s);
     }
     __syncthreads();
   }
@@ -476,10 +492,10 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> a) {
     const CoarseLevel<T> &C = a.L[l + 1];
     const T *b = l == 0 ? a.b0 : L.b;
     T *x = l == 0 ? a.x0 : L.x;
-    const T *xc = (l + 1 == last && last == 0) ? a.x0 : C.x;
-    const size_t nnf = (size_t)(L.nx + 1) * (L.ny + 1);
-    for (size_t nf = threadIdx.x; nf < nnf; nf += blockDim.x) {
-      const uint8_t m = L.fm[nf];
+    const T *xc = C.x;
+    const size_t nn = (size_t)(L.nx + 1) * (L.ny + 1);
+    for (size_t nf = t0; nf < nn; nf += nt) {
+      const uint8_t m = __ldg(L.fm + nf);
       if (!m) continue;
       const int ix = (int)(nf % (L.nx + 1)), iy = (int)(nf / (L.nx + 1));
       const int px0 = ix >> 1, py0 = iy >> 1, npx = (ix & 1) ? 2 : 1, npy = (iy & 1) ? 2 : 1;
@@ -491,33 +507,44 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> a) {
           const T wj = (npx == 2 ? T(0.5) : T(1)) * (npy == 2 ? T(0.5) : T(1));
           const size_t J = (size_t)(py0 + v) * (C.nx + 1) + (px0 + u);
 #pragma unroll
-          for (int c = 0; c < B; ++c) acc[c] += wj * xc[B * J + c];
+          for (int c = 0; c < B; ++c) acc[c] += wj * ld_(xc + B * J + c);
         }
 #pragma unroll
       for (int c = 0; c < B; ++c)
-        if ((m >> c) & 1) x[B * nf + c] += acc[c];
+        if ((m >> c) & 1) st_(x + B * nf + c, ld_(x + B * nf + c) + acc[c]);
     }
     __syncthreads();
-    const size_t n = (size_t)B * nnf;
     const T it = L.coef[0], c2 = L.coef[1], c1 = L.coef[2];
-    cta_apply<T, B>(L, x, b, L.r, 1);
-    __syncthreads();
-    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const T di = L.invd[i] * L.r[i] * it;
-      L.d[i] = di;
-      x[i] += di;
+    const T *invd = L.invd;
+    for (size_t n = t0; n < nn; n += nt) {
+      T acc[B];
+      const T *xr = x;
+      sten_row_by<T, B>(L.nx, L.ny, nn, L.S, n, [=](size_t q) { return ld_(xr + q); }, acc);
+      const uint8_t f = __ldg(L.fm + n);
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        const size_t i = B * n + c;
+        const T ri = ((f >> c) & 1) ? ld_(b + i) - acc[c] : T(0);
+        st_(L.r + i, ri);
+        st_(L.d + i, __ldg(invd + i) * ri * it);
+      }
     }
     __syncthreads();
-    cta_apply<T, B>(L, L.d, nullptr, L.y, 0);
-    __syncthreads();
-    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const T ri = L.r[i] - L.y[i];
-      const T di = c1 * L.d[i] + c2 * L.invd[i] * ri;
-      L.r[i] = ri;
-      L.d[i] = di;
-      x[i] += di;
+    for (size_t n = t0; n < nn; n += nt) {
+      T acc[B];
+      const T *dr = L.d;
+      sten_row_by<T, B>(L.nx, L.ny, nn, L.S, n, [=](size_t q) { return ld_(dr + q); }, acc);
+      const uint8_t f = __ldg(L.fm + n);
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        const size_t i = B * n + c;
+        const T di = ld_(L.d + i);
+        const T ri = ld_(L.r + i) - (((f >> c) & 1) ? acc[c] : T(0));
+        const T d2 = c1 * di + c2 * __ldg(invd + i) * ri;
+        st_(x + i, (ld_(x + i) + di) + d2);
+      }
     }
-    __syncthreads();
+    if (l > 0) __syncthreads();
   }
 }
 
@@ -928,9 +955,9 @@ void gmg_coarse_cycle(const Gmg<T> &G, int lc, const T *b0, T *x0, cudaStream_t 
   a.cinv = G.cinv;
   a.ncoarse = G.ncoarse;
   if (G.B == 2)
-    k_coarse_cycle<T, 2><<<1, 1024, 0, st>>>(a);
+    k_coarse_cycle<T, 2><<<1, COARSE_THREADS, 0, st>>>(a);
   else
-    k_coarse_cycle<T, 1><<<1, 1024, 0, st>>>(a);
+    k_coarse_cycle<T, 1><<<1, COARSE_THREADS, 0, st>>>(a);
 }
 
 #define GMG_INST(T)                                                                            \

@@ -248,8 +248,9 @@ pf_status pcg(pf_ctx *ctx, int slot, Apply apply, Fine fine, Gmg<T> *G, size_t n
   return PF_OK;
 }
 
-// FP32 inner solves inside FP64 iterative refinement:  x = 0; repeat {solve A_32 e =
-// r_32 to tol_inner; x += e; r = b - A_64 x; stop when ||r|| <= tol_lin ||b||}.
+// FP32 inner solves inside FP64 iterative refinement:  x = 0; repeat {s = 2^-floor(log2
+// ||r||); solve A_32 e = (s r)_32 to tol_inner; x += e / s; r = b - A_64 x; stop when
+// ||r|| <= tol_lin ||b||}.
 // inner(iters, ok) solves with rhs ctx->fb into ctx->fx.
 template <class ApplyD, class Inner>
 pf_status refine(pf_ctx *ctx, ApplyD applyd, Inner inner, size_t n, int ncomp, const double *b,
@@ -264,16 +265,20 @@ pf_status refine(pf_ctx *ctx, ApplyD applyd, Inner inner, size_t n, int ncomp, c
   *ok = true;
   if (!(bn > 0.0)) return PF_OK;
   *ok = false;
+  double rn = bn;
   for (int k = 0; k < ctx->opt.max_refine; ++k) {
-    convert<double, float>(n, ctx->kres, ctx->fb, st);
+    // The FP32 solve sees the residual scaled to unit size: late corrections are many
+    // orders of magnitude below the first one, and unscaled their FP32 dot products fall
+    // into the subnormal range, where CG loses its accuracy and stalls.
+    const double s = ldexp(1.0, -ilogb(rn));
+    scale_to_f32(n, s, ctx->kres, ctx->fb, st);
     ctx->launches++;
     int it = 0;
     bool iok = false;
     CKS(inner(&it, &iok));
     *iters += it;
-    convert<float, double>(n, ctx->fx, ctx->kq, st);
-    add(n, ctx->kq, x, st);
-    ctx->launches += 2;
+    add_scaled_f32(n, 1.0 / s, ctx->fx, x, st);
+    ctx->launches++;
     (*refines)++;
     applyd(x, ctx->kq);
     masked_comb(n, ncomp, ctx->g.dofm, 1.0, b, 1.0, ctx->kq, ctx->kres, st);
@@ -281,7 +286,7 @@ pf_status refine(pf_ctx *ctx, ApplyD applyd, Inner inner, size_t n, int ncomp, c
     ctx->launches += 3;
     CKS(check_launch(ctx));
     CKS(read_scalars(ctx, ctx->dscal, sizeof(double)));
-    const double rn = sqrt(ctx->hbuf[0]);
+    rn = sqrt(ctx->hbuf[0]);
     if (rn <= ctx->opt.tol_lin * bn) {
       *ok = true;
       break;

@@ -239,6 +239,20 @@ __global__ void k_convert(size_t n, const A *__restrict__ a, B *__restrict__ b) 
     b[i] = (B)a[i];
 }
 
+__global__ void k_scale_to_f32(size_t n, double s, const double *__restrict__ a,
+                               float *__restrict__ b) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (float)(s * a[i]);
+}
+
+__global__ void k_add_scaled_f32(size_t n, double s, const float *__restrict__ e,
+                                 double *__restrict__ x) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    x[i] += s * (double)e[i];
+}
+
 // c = G_c/l + 2 H (AT2 coefficient of the evolution-equation tangent)
 template <class T>
 __global__ void k_coef(size_t n, double gcl, const double *__restrict__ H, T *__restrict__ c) {
@@ -379,6 +393,12 @@ void add(size_t n, const double *x, double *y, cudaStream_t st) {
 template <class A, class B>
 void convert(size_t n, const A *a, B *b, cudaStream_t st) {
   k_convert<A, B><<<vblocks(n, 1 << 16), VEC_THREADS, 0, st>>>(n, a, b);
+}
+void scale_to_f32(size_t n, double s, const double *a, float *b, cudaStream_t st) {
+  k_scale_to_f32<<<vblocks(n, 1 << 16), VEC_THREADS, 0, st>>>(n, s, a, b);
+}
+void add_scaled_f32(size_t n, double s, const float *e, double *x, cudaStream_t st) {
+  k_add_scaled_f32<<<vblocks(n, 1 << 16), VEC_THREADS, 0, st>>>(n, s, e, x);
 }
 template <class T>
 void coef(size_t n, double gcl, const double *H, T *c, cudaStream_t st) {

@@ -221,3 +221,27 @@ def test_stag_cap_reports_not_converged(gpu):
     r = sim.load_step(6e-3, 0, 1e-14)
     assert r["status"] == binding.PF_ENOTCONV and r["converged"] == 0 and r["stag_iters"] == 1
     sim.close()
+
+
+@pytest.mark.parametrize("precond", PRECONDS)
+def test_fp32_refinement_is_scale_invariant(gpu, precond):
+    # The FP32 inner solves see the refinement residual scaled to unit size, so a load
+    # step scaled by 2^-60 solves like the unscaled one.  Unscaled, the FP32 dot products
+    # of such a step (values near 1e-40) are subnormal and CG stalls.  The load is small
+    # enough that the energy-driven part of the phase field is below 1e-8 (the slit's own
+    # profile is the same in both), and the staggered test, which is absolute, is loose so
+    # that both steps take one pass.
+    spec = S.tensile(64, l=0.08, steps=1, u_max=1e-8)
+    out = []
+    for scale in (1.0, 2.0 ** -60):
+        sim = binding.Simulation(spec, precision=binding.FP32_IR, precond=precond)
+        r = sim.load_step(1e-8 * scale, 0, 1.0)
+        u, d, H = sim.fields()
+        out.append((r, u / scale))
+        sim.close()
+    (ra, ua), (rb, ub) = out
+    assert ra["converged"] == rb["converged"] == 1
+    assert ra["stag_iters"] == rb["stag_iters"] == 1
+    assert abs(ra["lin_u"] - rb["lin_u"]) <= 0.1 * ra["lin_u"] + 16
+    assert np.allclose(ua, ub, rtol=1e-6, atol=1e-6 * np.abs(ua).max())
+    assert rb["reaction"] * 2.0 ** 60 == pytest.approx(ra["reaction"], rel=1e-6)
