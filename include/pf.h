@@ -85,7 +85,8 @@ typedef struct {
 typedef struct {
   double tol_nr;     /* [1e-7] Newton stop: ||R_free|| <= tol_nr*max(||R0_free||, ||F_constr||)
                         (TOL_NR of Sec. 4) */
-  double tol_lin;    /* [1e-10] relative residual of every FP64 linear solve */
+  double tol_lin;    /* [1e-10] relative residual of every linear solve (d-solves; u-solves
+                        when newton_forcing is 0) */
   double tol_inner;  /* [1e-4] relative residual of one FP32 inner solve (PF_FP32_IR) */
   int max_newton;    /* [50] Newton iterations per u-solve */
   int max_stag;      /* [1000] staggered iterations per load step */
@@ -93,7 +94,14 @@ typedef struct {
   int max_refine;    /* [30] FP64 refinement sweeps per linear solve (PF_FP32_IR) */
   double psi_crit;   /* [-1] < 0: G_c/(c_w l) of Sec. 3.5; else the given threshold */
   int project;       /* [0] 1: clamp d into [d_{n-1}, 1] after every d-solve */
-  int check_every;   /* [8] Krylov iterations between convergence reads */
+  int check_every;   /* [8] Krylov iterations between host convergence reads; used only
+                        where the device-side Krylov loop (CUDA graph conditional node) is
+                        unavailable */
+  double newton_forcing; /* [1e-3] inexact Newton for u: the correction at residual R_k is
+                        solved to the relative residual max(tol_lin, min(1e-2,
+                        newton_forcing * tol_nr * max(||R0||, ||F_constr||) / ||R_k||)), so
+                        that the linear residual stays below the Newton tolerance; 0 solves
+                        every correction to tol_lin */
 } pf_options;
 
 typedef struct {

@@ -15,40 +15,11 @@ __device__ __forceinline__ double gmg_gp(int hi) {
   return hi ? 0.78867513459481288225 : 0.21132486540518711775;
 }
 
-__device__ __forceinline__ double g_warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
 
-// Max over the grid into *out (last-CTA pattern, deterministic).
+// Max over the grid into *out (red_grid, deterministic).
 __device__ void grid_max(double v, const RedWs ws, double *out) {
-  __shared__ double sh[32];
-  __shared__ bool am_last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  v = g_warp_max(v);
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = sh[0];
-    for (int w = 1; w < nw; ++w) s = fmax(s, sh[w]);
-    ws.partials[blockIdx.x] = s;
-    am_last = red_arrive(ws.counter, blockIdx.x, gridDim.x);
-  }
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  double s = 0.0;
-  for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) s = fmax(s, __ldcg(ws.partials + i));
-  s = g_warp_max(s);
-  __syncthreads();
-  if (lane == 0) sh[warp] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = sh[0];
-    for (int w = 1; w < nw; ++w) t = fmax(t, sh[w]);
-    *out = t;
-  }
+  double a[1] = {v}, t[1];
+  if (red_grid<1>(a, ws, t, true)) *out = t[0];
 }
 
 inline unsigned nblk(size_t n, int cap = 1 << 16) {
@@ -354,26 +325,101 @@ __global__ void k_sten_apply(int nx, int ny, const T *__restrict__ S,
   }
 }
 
-// Fused Chebyshev step on a stencil level: y = A d_in; r -= y; d_out = c1 d_in +
-// c2/(0.45 lmax) D^-1 r; x += d_out.  d is double-buffered (neighbours read d_in).
+
+// ---- fused smoothing kernels of the grid-wide stencil levels ------------------------------
+// Pre-smoothing from x = 0 in one pass: d0 = it D^-1 b is formed at the neighbours, so
+// x = d0 + c1 d0 + c2 D^-1 (b - A d0) needs no stored d0 or residual.
 template <class T, int B>
-__global__ void k_sten_cheb(int nx, int ny, const T *__restrict__ S, const T *__restrict__ invd,
-                            const T *coef, const T *__restrict__ din, T *__restrict__ dout,
-                            T *__restrict__ x, T *__restrict__ r) {
+__global__ void k_sten_pre(int nx, int ny, const T *__restrict__ S, const T *__restrict__ invd,
+                           const T *coef, const uint8_t *__restrict__ fm, const T *__restrict__ b,
+                           T *__restrict__ x) {
   const size_t nn = (size_t)(nx + 1) * (ny + 1);
-  const T a = coef[2], bb = coef[1];
+  const T it = coef[0], c2 = coef[1], c1 = coef[2];
   for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
        n += (size_t)gridDim.x * blockDim.x) {
     T acc[B];
-    sten_row<T, B>(nx, ny, nn, S, din, n, acc);
+    sten_row_by<T, B>(nx, ny, nn, S, n,
+                      [=](size_t q) { return __ldg(invd + q) * __ldg(b + q) * it; }, acc);
+    const uint8_t f = __ldg(fm + n);
 #pragma unroll
     for (int c = 0; c < B; ++c) {
       const size_t i = B * n + c;
-      const T ri = r[i] - acc[c];
-      const T di = a * din[i] + bb * invd[i] * ri;
+      const T iv = __ldg(invd + i), bi = __ldg(b + i);
+      const T d0 = iv * bi * it;
+      const T d1 = c1 * d0 + c2 * iv * (bi - acc[c]);
+      x[i] = ((f >> c) & 1) ? d0 + d1 : T(0);
+    }
+  }
+}
+
+// Bilinear prolongation of the coarse correction at fine node (ix, iy), component c.
+template <class T, int B>
+__device__ __forceinline__ T prolong_at(int ix, int iy, int nxc, int nyc, const T *__restrict__ xc,
+                                        int c) {
+  const int px0 = ix >> 1, py0 = iy >> 1;
+  const int px1 = px0 + 1 <= nxc ? px0 + 1 : nxc, py1 = py0 + 1 <= nyc ? py0 + 1 : nyc;
+  const T wx1 = (ix & 1) ? T(0.5) : T(0), wx0 = T(1) - wx1;
+  const T wy1 = (iy & 1) ? T(0.5) : T(0), wy0 = T(1) - wy1;
+  const size_t J00 = (size_t)py0 * (nxc + 1) + px0, J01 = (size_t)py0 * (nxc + 1) + px1;
+  const size_t J10 = (size_t)py1 * (nxc + 1) + px0, J11 = (size_t)py1 * (nxc + 1) + px1;
+  return wy0 * (wx0 * __ldg(xc + B * J00 + c) + wx1 * __ldg(xc + B * J01 + c)) +
+         wy1 * (wx0 * __ldg(xc + B * J10 + c) + wx1 * __ldg(xc + B * J11 + c));
+}
+
+// Coarse-grid correction and first post-smoothing step in one pass: t = x_in + P x_c on the
+// free components is formed at the neighbours; r = b - A t, d = it D^-1 r, x_out = t + d.
+template <class T, int B>
+__global__ void k_sten_prolong_first(int nx, int ny, const T *__restrict__ S,
+                                     const T *__restrict__ invd, const T *coef,
+                                     const uint8_t *__restrict__ fm, int nxc, int nyc,
+                                     const T *__restrict__ xc, const T *__restrict__ b,
+                                     const T *__restrict__ xin, T *__restrict__ xout,
+                                     T *__restrict__ r, T *__restrict__ d) {
+  const size_t nn = (size_t)(nx + 1) * (ny + 1);
+  const int ld = nx + 1;
+  const T it = coef[0];
+  auto t_at = [=](size_t q) {
+    const size_t m = q / B;
+    const int c = (int)(q - m * B);
+    T v = __ldg(xin + q);
+    if ((__ldg(fm + m) >> c) & 1)
+      v += prolong_at<T, B>((int)(m % ld), (int)(m / ld), nxc, nyc, xc, c);
+    return v;
+  };
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
+       n += (size_t)gridDim.x * blockDim.x) {
+    T acc[B];
+    sten_row_by<T, B>(nx, ny, nn, S, n, t_at, acc);
+    const uint8_t f = __ldg(fm + n);
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      const size_t i = B * n + c;
+      const T ri = ((f >> c) & 1) ? __ldg(b + i) - acc[c] : T(0);
+      const T di = __ldg(invd + i) * ri * it;
       r[i] = ri;
-      dout[i] = di;
-      x[i] += di;
+      d[i] = di;
+      xout[i] = t_at(i) + di;
+    }
+  }
+}
+
+// Second post-smoothing step: x += c1 d + c2 D^-1 (r - A d).
+template <class T, int B>
+__global__ void k_sten_post(int nx, int ny, const T *__restrict__ S, const T *__restrict__ invd,
+                            const T *coef, const uint8_t *__restrict__ fm, const T *__restrict__ d,
+                            const T *__restrict__ r, T *__restrict__ x) {
+  const size_t nn = (size_t)(nx + 1) * (ny + 1);
+  const T c2 = coef[1], c1 = coef[2];
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
+       n += (size_t)gridDim.x * blockDim.x) {
+    T acc[B];
+    sten_row<T, B>(nx, ny, nn, S, d, n, acc);
+    const uint8_t f = __ldg(fm + n);
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      const size_t i = B * n + c;
+      const T ri = __ldg(r + i) - (((f >> c) & 1) ? acc[c] : T(0));
+      x[i] = x[i] + (c1 * __ldg(d + i) + c2 * __ldg(invd + i) * ri);
     }
   }
 }
@@ -665,17 +711,6 @@ __global__ void k_prolong_add(int nxf, int nyf, const uint8_t *__restrict__ fmf,
   }
 }
 
-// x = Cinv b (dense, one CTA).
-template <class T>
-__global__ void k_dense(int nc, const T *__restrict__ Cinv, const T *__restrict__ b,
-                        T *__restrict__ x) {
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-    double s = 0.0;
-    for (int j = 0; j < nc; ++j) s += (double)Cinv[(size_t)i * nc + j] * (double)b[j];
-    x[i] = (T)s;
-  }
-}
-
 // FP64 host Cholesky inverse of an SPD matrix (in place); non-positive pivots are
 // lifted to a small fraction of the largest diagonal entry.
 void host_spd_inverse(double *A, int n) {
@@ -734,7 +769,6 @@ cudaError_t gmg_alloc(Gmg<T> &G, int nx, int ny, int B, const RedWs &ws) {
     if ((e = cudaMalloc(&L.r, nb * sizeof(T))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&L.dv, nb * sizeof(T))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&L.y, nb * sizeof(T))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&L.dv2, nb * sizeof(T))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&L.fm, L.nn)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&L.lmax, sizeof(double))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&L.coef, 4 * sizeof(T))) != cudaSuccess) return e;
@@ -766,7 +800,7 @@ size_t gmg_bytes(int nx, int ny, int B, size_t tsize) {
   size_t last_nn = 0;
   while (true) {
     const size_t nn = (size_t)(cx + 1) * (cy + 1);
-    total += 9 * B * B * nn * tsize + 6 * B * nn * tsize + nn + sizeof(double) + 4 * tsize;
+    total += 9 * B * B * nn * tsize + 5 * B * nn * tsize + nn + sizeof(double) + 4 * tsize;
     last_nn = nn;
     ++l;
     if ((cx <= GMG_COARSE_MAX && cy <= GMG_COARSE_MAX) || l == GMG_MAX_LEVELS) break;
@@ -781,7 +815,7 @@ template <class T>
 void gmg_free(Gmg<T> &G) {
   for (int l = 0; l < G.nl; ++l) {
     GmgLevel<T> &L = G.lv[l];
-    void *p[] = {L.S, L.invd, L.x, L.b, L.r, L.dv, L.dv2, L.y, L.fm, L.lmax, L.coef};
+    void *p[] = {L.S, L.invd, L.x, L.b, L.r, L.dv, L.y, L.fm, L.lmax, L.coef};
     for (void *q : p)
       if (q) cudaFree(q);
     L = GmgLevel<T>();
@@ -931,16 +965,34 @@ void gmg_prolong_add(const Gmg<T> &G, int l, const T *xc, T *xf, cudaStream_t st
     k_prolong_add<T, 1><<<nblk(F.nn), 256, 0, st>>>(F.nx, F.ny, F.fm, C.nx, xc, xf);
 }
 template <class T>
-void gmg_dense(const Gmg<T> &G, const T *b, T *x, cudaStream_t st) {
-  k_dense<T><<<1, 256, 0, st>>>(G.ncoarse, G.cinv, b, x);
-}
-template <class T>
-void gmg_sten_cheb(const Gmg<T> &G, int l, const T *din, T *dout, T *x, T *r, cudaStream_t st) {
+void gmg_pre(const Gmg<T> &G, int l, const T *b, T *x, cudaStream_t st) {
   const GmgLevel<T> &L = G.lv[l];
   if (G.B == 2)
-    k_sten_cheb<T, 2><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.coef, din, dout, x, r);
+    k_sten_pre<T, 2><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.coef, L.fm, b, x);
   else
-    k_sten_cheb<T, 1><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.coef, din, dout, x, r);
+    k_sten_pre<T, 1><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.coef, L.fm, b, x);
+}
+template <class T>
+void gmg_prolong_first(const Gmg<T> &G, int l, const T *xin, T *xout, cudaStream_t st) {
+  const GmgLevel<T> &L = G.lv[l], &C = G.lv[l + 1];
+  if (G.B == 2)
+    k_sten_prolong_first<T, 2><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.coef, L.fm,
+                                                           C.nx, C.ny, C.x, L.b, xin, xout, L.r,
+                                                           L.dv);
+  else
+    k_sten_prolong_first<T, 1><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.coef, L.fm,
+                                                           C.nx, C.ny, C.x, L.b, xin, xout, L.r,
+                                                           L.dv);
+}
+template <class T>
+void gmg_post(const Gmg<T> &G, int l, T *x, cudaStream_t st) {
+  const GmgLevel<T> &L = G.lv[l];
+  if (G.B == 2)
+    k_sten_post<T, 2><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.coef, L.fm, L.dv,
+                                                  L.r, x);
+  else
+    k_sten_post<T, 1><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.coef, L.fm, L.dv,
+                                                  L.r, x);
 }
 template <class T>
 void gmg_coarse_cycle(const Gmg<T> &G, int lc, const T *b0, T *x0, cudaStream_t st) {
@@ -976,9 +1028,10 @@ void gmg_coarse_cycle(const Gmg<T> &G, int lc, const T *b0, T *x0, cudaStream_t 
   template void gmg_sub<T>(size_t, const T *, const T *, T *, cudaStream_t);                    \
   template void gmg_restrict<T>(const Gmg<T> &, int, const T *, T *, cudaStream_t);             \
   template void gmg_prolong_add<T>(const Gmg<T> &, int, const T *, T *, cudaStream_t);          \
-  template void gmg_dense<T>(const Gmg<T> &, const T *, T *, cudaStream_t);                     \
-  template void gmg_sten_cheb<T>(const Gmg<T> &, int, const T *, T *, T *, T *, cudaStream_t);  \
-  template void gmg_coarse_cycle<T>(const Gmg<T> &, int, const T *, T *, cudaStream_t);
+  template void gmg_coarse_cycle<T>(const Gmg<T> &, int, const T *, T *, cudaStream_t);      \
+  template void gmg_pre<T>(const Gmg<T> &, int, const T *, T *, cudaStream_t);                 \
+  template void gmg_prolong_first<T>(const Gmg<T> &, int, const T *, T *, cudaStream_t);       \
+  template void gmg_post<T>(const Gmg<T> &, int, T *, cudaStream_t);
 GMG_INST(double)
 GMG_INST(float)
 

@@ -27,7 +27,7 @@ struct GmgLevel {
   size_t nn = 0;
   T *S = nullptr;       // 9*B*B*nn stencil (SoA: entry-major), levels >= 0
   T *invd = nullptr;    // B*nn inverse diagonal (0 on constrained / empty DOFs)
-  T *x = nullptr, *b = nullptr, *r = nullptr, *dv = nullptr, *dv2 = nullptr, *y = nullptr;
+  T *x = nullptr, *b = nullptr, *r = nullptr, *dv = nullptr, *y = nullptr;
   uint8_t *fm = nullptr;   // nn bytes, bit c: component c free on this level
   double *lmax = nullptr;  // device scalar
   T *coef = nullptr;       // Chebyshev coefficients in T (see k_cheb_coef)
@@ -83,64 +83,66 @@ void gmg_restrict(const Gmg<T> &G, int l, const T *rf, T *bc, cudaStream_t st);
 template <class T>
 void gmg_prolong_add(const Gmg<T> &G, int l, const T *xc, T *xf, cudaStream_t st);
 template <class T>
-void gmg_dense(const Gmg<T> &G, const T *b, T *x, cudaStream_t st);
-template <class T>
-void gmg_sten_cheb(const Gmg<T> &G, int l, const T *din, T *dout, T *x, T *r, cudaStream_t st);
-template <class T>
 void gmg_coarse_cycle(const Gmg<T> &G, int lc, const T *b0, T *x0, cudaStream_t st);
+// Fused smoothing passes of a stencil level l (see pf_gmg.cu): pre-smoothing from zero
+// (x = S_pre b), coarse-grid correction plus first post step (reads lv[l+1].x, writes
+// lv[l].r and lv[l].dv), second post step on lv[l].dv and lv[l].r.
+template <class T>
+void gmg_pre(const Gmg<T> &G, int l, const T *b, T *x, cudaStream_t st);
+template <class T>
+void gmg_prolong_first(const Gmg<T> &G, int l, const T *xin, T *xout, cudaStream_t st);
+template <class T>
+void gmg_post(const Gmg<T> &G, int l, T *x, cudaStream_t st);
 
-// z = V(r): one V-cycle (Chebyshev degree 2 pre and post) on the fine residual r.
-// fine_apply(x, y) must compute y = A_0 x with constrained rows/columns zeroed.  Levels
-// below G.lc run as separate grid-wide kernels; levels from G.lc down to the dense
-// solve run in one single-CTA kernel.  Returns the number of kernel launches issued.
-template <class T, class FineApply>
-int gmg_vcycle(Gmg<T> &G, FineApply fine_apply, const T *r, T *z, cudaStream_t st) {
+// lv[l0].x = V_l0(lv[l0].b) for l0 >= 1: the V-cycle below level l0 - 1 on stencil
+// levels.  Levels l0 .. G.lc - 1 run as separate grid-wide kernels; levels from G.lc down
+// to the dense solve run in one single-CTA kernel.  Returns the kernel launches issued.
+template <class T>
+int gmg_mid(Gmg<T> &G, int l0, cudaStream_t st) {
   int launches = 0;
-  const int lc = G.lc;
-  for (int l = 0; l < lc; ++l) {
+  const int lc = G.lc > l0 ? G.lc : l0;
+  // down: pre-smoothed iterate in lv[l].y, residual restricted to lv[l+1].b
+  for (int l = l0; l < lc; ++l) {
     GmgLevel<T> &L = G.lv[l];
-    const T *b = (l == 0) ? r : L.b;
-    T *x = (l == 0) ? z : L.x;
-    gmg_cheb_first<T>(G, l, b, x, L.dv, L.r, st);
-    if (l == 0) {
-      fine_apply(L.dv, L.y);
-      gmg_cheb_step<T>(G, 0, L.y, x, L.dv, L.r, st);
-      fine_apply(x, L.y);
-      gmg_sub<T>((size_t)G.B * L.nn, b, L.y, L.r, st);
-      launches += 5;
-    } else {
-      gmg_sten_cheb<T>(G, l, L.dv, L.dv2, x, L.r, st);
-      gmg_sten_apply<T>(G, l, x, b, L.r, 1, st);
-      launches += 3;
-    }
+    gmg_pre<T>(G, l, L.b, L.y, st);
+    gmg_sten_apply<T>(G, l, L.y, L.b, L.r, 1, st);
     gmg_restrict<T>(G, l, L.r, G.lv[l + 1].b, st);
-    ++launches;
+    launches += 3;
   }
-  {
-    const T *b0 = lc == 0 ? r : G.lv[lc].b;
-    T *x0 = lc == 0 ? z : G.lv[lc].x;
-    gmg_coarse_cycle<T>(G, lc, b0, x0, st);
-    ++launches;
-  }
-  for (int l = lc - 1; l >= 0; --l) {
-    GmgLevel<T> &L = G.lv[l];
-    const T *b = (l == 0) ? r : L.b;
-    T *x = (l == 0) ? z : L.x;
-    gmg_prolong_add<T>(G, l, G.lv[l + 1].x, x, st);
-    if (l == 0) {
-      fine_apply(x, L.y);
-      gmg_cheb_first_x<T>(G, 0, b, L.y, x, L.dv, L.r, st);
-      fine_apply(L.dv, L.y);
-      gmg_cheb_step<T>(G, 0, L.y, x, L.dv, L.r, st);
-      launches += 5;
-    } else {
-      gmg_sten_apply<T>(G, l, x, nullptr, L.y, 0, st);
-      gmg_cheb_first_x<T>(G, l, b, L.y, x, L.dv, L.r, st);
-      gmg_sten_cheb<T>(G, l, L.dv, L.dv2, x, L.r, st);
-      launches += 4;
-    }
+  gmg_coarse_cycle<T>(G, lc, G.lv[lc].b, G.lv[lc].x, st);
+  ++launches;
+  // up: corrected and post-smoothed iterate in lv[l].x
+  for (int l = lc - 1; l >= l0; --l) {
+    gmg_prolong_first<T>(G, l, G.lv[l].y, G.lv[l].x, st);
+    gmg_post<T>(G, l, G.lv[l].x, st);
+    launches += 2;
   }
   return launches;
+}
+
+// z = V(r): one V-cycle (Chebyshev degree 2 pre and post) on the fine residual r.
+// fine_apply(x, y) must compute y = A_0 x with constrained rows/columns zeroed; level 0 is
+// applied matrix-free, coarser levels through gmg_mid.  Returns the kernel launches issued.
+template <class T, class FineApply>
+int gmg_vcycle(Gmg<T> &G, FineApply fine_apply, const T *r, T *z, cudaStream_t st) {
+  if (G.lc == 0) {
+    gmg_coarse_cycle<T>(G, 0, r, z, st);
+    return 1;
+  }
+  GmgLevel<T> &L = G.lv[0];
+  gmg_cheb_first<T>(G, 0, r, z, L.dv, L.r, st);
+  fine_apply(L.dv, L.y);
+  gmg_cheb_step<T>(G, 0, L.y, z, L.dv, L.r, st);
+  fine_apply(z, L.y);
+  gmg_sub<T>((size_t)G.B * L.nn, r, L.y, L.r, st);
+  gmg_restrict<T>(G, 0, L.r, G.lv[1].b, st);
+  int launches = 6 + gmg_mid<T>(G, 1, st);
+  gmg_prolong_add<T>(G, 0, G.lv[1].x, z, st);
+  fine_apply(z, L.y);
+  gmg_cheb_first_x<T>(G, 0, r, L.y, z, L.dv, L.r, st);
+  fine_apply(L.dv, L.y);
+  gmg_cheb_step<T>(G, 0, L.y, z, L.dv, L.r, st);
+  return launches + 5;
 }
 
 }  // namespace pf

@@ -28,16 +28,18 @@ struct MatD {
 };
 
 // Device scalars of one Krylov solve.  The last CTA of each fused reduction updates
-// them, so the host never sits between iterations.
+// them, so the host never sits between iterations; a device-side loop reads rtol2 and
+// maxit (written by the host before the solve) and counts passes in it.
 struct KrylovScal {
-  double rz;       // CG: r.z ;  MINRES: gamma_j
-  double pq;       // CG: p.q ;  MINRES: delta_j
-  double alpha;    // CG step
-  double beta;     // CG direction update
-  double rr;       // ||r||^2 (CG) or eta^2 (MINRES)
-  double rz_new;
-  // MINRES recurrences
-  double gam_old, c, c_old, s, s_old, eta, a1, a2, a3, cn;
+  double rz;     // r.z
+  double pq;     // p.q
+  double alpha;  // CG step
+  double beta;   // CG direction update
+  double rr;     // ||r||^2
+  double rr0;    // ||r||^2 after the initialisation
+  double rtol2;  // stop when rr <= rtol2 rr0
+  int maxit;     // stop after maxit iterations
+  int it;        // iterations done
   int breakdown;
   int pad;
 };
@@ -54,20 +56,96 @@ constexpr int RED_GROUP = 64;
 inline size_t red_counters(int max_blocks) { return 2 + (size_t)max_blocks / RED_GROUP; }
 
 #ifdef __CUDACC__
-// Arrival of CTA `bid` of `nblk` after it published its partials (thread 0 only).  CTAs
-// arrive in groups of RED_GROUP; the last CTA of a group arrives at the top counter, so
-// no single counter takes more than RED_GROUP atomics.  Returns true in exactly one CTA,
-// the last to arrive overall; counters are reset for the next launch.
-__device__ __forceinline__ bool red_arrive(unsigned *counter, unsigned bid, unsigned nblk) {
-  const unsigned g = bid / RED_GROUP;
-  const unsigned ng = (nblk + RED_GROUP - 1) / RED_GROUP;
-  const unsigned gsize = (g + 1) * RED_GROUP <= nblk ? RED_GROUP : nblk - g * RED_GROUP;
+__device__ __forceinline__ double red_warp(double v, bool is_max) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = is_max ? fmax(v, w) : v + w;
+  }
+  return v;
+}
+
+// CTA-wide sum (or max) of NV values per thread; thread 0 receives the totals in v.  The
+// order is fixed (xor tree in each warp, warps in index order).  sh: NV x 32 shared slots.
+template <int NV>
+__device__ __forceinline__ void red_cta(double (&v)[NV], double (*sh)[32], bool is_max) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const double s = red_warp(v[k], is_max);
+    if (lane == 0) sh[k][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = sh[k][0];
+      for (int w = 1; w < nw; ++w) s = is_max ? fmax(s, sh[k][w]) : s + sh[k][w];
+      v[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// Grid-wide sum (or max) of NV values, deterministic and without a second launch.  Every
+// CTA publishes its partials and arrives on the counter of its group of RED_GROUP CTAs; the
+// last CTA of a group sums the group's partials (one load per thread) into the group's
+// first slot and arrives on the top counter; the last group's CTA sums the group totals.
+// Each step reads its inputs in one round of loads.  Returns true in thread 0 of that
+// final CTA, with tot[] holding the totals; counters are reset for the next launch.
+// Every CTA of the grid must call it.
+template <int NV>
+__device__ bool red_grid(double (&v)[NV], const RedWs ws, double (&tot)[NV], bool is_max) {
+  __shared__ double sh[NV][32];
+  __shared__ int go;
+  const unsigned nblk = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
+  const unsigned g = bid / RED_GROUP, ng = (nblk + RED_GROUP - 1) / RED_GROUP;
+  const unsigned g0 = g * RED_GROUP, gsize = nblk - g0 < RED_GROUP ? nblk - g0 : RED_GROUP;
+  const double none = is_max ? -INFINITY : 0.0;
+  const size_t mb = (size_t)ws.max_blocks;
+  red_cta<NV>(v, sh, is_max);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) ws.partials[k * mb + bid] = v[k];
+    __threadfence();
+    go = atomicAdd(ws.counter + 1 + g, 1u) == gsize - 1;
+  }
+  __syncthreads();
+  if (!go) return false;
   __threadfence();
-  if (atomicAdd(counter + 1 + g, 1u) != gsize - 1) return false;
-  counter[1 + g] = 0u;
+  double w[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    w[k] = none;
+    for (unsigned i = threadIdx.x; i < gsize; i += blockDim.x) {
+      const double p = __ldcg(ws.partials + k * mb + g0 + i);
+      w[k] = is_max ? fmax(w[k], p) : w[k] + p;
+    }
+  }
+  red_cta<NV>(w, sh, is_max);
+  if (threadIdx.x == 0) {
+    ws.counter[1 + g] = 0u;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) ws.partials[k * mb + g0] = w[k];
+    __threadfence();
+    go = atomicAdd(ws.counter, 1u) == ng - 1;
+  }
+  __syncthreads();
+  if (!go) return false;
   __threadfence();
-  if (atomicAdd(counter, 1u) != ng - 1) return false;
-  counter[0] = 0u;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    w[k] = none;
+    for (unsigned i = threadIdx.x; i < ng; i += blockDim.x) {
+      const double p = __ldcg(ws.partials + k * mb + (size_t)i * RED_GROUP);
+      w[k] = is_max ? fmax(w[k], p) : w[k] + p;
+    }
+  }
+  red_cta<NV>(w, sh, is_max);
+  if (threadIdx.x != 0) return false;
+  ws.counter[0] = 0u;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) tot[k] = w[k];
   return true;
 }
 #endif
@@ -107,6 +185,27 @@ void dof_mask(int nx, int ny, const uint8_t *flags, const uint8_t *active, uint8
               cudaStream_t st);
 
 // Epilogues of the fused operator + reduction kernels.
-enum { EPI_NONE = 0, EPI_CG_ALPHA = 1, EPI_MINRES_DELTA = 2 };
+enum { EPI_NONE = 0, EPI_CG_ALPHA = 1 };
+
+// Buffers of the multigrid-preconditioned CG on the elasticity tangent whose fine-level
+// work runs fused into the strip apply (elas_mg_stage).  Vectors have 2 (nx+1)(ny+1)
+// entries, interleaved (u_x, u_y) per node.
+template <class T>
+struct ElasMgBufs {
+  const T *b;              // right-hand side
+  T *x;                    // iterate
+  T *r[2], *p[2];          // [0]: previous iterate's residual / direction, [1]: current
+  T *q, *za, *zb, *lr, *dv;  // A p; pre-smoothed z; preconditioned residual; level-0 scratch
+  const T *invd, *coef;    // level-0 inverse diagonal and Chebyshev coefficients
+  const uint8_t *fm;       // level-0 free-component mask
+  const T *xc;             // level-1 correction
+  int nxc, nyc;            // level-1 elements per direction
+  KrylovScal *sc;
+};
+enum { FS_DIR, FS_UPD, FS_UPD_INIT, FS_RESID, FS_PROLONG, FS_FINISH, FS_FINISH_FIRST };
+// One fused stage (see pf_ops.cu).
+template <class T>
+void elas_mg_stage(int stage, const GridD &g, const MatD &m, const T *d, const uint8_t *tens,
+                   const ElasMgBufs<T> &b, const RedWs &ws, cudaStream_t st);
 
 }  // namespace pf

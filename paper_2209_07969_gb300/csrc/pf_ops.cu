@@ -37,73 +37,19 @@ __device__ __forceinline__ void ld_pair(const double *x, size_t n, double &a, do
 }
 
 // ------------------------------------------------------------------------------------
-// Reductions: warp shuffle -> CTA -> per-CTA partials -> last-arriving CTA sums the
-// partials in a fixed order (deterministic) and runs an epilogue on the totals.
+// Reductions: warp shuffle -> CTA -> per-CTA partials -> grouped two-level sum in the last
+// arriving CTAs (red_grid; fixed order, deterministic) -> epilogue on the totals.
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
 
-// Sums NV values over the whole grid.  Returns true in thread 0 of the last CTA, with
-// tot[] holding the totals; all other threads return false.  blockDim.x must be a
-// multiple of 32 and at most 1024.  `is_max` selects max instead of sum.
+// Sums NV values over the whole grid (red_grid).  Returns true in thread 0 of the last CTA,
+// with tot[] holding the totals; all other threads return false.
 template <int NV>
-__device__ bool grid_reduce(double (&v)[NV], const RedWs ws, double (&tot)[NV],
-                            bool is_max = false) {
-  __shared__ double sh[NV][32];
-  __shared__ bool am_last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-  const unsigned nblk = gridDim.x * gridDim.y;
-  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double s = is_max ? warp_max(v[k]) : warp_sum(v[k]);
-    if (lane == 0) sh[k][warp] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double s = sh[k][0];
-      for (int w = 1; w < nw; ++w) s = is_max ? fmax(s, sh[k][w]) : s + sh[k][w];
-      ws.partials[k * ws.max_blocks + bid] = s;
-    }
-    am_last = red_arrive(ws.counter, bid, nblk);
-  }
-  __syncthreads();
-  if (!am_last) return false;
-  __threadfence();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double s = is_max ? -INFINITY : 0.0;
-    for (unsigned i = threadIdx.x; i < nblk; i += blockDim.x) {
-      double p = __ldcg(ws.partials + k * ws.max_blocks + i);
-      s = is_max ? fmax(s, p) : s + p;
-    }
-    s = is_max ? warp_max(s) : warp_sum(s);
-    __syncthreads();
-    if (lane == 0) sh[k][warp] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return false;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double s = sh[k][0];
-    for (int w = 1; w < nw; ++w) s = is_max ? fmax(s, sh[k][w]) : s + sh[k][w];
-    tot[k] = s;
-  }
-  return true;
+__device__ __forceinline__ bool grid_reduce(double (&v)[NV], const RedWs ws, double (&tot)[NV],
+                                            bool is_max = false) {
+  return red_grid<NV>(v, ws, tot, is_max);
 }
 
-// Epilogue for the fused matvec + dot: CG step length, or MINRES delta.
+// Epilogue for the fused matvec + dot: CG step length.
 __device__ __forceinline__ void krylov_epilogue(int epi, KrylovScal *sc, double dot) {
   if (epi == EPI_CG_ALPHA) {
     sc->pq = dot;
@@ -113,8 +59,6 @@ __device__ __forceinline__ void krylov_epilogue(int epi, KrylovScal *sc, double 
       sc->alpha = 0.0;
       sc->breakdown = 1;
     }
-  } else if (epi == EPI_MINRES_DELTA) {
-    sc->pq = dot;
   }
 }
 
@@ -333,19 +277,61 @@ k_elas(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restr
 constexpr int SW = 30;          // output node columns per warp
 constexpr int STRIP_WARPS = 4;  // warps per CTA
 
+template <class T>
+__device__ __forceinline__ void st_pair(T *y, size_t n, T a, T b) {
+  if (sizeof(T) == 4) {
+    reinterpret_cast<float2 *>(y)[n] = make_float2((float)a, (float)b);
+  } else {
+    reinterpret_cast<double2 *>(y)[n] = make_double2((double)a, (double)b);
+  }
+}
+// Plain (coherent) load of a pair the same thread rewrites in the same launch.
+template <class T>
+__device__ __forceinline__ void ld_pair_rw(const T *y, size_t n, T &a, T &b) {
+  a = y[2 * n];
+  b = y[2 * n + 1];
+}
+
+// Input / output policies of the strip kernel.  in(n, i, j, a, b) forms both components of
+// the operand at node n = (i, j) (constrained components are zeroed by the kernel);
+// out(n, ox, oy, cx, cy, acc) receives the masked product (ox, oy) = (A x)_n and the
+// operand (cx, cy) at its node; NR values summed over all nodes go to fin() in the last CTA.
+// Every node is output by exactly one lane, so out() may rewrite buffers at its own node;
+// buffers read by in() are never written in the same launch.
+template <class T>
+struct OpApply {  // y = A x (+ x.y for the Krylov epilogue)
+  static constexpr int NR = 1;
+  const T *x;
+  T *y;
+  KrylovScal *sc;
+  int epi;
+  __device__ void begin() {}
+  __device__ void in(size_t n, int, int, T &a, T &b) const { ld_pair(x, n, a, b); }
+  __device__ void out(size_t n, T ox, T oy, T cx, T cy, T (&acc)[1]) const {
+    st_pair(y, n, ox, oy);
+    acc[0] += cx * ox + cy * oy;
+  }
+  __device__ bool reduce() const { return epi != EPI_NONE; }
+  __device__ void fin(const double (&tot)[1]) const { krylov_epilogue(epi, sc, tot[0]); }
+};
+
 // SR node rows per warp: short strips on small grids (more warps to hide latency), long
 // strips on large ones (less halo re-reading).
-template <class T, int SR>
+template <class T, int SR, class Op>
 __global__ void __launch_bounds__(32 * STRIP_WARPS)
 k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restrict__ tens,
-             const T *__restrict__ x, T *__restrict__ y, KrylovScal *sc, RedWs ws, int epi) {
+             Op op, RedWs ws) {
+  constexpr int NR = Op::NR > 0 ? Op::NR : 1;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int nx = g.nx, ny = g.ny, ld = nx + 1;
   const int nstrips = (nx + 1 + SW - 1) / SW, nchunks = (ny + 1 + SR - 1) / SR;
   const int gw = blockIdx.x * STRIP_WARPS + (threadIdx.x >> 5);
   const int strip = gw % nstrips, chunk = gw / nstrips;
-  T dot = T(0);
+  op.begin();
+  T acc[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) acc[k] = T(0);
   if (chunk < nchunks) {
     const int i = strip * SW - 1 + lane;
     const int r0 = chunk * SR;
@@ -354,7 +340,7 @@ k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *_
       vx = vy = vd = T(0);
       if (col_ok && j >= 0 && j <= ny) {
         const size_t n = (size_t)j * ld + i;
-        ld_pair(x, n, vx, vy);
+        op.in(n, i, j, vx, vy);
         vd = ldg(d + n);
         if (g.dofm) {
           const uint8_t mk = ldg(g.dofm + n);
@@ -366,6 +352,7 @@ k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *_
     T cx, cy, cdv;
     load(r0 - 1, cx, cy, cdv);
     T carry_x = T(0), carry_y = T(0);
+#pragma unroll
     for (int j = r0 - 1; j < r0 + SR; ++j) {
       T nxv, nyv, ndv;
       load(j + 1, nxv, nyv, ndv);
@@ -393,12 +380,7 @@ k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *_
           if (mk & 1) ox = T(0);
           if (mk & 2) oy = T(0);
         }
-        if (sizeof(T) == 4) {
-          reinterpret_cast<float2 *>(y)[n] = make_float2((float)ox, (float)oy);
-        } else {
-          reinterpret_cast<double2 *>(y)[n] = make_double2((double)ox, (double)oy);
-        }
-        dot += cx * ox + cy * oy;
+        op.out(n, ox, oy, cx, cy, acc);
       }
       carry_x = f[4] + lx3;
       carry_y = f[5] + ly3;
@@ -407,11 +389,207 @@ k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *_
       cdv = ndv;
     }
   }
-  if (epi != EPI_NONE) {
-    double v[1] = {(double)dot}, tot[1];
-    if (grid_reduce<1>(v, ws, tot)) krylov_epilogue(epi, sc, tot[0]);
+  if (Op::NR > 0 && op.reduce()) {
+    double v[NR], tot[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) v[k] = (double)acc[k];
+    if (grid_reduce<NR>(v, ws, tot)) op.fin(tot);
   }
 }
+
+// ---- PCG with the multigrid V-cycle, fine-level work fused into the strip kernel ------------
+// One iteration runs five strip launches (plus the restriction and the coarse levels):
+//   DIR      p = z + beta p_old at the input; q = A p; alpha = rz / p.q
+//   UPD      r = r_old - alpha q, d0 = it D^-1 r at the input; y = A d0;
+//            z_a = d0 + c1 d0 + c2 D^-1 (r - y); x += alpha p; rr = r.r
+//   RESID    r_l = r - A z_a                                   (restricted to level 1)
+//   PROLONG  t = z_a + P x_1 at the input; r_l = r - A t; dv = it D^-1 r_l; z_b = t + dv
+//   FINISH   z_b += c1 dv + c2 D^-1 (r_l - A dv); rz = r.z_b; beta = rz / rz_old
+// Neighbours read r and p of the previous iteration while the current ones are written, so
+// each has two buffers: [0] previous, [1] current; FINISH copies [1] into [0] at its node.
+template <class T>
+struct OpDir {
+  static constexpr int NR = 1;
+  const T *z, *pold;
+  T *pnew, *q;
+  KrylovScal *sc;
+  T beta;
+  __device__ void begin() { beta = (T)sc->beta; }
+  __device__ void in(size_t n, int, int, T &a, T &b) const {
+    T z0, z1, p0, p1;
+    ld_pair(z, n, z0, z1);
+    ld_pair(pold, n, p0, p1);
+    a = z0 + beta * p0;
+    b = z1 + beta * p1;
+  }
+  __device__ void out(size_t n, T ox, T oy, T cx, T cy, T (&acc)[1]) const {
+    st_pair(pnew, n, cx, cy);
+    st_pair(q, n, ox, oy);
+    acc[0] += cx * ox + cy * oy;
+  }
+  __device__ bool reduce() const { return true; }
+  __device__ void fin(const double (&tot)[1]) const { krylov_epilogue(EPI_CG_ALPHA, sc, tot[0]); }
+};
+
+template <class T, bool INIT>
+struct OpUpd {
+  static constexpr int NR = 1;
+  const T *rold, *q, *p, *invd, *coef;
+  T *rnew, *x, *za;
+  KrylovScal *sc;
+  T alpha, it, c2, c1;
+  __device__ void begin() {
+    alpha = INIT ? T(0) : (T)sc->alpha;
+    it = coef[0];
+    c2 = coef[1];
+    c1 = coef[2];
+  }
+  __device__ void rn(size_t n, T &r0, T &r1) const {
+    ld_pair(rold, n, r0, r1);
+    if (!INIT) {
+      T q0, q1;
+      ld_pair(q, n, q0, q1);
+      r0 = r0 - alpha * q0;
+      r1 = r1 - alpha * q1;
+    }
+  }
+  __device__ void in(size_t n, int, int, T &a, T &b) const {
+    T r0, r1, i0, i1;
+    rn(n, r0, r1);
+    ld_pair(invd, n, i0, i1);
+    a = i0 * r0 * it;
+    b = i1 * r1 * it;
+  }
+  __device__ void out(size_t n, T ox, T oy, T cx, T cy, T (&acc)[1]) const {
+    T r0, r1, i0, i1;
+    rn(n, r0, r1);
+    ld_pair(invd, n, i0, i1);
+    const T e0 = c1 * cx + c2 * i0 * (r0 - ox), e1 = c1 * cy + c2 * i1 * (r1 - oy);
+    st_pair(za, n, cx + e0, cy + e1);
+    st_pair(rnew, n, r0, r1);
+    if (INIT) {
+      st_pair(x, n, T(0), T(0));
+    } else {
+      T p0, p1, x0, x1;
+      ld_pair(p, n, p0, p1);
+      ld_pair_rw(x, n, x0, x1);
+      st_pair(x, n, x0 + alpha * p0, x1 + alpha * p1);
+    }
+    acc[0] += r0 * r0 + r1 * r1;
+  }
+  __device__ bool reduce() const { return true; }
+  __device__ void fin(const double (&tot)[1]) const {
+    sc->rr = tot[0];
+    if (INIT) {
+      sc->rr0 = tot[0];
+      sc->it = 0;
+      sc->rz = 0.0;
+      sc->breakdown = 0;
+      sc->alpha = 0.0;
+      sc->beta = 0.0;
+    }
+  }
+};
+
+template <class T>
+struct OpResid {
+  static constexpr int NR = 0;
+  const T *z, *rnew;
+  T *lr;
+  __device__ void begin() {}
+  __device__ void in(size_t n, int, int, T &a, T &b) const { ld_pair(z, n, a, b); }
+  __device__ void out(size_t n, T ox, T oy, T, T, T (&)[1]) const {
+    T r0, r1;
+    ld_pair(rnew, n, r0, r1);
+    st_pair(lr, n, r0 - ox, r1 - oy);
+  }
+  __device__ bool reduce() const { return false; }
+  __device__ void fin(const double (&)[1]) const {}
+};
+
+template <class T>
+struct OpProlong {
+  static constexpr int NR = 0;
+  const T *za, *xc, *rnew, *invd, *coef;
+  const uint8_t *fm;
+  int nxc, nyc;
+  T *zb, *lr, *dv;
+  T it;
+  __device__ void begin() { it = coef[0]; }
+  // t = z_a + P x_1 on the free components (bilinear interpolation, coarse node I on fine 2I)
+  __device__ void in(size_t n, int ix, int iy, T &a, T &b) const {
+    ld_pair(za, n, a, b);
+    const uint8_t m = ldg(fm + n);
+    if (!m) return;
+    const int px0 = ix >> 1, py0 = iy >> 1;
+    const int px1 = px0 + 1 <= nxc ? px0 + 1 : nxc, py1 = py0 + 1 <= nyc ? py0 + 1 : nyc;
+    const T wx1 = (ix & 1) ? T(0.5) : T(0), wx0 = T(1) - wx1;
+    const T wy1 = (iy & 1) ? T(0.5) : T(0), wy0 = T(1) - wy1;
+    const size_t J00 = (size_t)py0 * (nxc + 1) + px0, J01 = (size_t)py0 * (nxc + 1) + px1;
+    const size_t J10 = (size_t)py1 * (nxc + 1) + px0, J11 = (size_t)py1 * (nxc + 1) + px1;
+    T v[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      v[c] = wy0 * (wx0 * ldg(xc + 2 * J00 + c) + wx1 * ldg(xc + 2 * J01 + c)) +
+             wy1 * (wx0 * ldg(xc + 2 * J10 + c) + wx1 * ldg(xc + 2 * J11 + c));
+    if (m & 1) a += v[0];
+    if (m & 2) b += v[1];
+  }
+  __device__ void out(size_t n, T ox, T oy, T cx, T cy, T (&)[1]) const {
+    T r0, r1, i0, i1;
+    ld_pair(rnew, n, r0, r1);
+    ld_pair(invd, n, i0, i1);
+    const T s0 = r0 - ox, s1 = r1 - oy;
+    const T d0 = i0 * s0 * it, d1 = i1 * s1 * it;
+    st_pair(zb, n, cx + d0, cy + d1);
+    st_pair(lr, n, s0, s1);
+    st_pair(dv, n, d0, d1);
+  }
+  __device__ bool reduce() const { return false; }
+  __device__ void fin(const double (&)[1]) const {}
+};
+
+template <class T, bool FIRST>
+struct OpFinish {
+  static constexpr int NR = 1;
+  const T *dv, *lr, *invd, *coef, *rnew, *pnew;
+  T *zb, *rprev, *pprev;
+  KrylovScal *sc;
+  T c2, c1;
+  __device__ void begin() {
+    c2 = coef[1];
+    c1 = coef[2];
+  }
+  __device__ void in(size_t n, int, int, T &a, T &b) const { ld_pair(dv, n, a, b); }
+  __device__ void out(size_t n, T ox, T oy, T cx, T cy, T (&acc)[1]) const {
+    T l0, l1, i0, i1, z0, z1, r0, r1;
+    ld_pair(lr, n, l0, l1);
+    ld_pair(invd, n, i0, i1);
+    ld_pair_rw(zb, n, z0, z1);
+    ld_pair(rnew, n, r0, r1);
+    z0 = z0 + (c1 * cx + c2 * i0 * (l0 - ox));
+    z1 = z1 + (c1 * cy + c2 * i1 * (l1 - oy));
+    st_pair(zb, n, z0, z1);
+    acc[0] += r0 * z0 + r1 * z1;
+    // current residual and direction become the previous ones (the first direction uses
+    // p_prev = 0)
+    st_pair(rprev, n, r0, r1);
+    if (FIRST) {
+      st_pair(pprev, n, T(0), T(0));
+    } else {
+      T p0, p1;
+      ld_pair(pnew, n, p0, p1);
+      st_pair(pprev, n, p0, p1);
+    }
+  }
+  __device__ bool reduce() const { return true; }
+  __device__ void fin(const double (&tot)[1]) const {
+    const double old = sc->rz;
+    sc->beta = (!FIRST && old > 0.0 && isfinite(tot[0])) ? tot[0] / old : 0.0;
+    sc->rz = tot[0];
+    if (!(tot[0] > 0.0)) sc->breakdown = 1;
+  }
+};
 
 // ------------------------------------------------------------------------------------
 // Evolution equation: K_dd apply / diagonal / AT2 right-hand side.
@@ -747,11 +925,9 @@ static inline unsigned elem_blocks(size_t n) {
   return (unsigned)(b < 1 ? 1 : (b > 65535u * 8u ? 65535u * 8u : b));
 }
 
-template <class T>
-void elas_apply(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, const T *x,
-                T *y, cudaStream_t st, KrylovScal *sc, const RedWs *ws, int epi) {
-  RedWs w = ws ? *ws : RedWs{nullptr, nullptr, 0};
-  const int e = ws ? epi : EPI_NONE;
+template <class T, class Op>
+static void strip_launch(const GridD &g, const MatD &m, const T *d, const uint8_t *tens,
+                         const Op &op, const RedWs &w, cudaStream_t st) {
   const size_t nn = (size_t)(g.nx + 1) * (g.ny + 1);
   const unsigned strips = (unsigned)((g.nx + 1 + SW - 1) / SW);
   auto blocks = [&](int sr) {
@@ -760,12 +936,63 @@ void elas_apply(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, 
   };
   const ElemConst<T> kc = elem_const<T>(g, m);
   if (nn < (size_t)1500000)
-    k_elas_strip<T, 2><<<blocks(2), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, x, y, sc, w, e);
+    k_elas_strip<T, 2, Op><<<blocks(2), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
   else if (nn < (size_t)6000000)
-    k_elas_strip<T, 4><<<blocks(4), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, x, y, sc, w, e);
+    k_elas_strip<T, 4, Op><<<blocks(4), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
   else
-    k_elas_strip<T, 8><<<blocks(8), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, x, y, sc, w, e);
+    k_elas_strip<T, 8, Op><<<blocks(8), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
 }
+
+template <class T>
+void elas_apply(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, const T *x,
+                T *y, cudaStream_t st, KrylovScal *sc, const RedWs *ws, int epi) {
+  const RedWs w = ws ? *ws : RedWs{nullptr, nullptr, 0};
+  const int e = ws ? epi : EPI_NONE;
+  strip_launch<T>(g, m, d, tens, OpApply<T>{x, y, sc, e}, w, st);
+}
+
+template <class T>
+void elas_mg_stage(int stage, const GridD &g, const MatD &m, const T *d, const uint8_t *tens,
+                   const ElasMgBufs<T> &B, const RedWs &ws, cudaStream_t st) {
+  T *rprev = B.r[0], *rcur = B.r[1], *pprev = B.p[0], *pcur = B.p[1];
+  switch (stage) {
+    case FS_DIR:
+      strip_launch<T>(g, m, d, tens, OpDir<T>{B.zb, pprev, pcur, B.q, B.sc}, ws, st);
+      break;
+    case FS_UPD:
+      strip_launch<T>(g, m, d, tens,
+                      OpUpd<T, false>{rprev, B.q, pcur, B.invd, B.coef, rcur, B.x, B.za, B.sc},
+                      ws, st);
+      break;
+    case FS_UPD_INIT:
+      strip_launch<T>(g, m, d, tens,
+                      OpUpd<T, true>{B.b, nullptr, nullptr, B.invd, B.coef, rcur, B.x, B.za, B.sc},
+                      ws, st);
+      break;
+    case FS_RESID:
+      strip_launch<T>(g, m, d, tens, OpResid<T>{B.za, rcur, B.lr}, ws, st);
+      break;
+    case FS_PROLONG:
+      strip_launch<T>(g, m, d, tens,
+                      OpProlong<T>{B.za, B.xc, rcur, B.invd, B.coef, B.fm, B.nxc, B.nyc, B.zb,
+                                   B.lr, B.dv},
+                      ws, st);
+      break;
+    case FS_FINISH:
+      strip_launch<T>(g, m, d, tens,
+                      OpFinish<T, false>{B.dv, B.lr, B.invd, B.coef, rcur, pcur, B.zb, rprev,
+                                         pprev, B.sc},
+                      ws, st);
+      break;
+    case FS_FINISH_FIRST:
+      strip_launch<T>(g, m, d, tens,
+                      OpFinish<T, true>{B.dv, B.lr, B.invd, B.coef, rcur, pcur, B.zb, rprev,
+                                        pprev, B.sc},
+                      ws, st);
+      break;
+  }
+}
+
 template <class T>
 void elas_diag(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, T *diag,
                cudaStream_t st) {
@@ -827,6 +1054,12 @@ template void elas_diag<double>(const GridD &, const MatD &, const double *, con
                                 double *, cudaStream_t);
 template void elas_diag<float>(const GridD &, const MatD &, const float *, const uint8_t *,
                                float *, cudaStream_t);
+template void elas_mg_stage<double>(int, const GridD &, const MatD &, const double *,
+                                    const uint8_t *, const ElasMgBufs<double> &, const RedWs &,
+                                    cudaStream_t);
+template void elas_mg_stage<float>(int, const GridD &, const MatD &, const float *,
+                                   const uint8_t *, const ElasMgBufs<float> &, const RedWs &,
+                                   cudaStream_t);
 template void damage_apply<double>(const GridD &, const double *, double, const double *,
                                    double *, cudaStream_t, KrylovScal *, const RedWs *, int);
 template void damage_apply<float>(const GridD &, const float *, double, const float *, float *,

@@ -41,6 +41,14 @@ struct MgState {
   }
 };
 
+// One Krylov solve as a single CUDA graph: the initialisation, then a conditional WHILE
+// node whose body is one iteration and the condition kernel.
+struct WhileGraph {
+  cudaGraphExec_t exec = nullptr;
+  int init_launches = 0, body_launches = 0;
+  bool unsupported = false;   // building failed once: use the batched host loop
+};
+
 struct GraphSlot {
   cudaGraphExec_t exec = nullptr;
   int launches = 0;
@@ -81,7 +89,8 @@ struct pf_ctx {
   RedWs ws{};
   Gmg<double> gu, gd;        // multigrid hierarchies (FP64 mode)
   Gmg<float> gu32, gd32;     // multigrid hierarchies (FP32 inner solves)
-  GraphSlot graphs[4];
+  GraphSlot graphs[5];        // batched fallback, [slot * 2 + multigrid] and [SL_FUSED]
+  WhileGraph wgraphs[5];      // device-side loops, same indexing
   bool use_graphs = true;
   MgState mg_u, mg_d;
   double prof[PF_PROF_PHASES] = {0};   // host milliseconds per phase (pf_profile)
@@ -150,67 +159,29 @@ GridD grid_nomask(const pf_ctx *ctx) {
 // precision).  Every pointer an iteration touches is a fixed context buffer, so a graph
 // captured once stays valid; operator data (d, tension bits, coefficients, multigrid
 // stencils) are rewritten in place between solves.
-enum { SL_U = 0, SL_D = 1, SL_COUNT = 2 };
+enum { SL_U = 0, SL_D = 1, SL_COUNT = 2, SL_FUSED = 4 };
 
-// Preconditioned CG on a masked SPD operator.  apply(p, q, epi): q = A p with the fused
-// dot epilogue; fine(x, y): y = A x without epilogue (multigrid smoothing).  G == nullptr
-// selects Jacobi with inverse diagonal `inv`.
-template <class T, class Apply, class Fine>
-pf_status pcg(pf_ctx *ctx, int slot, Apply apply, Fine fine, Gmg<T> *G, size_t n, T *b, T *x,
-              T *r, T *z, T *p, T *q, const T *inv, double rtol, int maxit, int *iters,
-              bool *ok) {
+// Runs batch() (`every` Krylov iterations) until ||r||^2 <= rtol^2 rr0, a breakdown, or
+// maxit.  Each batch ends with the read-back of ||r||^2 and the breakdown flag; with graphs
+// enabled the batch is captured once per slot and replayed, so the host launches once and
+// synchronises once per check.
+template <class Batch>
+pf_status krylov_batches(pf_ctx *ctx, int sidx, int every, Batch batch, double rr0, double rtol,
+                         int maxit, int *iters, bool *ok) {
   cudaStream_t st = ctx->st;
-  *iters = 0;
-  if (G) {
-    pcg_init<T>(n, b, x, r, ctx->sc, ctx->ws, st);
-  } else {
-    cg_init<T>(n, b, x, r, z, p, inv, ctx->sc, ctx->ws, st);
-  }
-  ctx->launches++;
-  CKS(check_launch(ctx));
-  CKS(read_scalars(ctx, &ctx->sc->rr, sizeof(double)));
-  const double rr0 = ctx->hbuf[0];
-  *ok = true;
-  if (!(rr0 > 0.0)) return PF_OK;
-  if (G) {
-    ctx->launches += gmg_vcycle<T>(*G, fine, r, z, st);
-    pcg_rz<T>(n, r, z, p, 1, ctx->sc, ctx->ws, st);
-    ctx->launches++;
-  }
-  auto body = [&]() -> int {
-    int nl = 1;
-    apply(p, q, EPI_CG_ALPHA);
-    if (G) {
-      pcg_update<T>(n, x, r, p, q, ctx->sc, ctx->ws, st);
-      nl += 1 + gmg_vcycle<T>(*G, fine, r, z, st);
-      pcg_rz<T>(n, r, z, p, 0, ctx->sc, ctx->ws, st);
-      cg_dir<T>(n, z, p, ctx->sc, st);
-      nl += 2;
-    } else {
-      cg_update<T>(n, x, r, z, p, q, inv, ctx->sc, ctx->ws, st);
-      cg_dir<T>(n, z, p, ctx->sc, st);
-      nl += 2;
-    }
-    return nl;
-  };
-  // One graph holds `every` iterations followed by the read-back of ||r||^2 and the
-  // breakdown flag, so the host launches once and synchronises once per check.
-  const int every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 8;
-  auto batch = [&]() -> int {
-    int nl = 0;
-    for (int k = 0; k < every; ++k) nl += body();
+  auto run = [&]() -> int {
+    const int nl = batch();
     cudaMemcpyAsync(ctx->hbuf, &ctx->sc->rr, sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(ctx->hbuf + 1, &ctx->sc->breakdown, sizeof(int), cudaMemcpyDeviceToHost, st);
     return nl;
   };
-  const int sidx = slot * 2 + (G ? 1 : 0);
   GraphSlot &S = ctx->graphs[sidx];
   if (ctx->use_graphs && (!S.exec || S.every != every)) {
     if (S.exec) cudaGraphExecDestroy(S.exec);
     S.exec = nullptr;
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    S.launches = batch();
+    S.launches = run();
     cudaError_t e = cudaStreamEndCapture(st, &graph);
     if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
     e = cudaGraphInstantiate(&S.exec, graph, 0);
@@ -219,7 +190,6 @@ pf_status pcg(pf_ctx *ctx, int slot, Apply apply, Fine fine, Gmg<T> *G, size_t n
       S.exec = nullptr;
       return set_err(ctx, PF_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
     }
-    S.n = n;
     S.every = every;
   }
   const double target = rtol * rtol * rr0;
@@ -229,7 +199,7 @@ pf_status pcg(pf_ctx *ctx, int slot, Apply apply, Fine fine, Gmg<T> *G, size_t n
     if (S.exec) {
       CK(cudaGraphLaunch(S.exec, st));
     } else {
-      S.launches = batch();
+      S.launches = run();
     }
     ctx->launches += S.launches;
     it += every;
@@ -248,13 +218,195 @@ pf_status pcg(pf_ctx *ctx, int slot, Apply apply, Fine fine, Gmg<T> *G, size_t n
   return PF_OK;
 }
 
+// Pinned host mirror of the Krylov scalars (inside the context's pinned buffer).
+inline KrylovScal *host_scal(pf_ctx *ctx) { return (KrylovScal *)((char *)ctx->hbuf + 128); }
+
+template <class Init, class Body>
+cudaError_t build_while(pf_ctx *ctx, WhileGraph &W, Init init, Body body) {
+  cudaStream_t st = ctx->st;
+  cudaGraph_t gi = nullptr, g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  W.init_launches = init();
+  if ((e = cudaStreamEndCapture(st, &gi)) != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  cudaGraphNode_t ni, nc;
+  cudaGraphNodeParams cp = {};
+  if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) goto done;
+  if ((e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+    goto done;
+  if ((e = cudaGraphAddChildGraphNode(&ni, g, nullptr, 0, gi)) != cudaSuccess) goto done;
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if ((e = cudaGraphAddNode(&nc, g, &ni, nullptr, 1, &cp)) != cudaSuccess) goto done;
+  {
+    cudaGraph_t bg = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(st, bg, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) goto done;
+    W.body_launches = body() + 1;
+    krylov_while(h, ctx->sc, st);
+    if ((e = cudaStreamEndCapture(st, &bg)) != cudaSuccess) goto done;
+  }
+  e = cudaGraphInstantiate(&W.exec, g, 0);
+  if (e != cudaSuccess) W.exec = nullptr;
+done:
+  if (gi) cudaGraphDestroy(gi);
+  if (g) cudaGraphDestroy(g);
+  return e;
+}
+
+// One Krylov solve: init() (returns its launches) sets x = 0 and the device scalars
+// (rr0, it = 0), body() runs one iteration (returns its launches).  Preferred form: one
+// graph launch per solve in which the iterations loop on the device (build_while) and
+// the host synchronises once, with no rounding of the iteration count.  Fallback: init
+// launched directly, then batches of `every` iterations with a host check after each.
+template <class Init, class Body>
+pf_status krylov_run(pf_ctx *ctx, int sidx, Init init, Body body, int every, double rtol,
+                     int maxit, int *iters, bool *ok) {
+  cudaStream_t st = ctx->st;
+  WhileGraph &W = ctx->wgraphs[sidx];
+  if (!W.exec && !W.unsupported) {
+    if (build_while(ctx, W, init, body) != cudaSuccess || !W.exec) {
+      W.unsupported = true;
+      cudaGetLastError();
+    }
+  }
+  *iters = 0;
+  if (W.exec) {
+    KrylovScal *hk = host_scal(ctx);
+    hk->rtol2 = rtol * rtol;
+    hk->maxit = maxit;
+    CK(cudaMemcpyAsync(&ctx->sc->rtol2, &hk->rtol2, sizeof(double) + sizeof(int),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaGraphLaunch(W.exec, st));
+    CK(cudaMemcpyAsync(hk, ctx->sc, sizeof(KrylovScal), cudaMemcpyDeviceToHost, st));
+    CKS(check_launch(ctx));
+    CK(cudaStreamSynchronize(st));
+    ctx->launches += W.init_launches + (long long)hk->it * W.body_launches;
+    if (!(hk->rr0 > 0.0)) {
+      *ok = true;
+      return PF_OK;
+    }
+    *iters = hk->it;
+    *ok = hk->rr <= hk->rtol2 * hk->rr0;
+    return PF_OK;
+  }
+  ctx->launches += init();
+  CKS(check_launch(ctx));
+  CKS(read_scalars(ctx, &ctx->sc->rr, sizeof(double)));
+  const double rr0 = ctx->hbuf[0];
+  *ok = true;
+  if (!(rr0 > 0.0)) return PF_OK;
+  auto batch = [&]() -> int {
+    int nl = 0;
+    for (int k = 0; k < every; ++k) nl += body();
+    return nl;
+  };
+  return krylov_batches(ctx, sidx, every, batch, rr0, rtol, maxit, iters, ok);
+}
+
+// Preconditioned CG on a masked SPD operator.  apply(p, q, epi): q = A p with the fused
+// dot epilogue; fine(x, y): y = A x without epilogue (multigrid smoothing).  G == nullptr
+// selects Jacobi with inverse diagonal `inv`.
+template <class T, class Apply, class Fine>
+pf_status pcg(pf_ctx *ctx, int slot, Apply apply, Fine fine, Gmg<T> *G, size_t n, T *b, T *x,
+              T *r, T *z, T *p, T *q, const T *inv, double rtol, int maxit, int *iters,
+              bool *ok) {
+  cudaStream_t st = ctx->st;
+  auto init = [&]() -> int {
+    if (!G) {
+      cg_init<T>(n, b, x, r, z, p, inv, ctx->sc, ctx->ws, st);
+      return 1;
+    }
+    pcg_init<T>(n, b, x, r, ctx->sc, ctx->ws, st);
+    const int nl = gmg_vcycle<T>(*G, fine, r, z, st);
+    pcg_rz<T>(n, r, z, p, 1, ctx->sc, ctx->ws, st);
+    return nl + 2;
+  };
+  auto body = [&]() -> int {
+    int nl = 1;
+    apply(p, q, EPI_CG_ALPHA);
+    if (G) {
+      pcg_update<T>(n, x, r, p, q, ctx->sc, ctx->ws, st);
+      nl += 1 + gmg_vcycle<T>(*G, fine, r, z, st);
+      pcg_rz<T>(n, r, z, p, 0, ctx->sc, ctx->ws, st);
+      cg_dir<T>(n, z, p, ctx->sc, st);
+      nl += 2;
+    } else {
+      cg_update<T>(n, x, r, z, p, q, inv, ctx->sc, ctx->ws, st);
+      cg_dir<T>(n, z, p, ctx->sc, st);
+      nl += 2;
+    }
+    return nl;
+  };
+  const int every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 8;
+  return krylov_run(ctx, slot * 2 + (G ? 1 : 0), init, body, every, rtol, maxit, iters, ok);
+}
+
+// Multigrid PCG on the elasticity tangent with the fine-level work fused into the strip
+// apply (elas_mg_stage): the iteration of pcg() with the V-cycle preconditioner, in five
+// fine-level launches per iteration instead of sixteen.  Needs a hierarchy with at least
+// one grid level above the single-CTA coarse cycle (G.lc >= 1).  Level-0 vectors of the
+// hierarchy serve as the second residual and direction buffers and as smoother scratch.
+template <class T>
+pf_status pcg_mg_elas(pf_ctx *ctx, Gmg<T> &G, const T *d, size_t n, const T *b, T *x, T *r,
+                      T *z, T *p, T *q, double rtol, int maxit, int *iters, bool *ok) {
+  cudaStream_t st = ctx->st;
+  GmgLevel<T> &L0 = G.lv[0];
+  ElasMgBufs<T> B;
+  B.b = b;
+  B.x = x;
+  B.r[0] = r;
+  B.r[1] = L0.b;
+  B.p[0] = p;
+  B.p[1] = L0.y;
+  B.q = q;
+  B.za = L0.x;
+  B.zb = z;
+  B.lr = L0.r;
+  B.dv = L0.dv;
+  B.invd = L0.invd;
+  B.coef = L0.coef;
+  B.fm = L0.fm;
+  B.xc = G.lv[1].x;
+  B.nxc = G.lv[1].nx;
+  B.nyc = G.lv[1].ny;
+  B.sc = ctx->sc;
+  (void)n;
+  auto stage = [&](int s) { elas_mg_stage<T>(s, ctx->g, ctx->m, d, ctx->tens, B, ctx->ws, st); };
+  // residual, restriction, coarse levels and post-smoothing of the V-cycle on r[1]
+  auto vcycle_rest = [&](bool first) -> int {
+    stage(FS_RESID);
+    gmg_restrict<T>(G, 0, L0.r, G.lv[1].b, st);
+    const int nl = 2 + gmg_mid<T>(G, 1, st);
+    stage(FS_PROLONG);
+    stage(first ? FS_FINISH_FIRST : FS_FINISH);
+    return nl + 2;
+  };
+  // x = 0, r = b, z = V(r), rz, beta = 0, p_prev = 0
+  auto init = [&]() -> int {
+    stage(FS_UPD_INIT);
+    return 1 + vcycle_rest(true);
+  };
+  auto body = [&]() -> int {
+    stage(FS_DIR);
+    stage(FS_UPD);
+    return 2 + vcycle_rest(false);
+  };
+  const int every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 8;
+  return krylov_run(ctx, SL_FUSED, init, body, every, rtol, maxit, iters, ok);
+}
+
 // FP32 inner solves inside FP64 iterative refinement:  x = 0; repeat {s = 2^-floor(log2
 // ||r||); solve A_32 e = (s r)_32 to tol_inner; x += e / s; r = b - A_64 x; stop when
-// ||r|| <= tol_lin ||b||}.
+// ||r|| <= tol ||b||}.
 // inner(iters, ok) solves with rhs ctx->fb into ctx->fx.
 template <class ApplyD, class Inner>
 pf_status refine(pf_ctx *ctx, ApplyD applyd, Inner inner, size_t n, int ncomp, const double *b,
-                 double *x, int *iters, int *refines, bool *ok) {
+                 double *x, double tol, int *iters, int *refines, bool *ok) {
   cudaStream_t st = ctx->st;
   CK(cudaMemsetAsync(x, 0, n * sizeof(double), st));
   CK(cudaMemcpyAsync(ctx->kres, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -287,7 +439,7 @@ pf_status refine(pf_ctx *ctx, ApplyD applyd, Inner inner, size_t n, int ncomp, c
     CKS(check_launch(ctx));
     CKS(read_scalars(ctx, ctx->dscal, sizeof(double)));
     rn = sqrt(ctx->hbuf[0]);
-    if (rn <= ctx->opt.tol_lin * bn) {
+    if (rn <= tol * bn) {
       *ok = true;
       break;
     }
@@ -336,7 +488,7 @@ pf_status mg_solve(pf_ctx *ctx, MgState &S, bool mg, Setup setup0, Solve solve, 
 
 // ---- u-solve ---------------------------------------------------------------------------
 // One Newton correction: K_t(d, tension) kx = kb on free DOFs.
-pf_status newton_correction(pf_ctx *ctx, int *lin, int *refines, bool *ok) {
+pf_status newton_correction(pf_ctx *ctx, double tol, int *lin, int *refines, bool *ok) {
   PhaseTimer tm(&ctx->prof[PF_PROF_U_SOLVE]);
   cudaStream_t st = ctx->st;
   const size_t n = 2 * ctx->nn;
@@ -359,8 +511,11 @@ pf_status newton_correction(pf_ctx *ctx, int *lin, int *refines, bool *ok) {
       return PF_OK;
     };
     auto solve = [&](int maxit, int *it, bool *sok) {
+      if (mg && ctx->gu.lc >= 1)
+        return pcg_mg_elas<double>(ctx, ctx->gu, ctx->d, n, ctx->kb, ctx->kx, ctx->kr, ctx->kz,
+                                   ctx->kp, ctx->kq, tol, maxit, it, sok);
       return pcg<double>(ctx, SL_U, A, Af, mg ? &ctx->gu : nullptr, n, ctx->kb, ctx->kx, ctx->kr,
-                         ctx->kz, ctx->kp, ctx->kq, ctx->kinv, ctx->opt.tol_lin, maxit, it, sok);
+                         ctx->kz, ctx->kp, ctx->kq, ctx->kinv, tol, maxit, it, sok);
     };
     return mg_solve(ctx, ctx->mg_u, mg, setup, solve, lin, ok);
   }
@@ -381,6 +536,9 @@ pf_status newton_correction(pf_ctx *ctx, int *lin, int *refines, bool *ok) {
     return PF_OK;
   };
   auto solve = [&](int maxit, int *it, bool *iok) {
+    if (mg && ctx->gu32.lc >= 1)
+      return pcg_mg_elas<float>(ctx, ctx->gu32, ctx->fd, n, ctx->fb, ctx->fx, ctx->fr, ctx->fz,
+                                ctx->fp, ctx->fq, ctx->opt.tol_inner, maxit, it, iok);
     return pcg<float>(ctx, SL_U, Af32, Ff32, mg ? &ctx->gu32 : nullptr, n, ctx->fb, ctx->fx,
                       ctx->fr, ctx->fz, ctx->fp, ctx->fq, ctx->finv, ctx->opt.tol_inner, maxit,
                       it, iok);
@@ -394,7 +552,7 @@ pf_status newton_correction(pf_ctx *ctx, int *lin, int *refines, bool *ok) {
   auto AD = [ctx, st](const double *xx, double *yy) {
     elas_apply<double>(ctx->g, ctx->m, ctx->d, ctx->tens, xx, yy, st);
   };
-  return refine(ctx, AD, inner, n, 2, ctx->kb, ctx->kx, lin, refines, ok);
+  return refine(ctx, AD, inner, n, 2, ctx->kb, ctx->kx, tol, lin, refines, ok);
 }
 
 pf_status solve_u(pf_ctx *ctx, int *newton, int *lin, int *refines, bool *ok) {
@@ -426,8 +584,15 @@ pf_status solve_u(pf_ctx *ctx, int *newton, int *lin, int *refines, bool *ok) {
     // rhs = -F on free DOFs
     masked_comb(n, 2, ctx->g.dofm, -1.0, ctx->F, 0.0, nullptr, ctx->kb, st);
     ctx->launches++;
+    // inexact Newton: the correction's linear residual need only stay below the Newton
+    // tolerance (forcing term newton_forcing * tol_nr * ref / ||R_k||, within [tol_lin, 1e-2])
+    double tol = ctx->opt.tol_lin;
+    if (ctx->opt.newton_forcing > 0.0) {
+      const double f = ctx->opt.newton_forcing * ctx->opt.tol_nr * fmax(r0, fref) / rn;
+      tol = fmax(tol, fmin(f, 1e-2));
+    }
     bool lok = false;
-    CKS(newton_correction(ctx, lin, refines, &lok));
+    CKS(newton_correction(ctx, tol, lin, refines, &lok));
     add(n, ctx->kx, ctx->u, st);
     ctx->launches++;
     (*newton)++;
@@ -506,7 +671,7 @@ pf_status solve_damage(pf_ctx *ctx, const double *c, const double *rhs, double *
   auto AD = [ctx, st, kappa](const double *xx, double *yy) {
     damage_apply<double>(ctx->g, ctx->csolve, kappa, xx, yy, st);
   };
-  return refine(ctx, AD, inner, n, 1, rhs, x, lin, refines, ok);
+  return refine(ctx, AD, inner, n, 1, rhs, x, ctx->opt.tol_lin, lin, refines, ok);
 }
 
 // rhs = free ? b(H) - K(c) d : 0 ; then d += K_ff^-1 rhs.
@@ -602,6 +767,8 @@ void free_all(pf_ctx *c) {
   gmg_free<float>(c->gd32);
   for (GraphSlot &g : c->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (WhileGraph &w : c->wgraphs)
+    if (w.exec) cudaGraphExecDestroy(w.exec);
   if (c->hbuf) cudaFreeHost(c->hbuf);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -627,6 +794,7 @@ void pf_default_options(pf_options *o) {
   o->psi_crit = -1.0;
   o->project = 0;
   o->check_every = 8;
+  o->newton_forcing = 1e-3;
 }
 
 const char *pf_status_string(pf_status s) {
@@ -732,7 +900,7 @@ pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double 
     }
     if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(PF_ENOMEM);
   }
-  if (cudaMallocHost((void **)&ctx->hbuf, 64) != cudaSuccess) return fail(PF_ENOMEM);
+  if (cudaMallocHost((void **)&ctx->hbuf, 256) != cudaSuccess) return fail(PF_ENOMEM);
   if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess)
     return fail(PF_ECUDA);
   cudaStream_t st = ctx->st;
@@ -804,7 +972,8 @@ size_t pf_footprint_bytes(const pf_mesh *mesh) {
 pf_status pf_set_options(pf_ctx *ctx, const pf_options *o) {
   if (!ctx || !o) return PF_EINVAL;
   if (!(o->tol_nr > 0) || !(o->tol_lin > 0) || !(o->tol_inner > 0) || o->max_newton < 1 ||
-      o->max_stag < 1 || o->max_lin < 1 || o->max_refine < 1 || o->check_every < 1)
+      o->max_stag < 1 || o->max_lin < 1 || o->max_refine < 1 || o->check_every < 1 ||
+      !(o->newton_forcing >= 0))
     return set_err(ctx, PF_EINVAL, "invalid options");
   ctx->opt = *o;
   return PF_OK;

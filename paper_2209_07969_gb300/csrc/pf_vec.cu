@@ -8,63 +8,11 @@
 
 namespace pf {
 
-__device__ __forceinline__ double vwarp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double vwarp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
 
 template <int NV>
-__device__ bool vgrid_reduce(double (&v)[NV], const RedWs ws, double (&tot)[NV], bool is_max) {
-  __shared__ double sh[NV][32];
-  __shared__ bool am_last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-  const unsigned nblk = gridDim.x;
-  const unsigned bid = blockIdx.x;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double s = is_max ? vwarp_max(v[k]) : vwarp_sum(v[k]);
-    if (lane == 0) sh[k][warp] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double s = sh[k][0];
-      for (int w = 1; w < nw; ++w) s = is_max ? fmax(s, sh[k][w]) : s + sh[k][w];
-      ws.partials[k * ws.max_blocks + bid] = s;
-    }
-    am_last = red_arrive(ws.counter, bid, nblk);
-  }
-  __syncthreads();
-  if (!am_last) return false;
-  __threadfence();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double s = is_max ? -INFINITY : 0.0;
-    for (unsigned i = threadIdx.x; i < nblk; i += blockDim.x) {
-      double p = __ldcg(ws.partials + k * ws.max_blocks + i);
-      s = is_max ? fmax(s, p) : s + p;
-    }
-    s = is_max ? vwarp_max(s) : vwarp_sum(s);
-    __syncthreads();
-    if (lane == 0) sh[k][warp] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return false;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double s = sh[k][0];
-    for (int w = 1; w < nw; ++w) s = is_max ? fmax(s, sh[k][w]) : s + sh[k][w];
-    tot[k] = s;
-  }
-  return true;
+__device__ __forceinline__ bool vgrid_reduce(double (&v)[NV], const RedWs ws, double (&tot)[NV],
+                                             bool is_max) {
+  return red_grid<NV>(v, ws, tot, is_max);
 }
 
 // DOF constrained?  ncomp = 2 (u: bit = component) or 1 (d: bit 2).
@@ -98,6 +46,8 @@ __global__ void k_cg_init(size_t n, const T *__restrict__ b, T *__restrict__ x,
   if (vgrid_reduce<2>(v, ws, tot, false)) {
     sc->rz = tot[0];
     sc->rr = tot[1];
+    sc->rr0 = tot[1];
+    sc->it = 0;
     sc->breakdown = 0;
     sc->alpha = 0.0;
     sc->beta = 0.0;
@@ -156,6 +106,8 @@ __global__ void k_pcg_init(size_t n, const T *__restrict__ b, T *__restrict__ x,
   double v[1] = {(double)rr}, tot[1];
   if (vgrid_reduce<1>(v, ws, tot, false)) {
     sc->rr = tot[0];
+    sc->rr0 = tot[0];
+    sc->it = 0;
     sc->rz = 0.0;
     sc->breakdown = 0;
     sc->alpha = 0.0;
@@ -200,6 +152,16 @@ __global__ void k_pcg_rz(size_t n, const T *__restrict__ r, const T *__restrict_
     sc->rz = tot[0];
     if (!(tot[0] > 0.0)) sc->breakdown = 1;
   }
+}
+
+// End of one pass of a device-side Krylov loop (a conditional WHILE node of a CUDA graph):
+// count the iteration and keep looping while ||r||^2 > rtol2 ||r0||^2, without breakdown,
+// for fewer than maxit iterations.  A NaN residual ends the loop (the comparison fails).
+__global__ void k_krylov_while(cudaGraphConditionalHandle h, KrylovScal *sc) {
+  const int it = sc->it + 1;
+  sc->it = it;
+  const bool more = sc->rr > sc->rtol2 * sc->rr0 && !sc->breakdown && it < sc->maxit;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // ---- helpers ---------------------------------------------------------------------------
@@ -382,6 +344,9 @@ void pcg_rz(size_t n, const T *r, const T *z, T *p, int first, KrylovScal *sc, c
 template <class T>
 void invert(size_t n, const T *diag, T *inv, cudaStream_t st) {
   k_invert<T><<<vblocks(n, 1 << 16), VEC_THREADS, 0, st>>>(n, diag, inv);
+}
+void krylov_while(cudaGraphConditionalHandle h, KrylovScal *sc, cudaStream_t st) {
+  k_krylov_while<<<1, 1, 0, st>>>(h, sc);
 }
 void masked_comb(size_t n, int ncomp, const uint8_t *dofm, double s, const double *a, double t,
                  const double *b, double *out, cudaStream_t st) {

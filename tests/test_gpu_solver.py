@@ -28,13 +28,13 @@ def _checker(spec):
 
 
 def _run_both(spec, scheme, tol, precision=binding.FP64, steps=None, tol_lin=1e-12,
-              precond=binding.PRECOND_JACOBI):
+              precond=binding.PRECOND_JACOBI, **options):
     g, m = _checker(spec)
     incs = spec.increments if steps is None else spec.increments[:steps]
     st = stg.State(g)
     opts = stg.Options(tol_st=tol)
     sim = binding.Simulation(spec, precision=precision, precond=precond)
-    sim.set_options(tol_lin=tol_lin)
+    sim.set_options(tol_lin=tol_lin, **options)
     out = []
     for du in incs:
         r_ref = stg.load_step(g, m, st, du, scheme, opts, spec.reaction_dir)
@@ -133,6 +133,18 @@ def test_tensile_path_fp64_matches_checker(gpu, scheme, precond):
         assert abs(r["stag_iters"] - r_ref.stag_iters) <= max(1, 0.2 * r_ref.stag_iters)
         cracked |= r_ref.reaction < 0.7 * peak or r_ref.stag_iters > 20
     assert cracked, "the small path must reach the crack"
+
+
+def test_exact_newton_corrections_match_checker(gpu):
+    # newton_forcing = 0: every u correction solved to tol_lin (the default solves it only
+    # to well below the Newton tolerance); same converged path
+    spec = S.tensile(SMALL["n"], l=SMALL["l"], steps=SMALL["steps"], u_max=SMALL["u_max"])
+    g, m, out = _run_both(spec, 1, tol=1e-8, precond=binding.PRECOND_GMG, newton_forcing=0.0)
+    peak = max(abs(o[0].reaction) for o in out)
+    for r_ref, r, st_ref, (u, d, H) in out:
+        assert r["converged"] == 1
+        assert abs(r["reaction"] - r_ref.reaction) <= 1e-6 * peak
+        assert _max_diff(g, d, H, st_ref)[0] < 1e-6
 
 
 @pytest.mark.parametrize("precond", PRECONDS)
