@@ -52,6 +52,9 @@ def parse():
                    help="time one operator kernel on the --grid tensile mesh and exit")
     p.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     p.add_argument("--reps", type=int, default=20)
+    p.add_argument("--host-loop", action="store_true",
+                   help="host-checked Krylov batches instead of device-side loops (same "
+                        "kernels; for profilers that cannot see inside conditional graph nodes)")
     return p.parse_args()
 
 
@@ -250,7 +253,7 @@ def run_ours(args):
     sims = [binding.Simulation(spec, precision=binding.FP32_IR, precond=binding.PRECOND_GMG)
             for _ in range(B)]
     for s in sims:
-        s.set_options(max_stag=1000)
+        s.set_options(max_stag=1000, device_loop=0 if args.host_loop else 1)
     incs = spec.increments
     step_idx = [0] * B
     results = [[] for _ in range(B)]

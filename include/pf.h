@@ -94,14 +94,17 @@ typedef struct {
   int max_refine;    /* [30] FP64 refinement sweeps per linear solve (PF_FP32_IR) */
   double psi_crit;   /* [-1] < 0: G_c/(c_w l) of Sec. 3.5; else the given threshold */
   int project;       /* [0] 1: clamp d into [d_{n-1}, 1] after every d-solve */
-  int check_every;   /* [8] Krylov iterations between host convergence reads; used only
-                        where the device-side Krylov loop (CUDA graph conditional node) is
-                        unavailable */
+  int check_every;   /* [8] Krylov iterations between host convergence reads when
+                        device_loop is 0 or the device-side loop is unavailable */
   double newton_forcing; /* [1e-3] inexact Newton for u: the correction at residual R_k is
                         solved to the relative residual max(tol_lin, min(1e-2,
                         newton_forcing * tol_nr * max(||R0||, ||F_constr||) / ||R_k||)), so
                         that the linear residual stays below the Newton tolerance; 0 solves
                         every correction to tol_lin */
+  int device_loop;   /* [1] 1: each Krylov solve is one CUDA graph whose iterations loop on
+                        the device (conditional WHILE node, one host synchronisation per
+                        solve); 0: host-checked batches of check_every iterations (same
+                        kernels; for profilers that cannot see inside conditional nodes) */
 } pf_options;
 
 typedef struct {

@@ -39,7 +39,8 @@ class Options(C.Structure):
     _fields_ = [("tol_nr", C.c_double), ("tol_lin", C.c_double), ("tol_inner", C.c_double),
                 ("max_newton", C.c_int), ("max_stag", C.c_int), ("max_lin", C.c_int),
                 ("max_refine", C.c_int), ("psi_crit", C.c_double), ("project", C.c_int),
-                ("check_every", C.c_int), ("newton_forcing", C.c_double)]
+                ("check_every", C.c_int), ("newton_forcing", C.c_double),
+                ("device_loop", C.c_int)]
 
 
 class StepResult(C.Structure):

@@ -207,7 +207,7 @@ namespace {
 constexpr int NOALLOC_BLOCKS = 1024;  // reduction partial slots (>= 2 CTAs per SM)
 constexpr size_t NOALLOC_FIELD_DOUBLES = PF_NOALLOC_MAX_DOUBLES;
 constexpr size_t NOALLOC_DOUBLES = 4 * NOALLOC_BLOCKS + 2 + NOALLOC_FIELD_DOUBLES;
-constexpr size_t NOALLOC_COUNTERS = 2 + NOALLOC_BLOCKS / RED_GROUP;
+constexpr size_t NOALLOC_COUNTERS = 2;
 
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
 static __device__ __align__(256) unsigned g_noalloc_counters[NOALLOC_COUNTERS];

@@ -44,16 +44,14 @@ struct KrylovScal {
   int pad;
 };
 
-// Reduction workspace: per-CTA partials (up to 4 values each) and arrival counters
-// (counter[0] for groups, counter[1 + g] for the CTAs of group g), all kept at zero
-// between launches.
+// Reduction workspace: per-CTA partials (up to 4 values each) and the arrival counter,
+// kept at zero between launches.
 struct RedWs {
   double *partials;   // 4 * max_blocks doubles
-  unsigned *counter;  // red_counters(max_blocks) counters
+  unsigned *counter;  // red_counters() arrival counters
   int max_blocks;
 };
-constexpr int RED_GROUP = 64;
-inline size_t red_counters(int max_blocks) { return 2 + (size_t)max_blocks / RED_GROUP; }
+inline size_t red_counters(int) { return 2; }
 
 #ifdef __CUDACC__
 __device__ __forceinline__ double red_warp(double v, bool is_max) {
@@ -88,19 +86,16 @@ __device__ __forceinline__ void red_cta(double (&v)[NV], double (*sh)[32], bool 
 }
 
 // Grid-wide sum (or max) of NV values, deterministic and without a second launch.  Every
-// CTA publishes its partials and arrives on the counter of its group of RED_GROUP CTAs; the
-// last CTA of a group sums the group's partials (one load per thread) into the group's
-// first slot and arrives on the top counter; the last group's CTA sums the group totals.
-// Each step reads its inputs in one round of loads.  Returns true in thread 0 of that
-// final CTA, with tot[] holding the totals; counters are reset for the next launch.
-// Every CTA of the grid must call it.
+// CTA publishes its partials and arrives on one counter; the last CTA to arrive reads all
+// partials with RED_UNROLL independent loads in flight per thread and sums them in a fixed
+// order.  Returns true in thread 0 of that CTA, with tot[] holding the totals; the counter
+// is reset for the next launch.  Every CTA of the grid must call it.
+constexpr int RED_UNROLL = 8;
 template <int NV>
 __device__ bool red_grid(double (&v)[NV], const RedWs ws, double (&tot)[NV], bool is_max) {
   __shared__ double sh[NV][32];
   __shared__ int go;
   const unsigned nblk = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
-  const unsigned g = bid / RED_GROUP, ng = (nblk + RED_GROUP - 1) / RED_GROUP;
-  const unsigned g0 = g * RED_GROUP, gsize = nblk - g0 < RED_GROUP ? nblk - g0 : RED_GROUP;
   const double none = is_max ? -INFINITY : 0.0;
   const size_t mb = (size_t)ws.max_blocks;
   red_cta<NV>(v, sh, is_max);
@@ -108,7 +103,7 @@ __device__ bool red_grid(double (&v)[NV], const RedWs ws, double (&tot)[NV], boo
 #pragma unroll
     for (int k = 0; k < NV; ++k) ws.partials[k * mb + bid] = v[k];
     __threadfence();
-    go = atomicAdd(ws.counter + 1 + g, 1u) == gsize - 1;
+    go = atomicAdd(ws.counter, 1u) == nblk - 1;
   }
   __syncthreads();
   if (!go) return false;
@@ -116,30 +111,22 @@ __device__ bool red_grid(double (&v)[NV], const RedWs ws, double (&tot)[NV], boo
   double w[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    w[k] = none;
-    for (unsigned i = threadIdx.x; i < gsize; i += blockDim.x) {
-      const double p = __ldcg(ws.partials + k * mb + g0 + i);
-      w[k] = is_max ? fmax(w[k], p) : w[k] + p;
-    }
-  }
-  red_cta<NV>(w, sh, is_max);
-  if (threadIdx.x == 0) {
-    ws.counter[1 + g] = 0u;
+    double a[RED_UNROLL];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) ws.partials[k * mb + g0] = w[k];
-    __threadfence();
-    go = atomicAdd(ws.counter, 1u) == ng - 1;
-  }
-  __syncthreads();
-  if (!go) return false;
-  __threadfence();
+    for (int u = 0; u < RED_UNROLL; ++u) a[u] = none;
+    for (unsigned base = threadIdx.x; base < nblk; base += RED_UNROLL * blockDim.x) {
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    w[k] = none;
-    for (unsigned i = threadIdx.x; i < ng; i += blockDim.x) {
-      const double p = __ldcg(ws.partials + k * mb + (size_t)i * RED_GROUP);
-      w[k] = is_max ? fmax(w[k], p) : w[k] + p;
+      for (int u = 0; u < RED_UNROLL; ++u) {
+        const unsigned i = base + u * blockDim.x;
+        if (i < nblk) {
+          const double p = __ldcg(ws.partials + k * mb + i);
+          a[u] = is_max ? fmax(a[u], p) : a[u] + p;
+        }
+      }
     }
+    w[k] = a[0];
+#pragma unroll
+    for (int u = 1; u < RED_UNROLL; ++u) w[k] = is_max ? fmax(w[k], a[u]) : w[k] + a[u];
   }
   red_cta<NV>(w, sh, is_max);
   if (threadIdx.x != 0) return false;
@@ -187,11 +174,11 @@ void dof_mask(int nx, int ny, const uint8_t *flags, const uint8_t *active, uint8
 // Epilogues of the fused operator + reduction kernels.
 enum { EPI_NONE = 0, EPI_CG_ALPHA = 1 };
 
-// Buffers of the multigrid-preconditioned CG on the elasticity tangent whose fine-level
-// work runs fused into the strip apply (elas_mg_stage).  Vectors have 2 (nx+1)(ny+1)
-// entries, interleaved (u_x, u_y) per node.
+// Buffers of the multigrid-preconditioned CG whose fine-level work runs fused into the
+// operator kernel (elas_mg_stage, damage_mg_stage).  Vectors have B (nx+1)(ny+1) entries
+// (B = 2: interleaved (u_x, u_y) per node; B = 1: phase field).
 template <class T>
-struct ElasMgBufs {
+struct MgBufs {
   const T *b;              // right-hand side
   T *x;                    // iterate
   T *r[2], *p[2];          // [0]: previous iterate's residual / direction, [1]: current
@@ -203,9 +190,13 @@ struct ElasMgBufs {
   KrylovScal *sc;
 };
 enum { FS_DIR, FS_UPD, FS_UPD_INIT, FS_RESID, FS_PROLONG, FS_FINISH, FS_FINISH_FIRST };
-// One fused stage (see pf_ops.cu).
+// One fused stage (pf_fused.cuh) on the elasticity tangent (strip kernel) or on K_dd(c)
+// (tile kernel).
 template <class T>
 void elas_mg_stage(int stage, const GridD &g, const MatD &m, const T *d, const uint8_t *tens,
-                   const ElasMgBufs<T> &b, const RedWs &ws, cudaStream_t st);
+                   const MgBufs<T> &b, const RedWs &ws, cudaStream_t st);
+template <class T>
+void damage_mg_stage(int stage, const GridD &g, const T *c, double kappa, const MgBufs<T> &b,
+                     const RedWs &ws, cudaStream_t st);
 
 }  // namespace pf

@@ -15,6 +15,7 @@
 #include <stdio.h>
 
 #include "pf_internal.cuh"
+#include "pf_fused.cuh"
 
 namespace pf {
 
@@ -23,18 +24,6 @@ __device__ __forceinline__ double gp_hi() { return 0.78867513459481288225; }  //
 
 template <class T>
 __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
-
-// Both displacement components of node n (interleaved storage) in one vector load.
-__device__ __forceinline__ void ld_pair(const float *x, size_t n, float &a, float &b) {
-  const float2 v = __ldg(reinterpret_cast<const float2 *>(x) + n);
-  a = v.x;
-  b = v.y;
-}
-__device__ __forceinline__ void ld_pair(const double *x, size_t n, double &a, double &b) {
-  const double2 v = __ldg(reinterpret_cast<const double2 *>(x) + n);
-  a = v.x;
-  b = v.y;
-}
 
 // ------------------------------------------------------------------------------------
 // Reductions: warp shuffle -> CTA -> per-CTA partials -> grouped two-level sum in the last
@@ -49,18 +38,6 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NV], const RedWs ws, dou
   return red_grid<NV>(v, ws, tot, is_max);
 }
 
-// Epilogue for the fused matvec + dot: CG step length.
-__device__ __forceinline__ void krylov_epilogue(int epi, KrylovScal *sc, double dot) {
-  if (epi == EPI_CG_ALPHA) {
-    sc->pq = dot;
-    if (dot > 0.0 && isfinite(dot) && sc->rz > 0.0) {
-      sc->alpha = sc->rz / dot;
-    } else {
-      sc->alpha = 0.0;
-      sc->breakdown = 1;
-    }
-  }
-}
 
 // ------------------------------------------------------------------------------------
 // Per-launch constants in the kernel's arithmetic type, computed on the host: GB300 runs
@@ -277,44 +254,6 @@ k_elas(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restr
 constexpr int SW = 30;          // output node columns per warp
 constexpr int STRIP_WARPS = 4;  // warps per CTA
 
-template <class T>
-__device__ __forceinline__ void st_pair(T *y, size_t n, T a, T b) {
-  if (sizeof(T) == 4) {
-    reinterpret_cast<float2 *>(y)[n] = make_float2((float)a, (float)b);
-  } else {
-    reinterpret_cast<double2 *>(y)[n] = make_double2((double)a, (double)b);
-  }
-}
-// Plain (coherent) load of a pair the same thread rewrites in the same launch.
-template <class T>
-__device__ __forceinline__ void ld_pair_rw(const T *y, size_t n, T &a, T &b) {
-  a = y[2 * n];
-  b = y[2 * n + 1];
-}
-
-// Input / output policies of the strip kernel.  in(n, i, j, a, b) forms both components of
-// the operand at node n = (i, j) (constrained components are zeroed by the kernel);
-// out(n, ox, oy, cx, cy, acc) receives the masked product (ox, oy) = (A x)_n and the
-// operand (cx, cy) at its node; NR values summed over all nodes go to fin() in the last CTA.
-// Every node is output by exactly one lane, so out() may rewrite buffers at its own node;
-// buffers read by in() are never written in the same launch.
-template <class T>
-struct OpApply {  // y = A x (+ x.y for the Krylov epilogue)
-  static constexpr int NR = 1;
-  const T *x;
-  T *y;
-  KrylovScal *sc;
-  int epi;
-  __device__ void begin() {}
-  __device__ void in(size_t n, int, int, T &a, T &b) const { ld_pair(x, n, a, b); }
-  __device__ void out(size_t n, T ox, T oy, T cx, T cy, T (&acc)[1]) const {
-    st_pair(y, n, ox, oy);
-    acc[0] += cx * ox + cy * oy;
-  }
-  __device__ bool reduce() const { return epi != EPI_NONE; }
-  __device__ void fin(const double (&tot)[1]) const { krylov_epilogue(epi, sc, tot[0]); }
-};
-
 // SR node rows per warp: short strips on small grids (more warps to hide latency), long
 // strips on large ones (less halo re-reading).
 template <class T, int SR, class Op>
@@ -340,7 +279,10 @@ k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *_
       vx = vy = vd = T(0);
       if (col_ok && j >= 0 && j <= ny) {
         const size_t n = (size_t)j * ld + i;
-        op.in(n, i, j, vx, vy);
+        T v[2];
+        op.in(n, i, j, v);
+        vx = v[0];
+        vy = v[1];
         vd = ldg(d + n);
         if (g.dofm) {
           const uint8_t mk = ldg(g.dofm + n);
@@ -380,7 +322,8 @@ k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *_
           if (mk & 1) ox = T(0);
           if (mk & 2) oy = T(0);
         }
-        op.out(n, ox, oy, cx, cy, acc);
+        const T o[2] = {ox, oy}, ci[2] = {cx, cy};
+        op.out(n, o, ci, acc);
       }
       carry_x = f[4] + lx3;
       carry_y = f[5] + ly3;
@@ -397,251 +340,35 @@ k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *_
   }
 }
 
-// ---- PCG with the multigrid V-cycle, fine-level work fused into the strip kernel ------------
-// One iteration runs five strip launches (plus the restriction and the coarse levels):
-//   DIR      p = z + beta p_old at the input; q = A p; alpha = rz / p.q
-//   UPD      r = r_old - alpha q, d0 = it D^-1 r at the input; y = A d0;
-//            z_a = d0 + c1 d0 + c2 D^-1 (r - y); x += alpha p; rr = r.r
-//   RESID    r_l = r - A z_a                                   (restricted to level 1)
-//   PROLONG  t = z_a + P x_1 at the input; r_l = r - A t; dv = it D^-1 r_l; z_b = t + dv
-//   FINISH   z_b += c1 dv + c2 D^-1 (r_l - A dv); rz = r.z_b; beta = rz / rz_old
-// Neighbours read r and p of the previous iteration while the current ones are written, so
-// each has two buffers: [0] previous, [1] current; FINISH copies [1] into [0] at its node.
-template <class T>
-struct OpDir {
-  static constexpr int NR = 1;
-  const T *z, *pold;
-  T *pnew, *q;
-  KrylovScal *sc;
-  T beta;
-  __device__ void begin() { beta = (T)sc->beta; }
-  __device__ void in(size_t n, int, int, T &a, T &b) const {
-    T z0, z1, p0, p1;
-    ld_pair(z, n, z0, z1);
-    ld_pair(pold, n, p0, p1);
-    a = z0 + beta * p0;
-    b = z1 + beta * p1;
-  }
-  __device__ void out(size_t n, T ox, T oy, T cx, T cy, T (&acc)[1]) const {
-    st_pair(pnew, n, cx, cy);
-    st_pair(q, n, ox, oy);
-    acc[0] += cx * ox + cy * oy;
-  }
-  __device__ bool reduce() const { return true; }
-  __device__ void fin(const double (&tot)[1]) const { krylov_epilogue(EPI_CG_ALPHA, sc, tot[0]); }
-};
-
-template <class T, bool INIT>
-struct OpUpd {
-  static constexpr int NR = 1;
-  const T *rold, *q, *p, *invd, *coef;
-  T *rnew, *x, *za;
-  KrylovScal *sc;
-  T alpha, it, c2, c1;
-  __device__ void begin() {
-    alpha = INIT ? T(0) : (T)sc->alpha;
-    it = coef[0];
-    c2 = coef[1];
-    c1 = coef[2];
-  }
-  __device__ void rn(size_t n, T &r0, T &r1) const {
-    ld_pair(rold, n, r0, r1);
-    if (!INIT) {
-      T q0, q1;
-      ld_pair(q, n, q0, q1);
-      r0 = r0 - alpha * q0;
-      r1 = r1 - alpha * q1;
-    }
-  }
-  __device__ void in(size_t n, int, int, T &a, T &b) const {
-    T r0, r1, i0, i1;
-    rn(n, r0, r1);
-    ld_pair(invd, n, i0, i1);
-    a = i0 * r0 * it;
-    b = i1 * r1 * it;
-  }
-  __device__ void out(size_t n, T ox, T oy, T cx, T cy, T (&acc)[1]) const {
-    T r0, r1, i0, i1;
-    rn(n, r0, r1);
-    ld_pair(invd, n, i0, i1);
-    const T e0 = c1 * cx + c2 * i0 * (r0 - ox), e1 = c1 * cy + c2 * i1 * (r1 - oy);
-    st_pair(za, n, cx + e0, cy + e1);
-    st_pair(rnew, n, r0, r1);
-    if (INIT) {
-      st_pair(x, n, T(0), T(0));
-    } else {
-      T p0, p1, x0, x1;
-      ld_pair(p, n, p0, p1);
-      ld_pair_rw(x, n, x0, x1);
-      st_pair(x, n, x0 + alpha * p0, x1 + alpha * p1);
-    }
-    acc[0] += r0 * r0 + r1 * r1;
-  }
-  __device__ bool reduce() const { return true; }
-  __device__ void fin(const double (&tot)[1]) const {
-    sc->rr = tot[0];
-    if (INIT) {
-      sc->rr0 = tot[0];
-      sc->it = 0;
-      sc->rz = 0.0;
-      sc->breakdown = 0;
-      sc->alpha = 0.0;
-      sc->beta = 0.0;
-    }
-  }
-};
-
-template <class T>
-struct OpResid {
-  static constexpr int NR = 0;
-  const T *z, *rnew;
-  T *lr;
-  __device__ void begin() {}
-  __device__ void in(size_t n, int, int, T &a, T &b) const { ld_pair(z, n, a, b); }
-  __device__ void out(size_t n, T ox, T oy, T, T, T (&)[1]) const {
-    T r0, r1;
-    ld_pair(rnew, n, r0, r1);
-    st_pair(lr, n, r0 - ox, r1 - oy);
-  }
-  __device__ bool reduce() const { return false; }
-  __device__ void fin(const double (&)[1]) const {}
-};
-
-template <class T>
-struct OpProlong {
-  static constexpr int NR = 0;
-  const T *za, *xc, *rnew, *invd, *coef;
-  const uint8_t *fm;
-  int nxc, nyc;
-  T *zb, *lr, *dv;
-  T it;
-  __device__ void begin() { it = coef[0]; }
-  // t = z_a + P x_1 on the free components (bilinear interpolation, coarse node I on fine 2I)
-  __device__ void in(size_t n, int ix, int iy, T &a, T &b) const {
-    ld_pair(za, n, a, b);
-    const uint8_t m = ldg(fm + n);
-    if (!m) return;
-    const int px0 = ix >> 1, py0 = iy >> 1;
-    const int px1 = px0 + 1 <= nxc ? px0 + 1 : nxc, py1 = py0 + 1 <= nyc ? py0 + 1 : nyc;
-    const T wx1 = (ix & 1) ? T(0.5) : T(0), wx0 = T(1) - wx1;
-    const T wy1 = (iy & 1) ? T(0.5) : T(0), wy0 = T(1) - wy1;
-    const size_t J00 = (size_t)py0 * (nxc + 1) + px0, J01 = (size_t)py0 * (nxc + 1) + px1;
-    const size_t J10 = (size_t)py1 * (nxc + 1) + px0, J11 = (size_t)py1 * (nxc + 1) + px1;
-    T v[2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-      v[c] = wy0 * (wx0 * ldg(xc + 2 * J00 + c) + wx1 * ldg(xc + 2 * J01 + c)) +
-             wy1 * (wx0 * ldg(xc + 2 * J10 + c) + wx1 * ldg(xc + 2 * J11 + c));
-    if (m & 1) a += v[0];
-    if (m & 2) b += v[1];
-  }
-  __device__ void out(size_t n, T ox, T oy, T cx, T cy, T (&)[1]) const {
-    T r0, r1, i0, i1;
-    ld_pair(rnew, n, r0, r1);
-    ld_pair(invd, n, i0, i1);
-    const T s0 = r0 - ox, s1 = r1 - oy;
-    const T d0 = i0 * s0 * it, d1 = i1 * s1 * it;
-    st_pair(zb, n, cx + d0, cy + d1);
-    st_pair(lr, n, s0, s1);
-    st_pair(dv, n, d0, d1);
-  }
-  __device__ bool reduce() const { return false; }
-  __device__ void fin(const double (&)[1]) const {}
-};
-
-template <class T, bool FIRST>
-struct OpFinish {
-  static constexpr int NR = 1;
-  const T *dv, *lr, *invd, *coef, *rnew, *pnew;
-  T *zb, *rprev, *pprev;
-  KrylovScal *sc;
-  T c2, c1;
-  __device__ void begin() {
-    c2 = coef[1];
-    c1 = coef[2];
-  }
-  __device__ void in(size_t n, int, int, T &a, T &b) const { ld_pair(dv, n, a, b); }
-  __device__ void out(size_t n, T ox, T oy, T cx, T cy, T (&acc)[1]) const {
-    T l0, l1, i0, i1, z0, z1, r0, r1;
-    ld_pair(lr, n, l0, l1);
-    ld_pair(invd, n, i0, i1);
-    ld_pair_rw(zb, n, z0, z1);
-    ld_pair(rnew, n, r0, r1);
-    z0 = z0 + (c1 * cx + c2 * i0 * (l0 - ox));
-    z1 = z1 + (c1 * cy + c2 * i1 * (l1 - oy));
-    st_pair(zb, n, z0, z1);
-    acc[0] += r0 * z0 + r1 * z1;
-    // current residual and direction become the previous ones (the first direction uses
-    // p_prev = 0)
-    st_pair(rprev, n, r0, r1);
-    if (FIRST) {
-      st_pair(pprev, n, T(0), T(0));
-    } else {
-      T p0, p1;
-      ld_pair(pnew, n, p0, p1);
-      st_pair(pprev, n, p0, p1);
-    }
-  }
-  __device__ bool reduce() const { return true; }
-  __device__ void fin(const double (&tot)[1]) const {
-    const double old = sc->rz;
-    sc->beta = (!FIRST && old > 0.0 && isfinite(tot[0])) ? tot[0] / old : 0.0;
-    sc->rz = tot[0];
-    if (!(tot[0] > 0.0)) sc->breakdown = 1;
-  }
-};
-
 // ------------------------------------------------------------------------------------
-// Evolution equation: K_dd apply / diagonal / AT2 right-hand side.
+// Evolution equation: K_dd diagonal / AT2 right-hand side (one tile of nodes per CTA,
+// element values staged in shared memory) and the K_dd apply (k_damage_op below).
 // ------------------------------------------------------------------------------------
-enum { DM_APPLY = 0, DM_DIAG = 1, DM_RHS = 2 };
+enum { DM_DIAG = 1, DM_RHS = 2 };
 
 template <class T, class C, int MODE>
 __global__ void __launch_bounds__(TILE_THREADS, sizeof(T) == 4 ? 8 : 4)
-k_damage(GridD g, ElemConst<T> kc, const C *__restrict__ c, const T *__restrict__ x,
-         T *__restrict__ y, KrylovScal *sc, RedWs ws, int epi) {
-  constexpr int PX = TX + 2, PY = TY + 2, EX = TX + 1, EY = TY + 1, NE = EX * EY;
-  __shared__ T sxv[PY * PX];
+k_damage(GridD g, ElemConst<T> kc, const C *__restrict__ c, T *__restrict__ y) {
+  constexpr int EX = TX + 1, EY = TY + 1, NE = EX * EY;
   __shared__ T ef[4][NE];
   const int nx = g.nx, ny = g.ny, ld = nx + 1;
   const int tbx = (nx + 1 + TX - 1) / TX, ntiles = tbx * ((ny + 1 + TY - 1) / TY);
-  T dot = T(0);
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-  const int i0 = (tile % tbx) * TX, j0 = (tile / tbx) * TY;
-  if (MODE == DM_APPLY) {
-    for (int t = threadIdx.x; t < PX * PY; t += TILE_THREADS) {
-      const int li = t % PX, lj = t / PX;
-      const int gi = i0 - 1 + li, gj = j0 - 1 + lj;
-      T v = T(0);
-      if (gi >= 0 && gi <= nx && gj >= 0 && gj <= ny) {
-        const size_t n = (size_t)gj * ld + gi;
-        v = ldg(x + n);
-        if (g.dofm && (ldg(g.dofm + n) & 4)) v = T(0);
-      }
-      sxv[t] = v;
-    }
-    __syncthreads();
-  }
   const T ihx = kc.ihx, ihy = kc.ihy, w = kc.w;
   const T kappa = kc.kappa;
   const T G0 = kc.G0, G1 = kc.G1;
-  for (int t = threadIdx.x; t < NE; t += TILE_THREADS) {
-    const int le = t % EX, me = t / EX;
-    const int ei = i0 - 1 + le, ej = j0 - 1 + me;
-    T f[4] = {T(0), T(0), T(0), T(0)};
-    bool live = ei >= 0 && ei < nx && ej >= 0 && ej < ny;
-    size_t e = 0;
-    if (live) {
-      e = (size_t)ej * nx + ei;
-      if (g.active && !ldg(g.active + e)) live = false;
-    }
-    if (live) {
-      T x0 = 0, x1 = 0, x2 = 0, x3 = 0;
-      if (MODE == DM_APPLY) {
-        const int p0 = me * PX + le;
-        x0 = sxv[p0]; x1 = sxv[p0 + 1]; x2 = sxv[p0 + PX]; x3 = sxv[p0 + PX + 1];
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int i0 = (tile % tbx) * TX, j0 = (tile / tbx) * TY;
+    for (int t = threadIdx.x; t < NE; t += TILE_THREADS) {
+      const int le = t % EX, me = t / EX;
+      const int ei = i0 - 1 + le, ej = j0 - 1 + me;
+      T f[4] = {T(0), T(0), T(0), T(0)};
+      bool live = ei >= 0 && ei < nx && ej >= 0 && ej < ny;
+      size_t e = 0;
+      if (live) {
+        e = (size_t)ej * nx + ei;
+        if (g.active && !ldg(g.active + e)) live = false;
       }
-      if (MODE != DM_APPLY) {
+      if (live) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const T s = (q & 1) ? G1 : G0, tt = (q & 2) ? G1 : G0;
@@ -659,7 +386,70 @@ k_damage(GridD g, ElemConst<T> kc, const C *__restrict__ c, const T *__restrict_
               f[a] += w * (cq * N[a] * N[a] + kappa * (ax[a] * ax[a] + ay[a] * ay[a]));
           }
         }
-      } else {
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) ef[k][t] = f[k];
+    }
+    __syncthreads();
+    const int li = threadIdx.x % TX, lj = threadIdx.x / TX;
+    const int gi = i0 + li, gj = j0 + lj;
+    if (lj < TY && gi <= nx && gj <= ny) {
+      const int e00 = lj * EX + li, e10 = e00 + 1, e01 = e00 + EX, e11 = e01 + 1;
+      T v = ef[3][e00] + ef[2][e10] + ef[1][e01] + ef[0][e11];
+      const size_t n = (size_t)gj * ld + gi;
+      if (MODE != DM_RHS && g.dofm && (ldg(g.dofm + n) & 4)) v = T(0);
+      y[n] = v;
+    }
+    __syncthreads();
+  }  // tiles
+}
+
+// K_dd x with an input/output policy (pf_fused.cuh, B = 1): the tile form of k_damage's
+// apply, the operand formed by op.in() while the CTA stages its node patch and the product
+// handed to op.out() at each owned node.
+template <class T, class Op>
+__global__ void __launch_bounds__(TILE_THREADS, sizeof(T) == 4 ? 8 : 4)
+k_damage_op(GridD g, ElemConst<T> kc, const T *__restrict__ c, Op op, RedWs ws) {
+  constexpr int PX = TX + 2, PY = TY + 2, EX = TX + 1, EY = TY + 1, NE = EX * EY;
+  constexpr int NR = Op::NR > 0 ? Op::NR : 1;
+  __shared__ T sxv[PY * PX];
+  __shared__ T ef[4][NE];
+  const int nx = g.nx, ny = g.ny, ld = nx + 1;
+  const int tbx = (nx + 1 + TX - 1) / TX, ntiles = tbx * ((ny + 1 + TY - 1) / TY);
+  op.begin();
+  T acc[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) acc[k] = T(0);
+  const T ihx = kc.ihx, ihy = kc.ihy, w = kc.w;
+  const T kappa = kc.kappa;
+  const T G0 = kc.G0, G1 = kc.G1;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int i0 = (tile % tbx) * TX, j0 = (tile / tbx) * TY;
+    for (int t = threadIdx.x; t < PX * PY; t += TILE_THREADS) {
+      const int li = t % PX, lj = t / PX;
+      const int gi = i0 - 1 + li, gj = j0 - 1 + lj;
+      T v[1] = {T(0)};
+      if (gi >= 0 && gi <= nx && gj >= 0 && gj <= ny) {
+        const size_t n = (size_t)gj * ld + gi;
+        op.in(n, gi, gj, v);
+        if (g.dofm && (ldg(g.dofm + n) & 4)) v[0] = T(0);
+      }
+      sxv[t] = v[0];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < NE; t += TILE_THREADS) {
+      const int le = t % EX, me = t / EX;
+      const int ei = i0 - 1 + le, ej = j0 - 1 + me;
+      T f[4] = {T(0), T(0), T(0), T(0)};
+      bool live = ei >= 0 && ei < nx && ej >= 0 && ej < ny;
+      size_t e = 0;
+      if (live) {
+        e = (size_t)ej * nx + ei;
+        if (g.active && !ldg(g.active + e)) live = false;
+      }
+      if (live) {
+        const int p0 = me * PX + le;
+        const T x0 = sxv[p0], x1 = sxv[p0 + 1], x2 = sxv[p0 + PX], x3 = sxv[p0 + PX + 1];
         // separable form over the Gauss points (s = G[q & 1], t = G[q >> 1], G0 + G1 = 1)
         const T xbl = G1 * x0 + G0 * x1, xbr = G0 * x0 + G1 * x1;
         const T xtl = G1 * x2 + G0 * x3, xtr = G0 * x2 + G1 * x3;
@@ -667,7 +457,7 @@ k_damage(GridD g, ElemConst<T> kc, const C *__restrict__ c, const T *__restrict_
                          G0 * xbr + G1 * xtr};
         T m[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) m[q] = w * T(ldg(c + 4 * e + q)) * xq[q];
+        for (int q = 0; q < 4; ++q) m[q] = w * ldg(c + 4 * e + q) * xq[q];
         const T ml_lo = G1 * m[0] + G0 * m[1], mr_lo = G0 * m[0] + G1 * m[1];
         const T ml_hi = G1 * m[2] + G0 * m[3], mr_hi = G0 * m[2] + G1 * m[3];
         const T bx = x1 - x0, tx = x3 - x2, ly = x2 - x0, ry = x3 - x1;
@@ -681,26 +471,27 @@ k_damage(GridD g, ElemConst<T> kc, const C *__restrict__ c, const T *__restrict_
         f[2] = G0 * ml_lo + G1 * ml_hi - kx2 + ky1;
         f[3] = G0 * mr_lo + G1 * mr_hi + kx2 + ky2;
       }
-    }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) ef[k][t] = f[k];
-  }
-  __syncthreads();
-  const int li = threadIdx.x % TX, lj = threadIdx.x / TX;
-  const int gi = i0 + li, gj = j0 + lj;
-  if (lj < TY && gi <= nx && gj <= ny) {
-    const int e00 = lj * EX + li, e10 = e00 + 1, e01 = e00 + EX, e11 = e01 + 1;
-    T v = ef[3][e00] + ef[2][e10] + ef[1][e01] + ef[0][e11];
-    const size_t n = (size_t)gj * ld + gi;
-    if (MODE != DM_RHS && g.dofm && (ldg(g.dofm + n) & 4)) v = T(0);
-    y[n] = v;
-    if (MODE == DM_APPLY && epi != EPI_NONE) dot += sxv[(lj + 1) * PX + li + 1] * v;
-  }
-  __syncthreads();
+      for (int k = 0; k < 4; ++k) ef[k][t] = f[k];
+    }
+    __syncthreads();
+    const int li = threadIdx.x % TX, lj = threadIdx.x / TX;
+    const int gi = i0 + li, gj = j0 + lj;
+    if (lj < TY && gi <= nx && gj <= ny) {
+      const int e00 = lj * EX + li, e10 = e00 + 1, e01 = e00 + EX, e11 = e01 + 1;
+      T o[1] = {ef[3][e00] + ef[2][e10] + ef[1][e01] + ef[0][e11]};
+      const size_t n = (size_t)gj * ld + gi;
+      if (g.dofm && (ldg(g.dofm + n) & 4)) o[0] = T(0);
+      const T ci[1] = {sxv[(lj + 1) * PX + li + 1]};
+      op.out(n, o, ci, acc);
+    }
+    __syncthreads();
   }  // tiles
-  if (MODE == DM_APPLY && epi != EPI_NONE) {
-    double vv[1] = {(double)dot}, tot[1];
-    if (grid_reduce<1>(vv, ws, tot)) krylov_epilogue(epi, sc, tot[0]);
+  if (Op::NR > 0 && op.reduce()) {
+    double v[NR], tot[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) v[k] = (double)acc[k];
+    if (grid_reduce<NR>(v, ws, tot)) op.fin(tot);
   }
 }
 
@@ -948,45 +739,45 @@ void elas_apply(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, 
                 T *y, cudaStream_t st, KrylovScal *sc, const RedWs *ws, int epi) {
   const RedWs w = ws ? *ws : RedWs{nullptr, nullptr, 0};
   const int e = ws ? epi : EPI_NONE;
-  strip_launch<T>(g, m, d, tens, OpApply<T>{x, y, sc, e}, w, st);
+  strip_launch<T>(g, m, d, tens, OpApply<T, 2>{x, y, sc, e}, w, st);
 }
 
 template <class T>
 void elas_mg_stage(int stage, const GridD &g, const MatD &m, const T *d, const uint8_t *tens,
-                   const ElasMgBufs<T> &B, const RedWs &ws, cudaStream_t st) {
+                   const MgBufs<T> &B, const RedWs &ws, cudaStream_t st) {
   T *rprev = B.r[0], *rcur = B.r[1], *pprev = B.p[0], *pcur = B.p[1];
   switch (stage) {
     case FS_DIR:
-      strip_launch<T>(g, m, d, tens, OpDir<T>{B.zb, pprev, pcur, B.q, B.sc}, ws, st);
+      strip_launch<T>(g, m, d, tens, OpDir<T, 2>{B.zb, pprev, pcur, B.q, B.sc}, ws, st);
       break;
     case FS_UPD:
       strip_launch<T>(g, m, d, tens,
-                      OpUpd<T, false>{rprev, B.q, pcur, B.invd, B.coef, rcur, B.x, B.za, B.sc},
+                      OpUpd<T, 2, false>{rprev, B.q, pcur, B.invd, B.coef, rcur, B.x, B.za, B.sc},
                       ws, st);
       break;
     case FS_UPD_INIT:
       strip_launch<T>(g, m, d, tens,
-                      OpUpd<T, true>{B.b, nullptr, nullptr, B.invd, B.coef, rcur, B.x, B.za, B.sc},
+                      OpUpd<T, 2, true>{B.b, nullptr, nullptr, B.invd, B.coef, rcur, B.x, B.za, B.sc},
                       ws, st);
       break;
     case FS_RESID:
-      strip_launch<T>(g, m, d, tens, OpResid<T>{B.za, rcur, B.lr}, ws, st);
+      strip_launch<T>(g, m, d, tens, OpResid<T, 2>{B.za, rcur, B.lr}, ws, st);
       break;
     case FS_PROLONG:
       strip_launch<T>(g, m, d, tens,
-                      OpProlong<T>{B.za, B.xc, rcur, B.invd, B.coef, B.fm, B.nxc, B.nyc, B.zb,
+                      OpProlong<T, 2>{B.za, B.xc, rcur, B.invd, B.coef, B.fm, B.nxc, B.nyc, B.zb,
                                    B.lr, B.dv},
                       ws, st);
       break;
     case FS_FINISH:
       strip_launch<T>(g, m, d, tens,
-                      OpFinish<T, false>{B.dv, B.lr, B.invd, B.coef, rcur, pcur, B.zb, rprev,
+                      OpFinish<T, 2, false>{B.dv, B.lr, B.invd, B.coef, rcur, pcur, B.zb, rprev,
                                          pprev, B.sc},
                       ws, st);
       break;
     case FS_FINISH_FIRST:
       strip_launch<T>(g, m, d, tens,
-                      OpFinish<T, true>{B.dv, B.lr, B.invd, B.coef, rcur, pcur, B.zb, rprev,
+                      OpFinish<T, 2, true>{B.dv, B.lr, B.invd, B.coef, rcur, pcur, B.zb, rprev,
                                         pprev, B.sc},
                       ws, st);
       break;
@@ -1005,22 +796,69 @@ void elas_residual(const GridD &g, const MatD &m, const double *u, const double 
   k_elas<double, EL_RESID><<<tile_grid(g), TILE_THREADS, 0, st>>>(
       g, elem_const<double>(g, m), d, nullptr, u, F, tens, nullptr, RedWs{}, EPI_NONE);
 }
+
 template <class T>
 void damage_apply(const GridD &g, const T *c, double kappa, const T *x, T *y, cudaStream_t st,
                   KrylovScal *sc, const RedWs *ws, int epi) {
-  RedWs w = ws ? *ws : RedWs{nullptr, nullptr, 0};
+  const RedWs w = ws ? *ws : RedWs{nullptr, nullptr, 0};
   const int e = ws ? epi : EPI_NONE;
-  k_damage<T, T, DM_APPLY><<<tile_grid(g), TILE_THREADS, 0, st>>>(
-      g, elem_const<T>(g, MatD{}, kappa), c, x, y, sc, w, e);
+  k_damage_op<T, OpApply<T, 1>><<<tile_grid(g), TILE_THREADS, 0, st>>>(
+      g, elem_const<T>(g, MatD{}, kappa), c, OpApply<T, 1>{x, y, sc, e}, w);
+}
+
+template <class T>
+void damage_mg_stage(int stage, const GridD &g, const T *c, double kappa, const MgBufs<T> &B,
+                     const RedWs &ws, cudaStream_t st) {
+  T *rprev = B.r[0], *rcur = B.r[1], *pprev = B.p[0], *pcur = B.p[1];
+  const ElemConst<T> kc = elem_const<T>(g, MatD{}, kappa);
+  const dim3 gt = tile_grid(g);
+  switch (stage) {
+    case FS_DIR:
+      k_damage_op<T, OpDir<T, 1>><<<gt, TILE_THREADS, 0, st>>>(
+          g, kc, c, OpDir<T, 1>{B.zb, pprev, pcur, B.q, B.sc}, ws);
+      break;
+    case FS_UPD:
+      k_damage_op<T, OpUpd<T, 1, false>><<<gt, TILE_THREADS, 0, st>>>(
+          g, kc, c, OpUpd<T, 1, false>{rprev, B.q, pcur, B.invd, B.coef, rcur, B.x, B.za, B.sc},
+          ws);
+      break;
+    case FS_UPD_INIT:
+      k_damage_op<T, OpUpd<T, 1, true>><<<gt, TILE_THREADS, 0, st>>>(
+          g, kc, c,
+          OpUpd<T, 1, true>{B.b, nullptr, nullptr, B.invd, B.coef, rcur, B.x, B.za, B.sc}, ws);
+      break;
+    case FS_RESID:
+      k_damage_op<T, OpResid<T, 1>><<<gt, TILE_THREADS, 0, st>>>(
+          g, kc, c, OpResid<T, 1>{B.za, rcur, B.lr}, ws);
+      break;
+    case FS_PROLONG:
+      k_damage_op<T, OpProlong<T, 1>><<<gt, TILE_THREADS, 0, st>>>(
+          g, kc, c,
+          OpProlong<T, 1>{B.za, B.xc, rcur, B.invd, B.coef, B.fm, B.nxc, B.nyc, B.zb, B.lr, B.dv},
+          ws);
+      break;
+    case FS_FINISH:
+      k_damage_op<T, OpFinish<T, 1, false>><<<gt, TILE_THREADS, 0, st>>>(
+          g, kc, c,
+          OpFinish<T, 1, false>{B.dv, B.lr, B.invd, B.coef, rcur, pcur, B.zb, rprev, pprev, B.sc},
+          ws);
+      break;
+    case FS_FINISH_FIRST:
+      k_damage_op<T, OpFinish<T, 1, true>><<<gt, TILE_THREADS, 0, st>>>(
+          g, kc, c,
+          OpFinish<T, 1, true>{B.dv, B.lr, B.invd, B.coef, rcur, pcur, B.zb, rprev, pprev, B.sc},
+          ws);
+      break;
+  }
 }
 template <class T>
 void damage_diag(const GridD &g, const T *c, double kappa, T *diag, cudaStream_t st) {
   k_damage<T, T, DM_DIAG><<<tile_grid(g), TILE_THREADS, 0, st>>>(
-      g, elem_const<T>(g, MatD{}, kappa), c, nullptr, diag, nullptr, RedWs{}, EPI_NONE);
+      g, elem_const<T>(g, MatD{}, kappa), c, diag);
 }
 void damage_rhs(const GridD &g, const double *H, double *b, cudaStream_t st) {
   k_damage<double, double, DM_RHS><<<tile_grid(g), TILE_THREADS, 0, st>>>(
-      g, elem_const<double>(g, MatD{}, 0.0), H, nullptr, b, nullptr, RedWs{}, EPI_NONE);
+      g, elem_const<double>(g, MatD{}, 0.0), H, b);
 }
 void qp_energy(const GridD &g, const MatD &m, const double *u, const double *Hprev,
                double *psi, double *Hout, cudaStream_t st) {
@@ -1055,11 +893,15 @@ template void elas_diag<double>(const GridD &, const MatD &, const double *, con
 template void elas_diag<float>(const GridD &, const MatD &, const float *, const uint8_t *,
                                float *, cudaStream_t);
 template void elas_mg_stage<double>(int, const GridD &, const MatD &, const double *,
-                                    const uint8_t *, const ElasMgBufs<double> &, const RedWs &,
+                                    const uint8_t *, const MgBufs<double> &, const RedWs &,
                                     cudaStream_t);
 template void elas_mg_stage<float>(int, const GridD &, const MatD &, const float *,
-                                   const uint8_t *, const ElasMgBufs<float> &, const RedWs &,
+                                   const uint8_t *, const MgBufs<float> &, const RedWs &,
                                    cudaStream_t);
+template void damage_mg_stage<double>(int, const GridD &, const double *, double,
+                                      const MgBufs<double> &, const RedWs &, cudaStream_t);
+template void damage_mg_stage<float>(int, const GridD &, const float *, double,
+                                     const MgBufs<float> &, const RedWs &, cudaStream_t);
 template void damage_apply<double>(const GridD &, const double *, double, const double *,
                                    double *, cudaStream_t, KrylovScal *, const RedWs *, int);
 template void damage_apply<float>(const GridD &, const float *, double, const float *, float *,

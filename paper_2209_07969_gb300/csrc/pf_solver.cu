@@ -89,8 +89,8 @@ struct pf_ctx {
   RedWs ws{};
   Gmg<double> gu, gd;        // multigrid hierarchies (FP64 mode)
   Gmg<float> gu32, gd32;     // multigrid hierarchies (FP32 inner solves)
-  GraphSlot graphs[5];        // batched fallback, [slot * 2 + multigrid] and [SL_FUSED]
-  WhileGraph wgraphs[5];      // device-side loops, same indexing
+  GraphSlot graphs[6];        // batched fallback, [slot * 2 + multigrid], [SL_FUSED(_D)]
+  WhileGraph wgraphs[6];      // device-side loops, same indexing
   bool use_graphs = true;
   MgState mg_u, mg_d;
   double prof[PF_PROF_PHASES] = {0};   // host milliseconds per phase (pf_profile)
@@ -159,7 +159,7 @@ GridD grid_nomask(const pf_ctx *ctx) {
 // precision).  Every pointer an iteration touches is a fixed context buffer, so a graph
 // captured once stays valid; operator data (d, tension bits, coefficients, multigrid
 // stencils) are rewritten in place between solves.
-enum { SL_U = 0, SL_D = 1, SL_COUNT = 2, SL_FUSED = 4 };
+enum { SL_U = 0, SL_D = 1, SL_COUNT = 2, SL_FUSED = 4, SL_FUSED_D = 5 };
 
 // Runs batch() (`every` Krylov iterations) until ||r||^2 <= rtol^2 rr0, a breakdown, or
 // maxit.  Each batch ends with the read-back of ||r||^2 and the breakdown flag; with graphs
@@ -268,14 +268,14 @@ pf_status krylov_run(pf_ctx *ctx, int sidx, Init init, Body body, int every, dou
                      int maxit, int *iters, bool *ok) {
   cudaStream_t st = ctx->st;
   WhileGraph &W = ctx->wgraphs[sidx];
-  if (!W.exec && !W.unsupported) {
+  if (ctx->opt.device_loop && !W.exec && !W.unsupported) {
     if (build_while(ctx, W, init, body) != cudaSuccess || !W.exec) {
       W.unsupported = true;
       cudaGetLastError();
     }
   }
   *iters = 0;
-  if (W.exec) {
+  if (ctx->opt.device_loop && W.exec) {
     KrylovScal *hk = host_scal(ctx);
     hk->rtol2 = rtol * rtol;
     hk->maxit = maxit;
@@ -346,17 +346,18 @@ pf_status pcg(pf_ctx *ctx, int slot, Apply apply, Fine fine, Gmg<T> *G, size_t n
   return krylov_run(ctx, slot * 2 + (G ? 1 : 0), init, body, every, rtol, maxit, iters, ok);
 }
 
-// Multigrid PCG on the elasticity tangent with the fine-level work fused into the strip
-// apply (elas_mg_stage): the iteration of pcg() with the V-cycle preconditioner, in five
-// fine-level launches per iteration instead of sixteen.  Needs a hierarchy with at least
-// one grid level above the single-CTA coarse cycle (G.lc >= 1).  Level-0 vectors of the
-// hierarchy serve as the second residual and direction buffers and as smoother scratch.
-template <class T>
-pf_status pcg_mg_elas(pf_ctx *ctx, Gmg<T> &G, const T *d, size_t n, const T *b, T *x, T *r,
-                      T *z, T *p, T *q, double rtol, int maxit, int *iters, bool *ok) {
+// Multigrid PCG with the fine-level work fused into the operator kernel (pf_fused.cuh):
+// the iteration of pcg() with the V-cycle preconditioner in five fine-level launches per
+// iteration instead of sixteen.  stage(s, bufs) launches fused stage s on the fine
+// operator.  Needs a hierarchy with at least one grid level above the single-CTA coarse
+// cycle (G.lc >= 1).  Level-0 vectors of the hierarchy serve as the second residual and
+// direction buffers and as smoother scratch.
+template <class T, class Stage>
+pf_status pcg_mg_fused(pf_ctx *ctx, int sidx, Gmg<T> &G, Stage stage_fn, const T *b, T *x,
+                       T *r, T *z, T *p, T *q, double rtol, int maxit, int *iters, bool *ok) {
   cudaStream_t st = ctx->st;
   GmgLevel<T> &L0 = G.lv[0];
-  ElasMgBufs<T> B;
+  MgBufs<T> B;
   B.b = b;
   B.x = x;
   B.r[0] = r;
@@ -375,8 +376,7 @@ pf_status pcg_mg_elas(pf_ctx *ctx, Gmg<T> &G, const T *d, size_t n, const T *b, 
   B.nxc = G.lv[1].nx;
   B.nyc = G.lv[1].ny;
   B.sc = ctx->sc;
-  (void)n;
-  auto stage = [&](int s) { elas_mg_stage<T>(s, ctx->g, ctx->m, d, ctx->tens, B, ctx->ws, st); };
+  auto stage = [&](int s) { stage_fn(s, B); };
   // residual, restriction, coarse levels and post-smoothing of the V-cycle on r[1]
   auto vcycle_rest = [&](bool first) -> int {
     stage(FS_RESID);
@@ -397,7 +397,25 @@ pf_status pcg_mg_elas(pf_ctx *ctx, Gmg<T> &G, const T *d, size_t n, const T *b, 
     return 2 + vcycle_rest(false);
   };
   const int every = ctx->opt.check_every > 0 ? ctx->opt.check_every : 8;
-  return krylov_run(ctx, SL_FUSED, init, body, every, rtol, maxit, iters, ok);
+  return krylov_run(ctx, sidx, init, body, every, rtol, maxit, iters, ok);
+}
+
+template <class T>
+pf_status pcg_mg_elas(pf_ctx *ctx, Gmg<T> &G, const T *d, const T *b, T *x, T *r, T *z, T *p,
+                      T *q, double rtol, int maxit, int *iters, bool *ok) {
+  auto stage = [ctx, d](int s, const MgBufs<T> &B) {
+    elas_mg_stage<T>(s, ctx->g, ctx->m, d, ctx->tens, B, ctx->ws, ctx->st);
+  };
+  return pcg_mg_fused<T>(ctx, SL_FUSED, G, stage, b, x, r, z, p, q, rtol, maxit, iters, ok);
+}
+
+template <class T>
+pf_status pcg_mg_damage(pf_ctx *ctx, Gmg<T> &G, const T *c, double kappa, const T *b, T *x,
+                        T *r, T *z, T *p, T *q, double rtol, int maxit, int *iters, bool *ok) {
+  auto stage = [ctx, c, kappa](int s, const MgBufs<T> &B) {
+    damage_mg_stage<T>(s, ctx->g, c, kappa, B, ctx->ws, ctx->st);
+  };
+  return pcg_mg_fused<T>(ctx, SL_FUSED_D, G, stage, b, x, r, z, p, q, rtol, maxit, iters, ok);
 }
 
 // FP32 inner solves inside FP64 iterative refinement:  x = 0; repeat {s = 2^-floor(log2
@@ -512,7 +530,7 @@ pf_status newton_correction(pf_ctx *ctx, double tol, int *lin, int *refines, boo
     };
     auto solve = [&](int maxit, int *it, bool *sok) {
       if (mg && ctx->gu.lc >= 1)
-        return pcg_mg_elas<double>(ctx, ctx->gu, ctx->d, n, ctx->kb, ctx->kx, ctx->kr, ctx->kz,
+        return pcg_mg_elas<double>(ctx, ctx->gu, ctx->d, ctx->kb, ctx->kx, ctx->kr, ctx->kz,
                                    ctx->kp, ctx->kq, tol, maxit, it, sok);
       return pcg<double>(ctx, SL_U, A, Af, mg ? &ctx->gu : nullptr, n, ctx->kb, ctx->kx, ctx->kr,
                          ctx->kz, ctx->kp, ctx->kq, ctx->kinv, tol, maxit, it, sok);
@@ -537,7 +555,7 @@ pf_status newton_correction(pf_ctx *ctx, double tol, int *lin, int *refines, boo
   };
   auto solve = [&](int maxit, int *it, bool *iok) {
     if (mg && ctx->gu32.lc >= 1)
-      return pcg_mg_elas<float>(ctx, ctx->gu32, ctx->fd, n, ctx->fb, ctx->fx, ctx->fr, ctx->fz,
+      return pcg_mg_elas<float>(ctx, ctx->gu32, ctx->fd, ctx->fb, ctx->fx, ctx->fr, ctx->fz,
                                 ctx->fp, ctx->fq, ctx->opt.tol_inner, maxit, it, iok);
     return pcg<float>(ctx, SL_U, Af32, Ff32, mg ? &ctx->gu32 : nullptr, n, ctx->fb, ctx->fx,
                       ctx->fr, ctx->fz, ctx->fp, ctx->fq, ctx->finv, ctx->opt.tol_inner, maxit,
@@ -632,6 +650,9 @@ pf_status solve_damage(pf_ctx *ctx, const double *c, const double *rhs, double *
       return PF_OK;
     };
     auto solve = [&](int maxit, int *it, bool *sok) {
+      if (mg && ctx->gd.lc >= 1)
+        return pcg_mg_damage<double>(ctx, ctx->gd, ctx->csolve, kappa, ctx->kb, ctx->dd, ctx->kr,
+                                     ctx->kz, ctx->kp, ctx->kq, ctx->opt.tol_lin, maxit, it, sok);
       return pcg<double>(ctx, SL_D, A, Af, mg ? &ctx->gd : nullptr, n, ctx->kb, ctx->dd, ctx->kr,
                          ctx->kz, ctx->kp, ctx->kq, ctx->kinv, ctx->opt.tol_lin, maxit, it, sok);
     };
@@ -658,6 +679,9 @@ pf_status solve_damage(pf_ctx *ctx, const double *c, const double *rhs, double *
     return PF_OK;
   };
   auto solve = [&](int maxit, int *it, bool *iok) {
+    if (mg && ctx->gd32.lc >= 1)
+      return pcg_mg_damage<float>(ctx, ctx->gd32, ctx->fc, kappa, ctx->fb, ctx->fx, ctx->fr,
+                                  ctx->fz, ctx->fp, ctx->fq, ctx->opt.tol_inner, maxit, it, iok);
     return pcg<float>(ctx, SL_D, Af32, Ff32, mg ? &ctx->gd32 : nullptr, n, ctx->fb, ctx->fx,
                       ctx->fr, ctx->fz, ctx->fp, ctx->fq, ctx->finv, ctx->opt.tol_inner, maxit,
                       it, iok);
@@ -795,6 +819,7 @@ void pf_default_options(pf_options *o) {
   o->project = 0;
   o->check_every = 8;
   o->newton_forcing = 1e-3;
+  o->device_loop = 1;
 }
 
 const char *pf_status_string(pf_status s) {
@@ -973,7 +998,7 @@ pf_status pf_set_options(pf_ctx *ctx, const pf_options *o) {
   if (!ctx || !o) return PF_EINVAL;
   if (!(o->tol_nr > 0) || !(o->tol_lin > 0) || !(o->tol_inner > 0) || o->max_newton < 1 ||
       o->max_stag < 1 || o->max_lin < 1 || o->max_refine < 1 || o->check_every < 1 ||
-      !(o->newton_forcing >= 0))
+      !(o->newton_forcing >= 0) || (o->device_loop != 0 && o->device_loop != 1))
     return set_err(ctx, PF_EINVAL, "invalid options");
   ctx->opt = *o;
   return PF_OK;

@@ -43,7 +43,7 @@ def test_every_declared_symbol_is_exported(L):
 def test_host_only_entry_points(L):
     o = binding.default_options()
     assert o.tol_nr == 1e-7 and o.max_stag == 1000 and o.check_every == 8
-    assert o.newton_forcing == 1e-3
+    assert o.newton_forcing == 1e-3 and o.device_loop == 1
     m = binding.material(210.0, 0.3, 2.7e-3, 0.03, 1e-9, 0)
     assert m.mu == pytest.approx(210.0 / 2.6, rel=1e-15)
     lam = 210.0 * 0.3 / (1.3 * 0.4)
