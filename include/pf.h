@@ -87,7 +87,7 @@ typedef struct {
                         (TOL_NR of Sec. 4) */
   double tol_lin;    /* [1e-10] relative residual of every linear solve (d-solves; u-solves
                         when newton_forcing is 0) */
-  double tol_inner;  /* [1e-4] relative residual of one FP32 inner solve (PF_FP32_IR) */
+  double tol_inner;  /* [1e-3] relative residual of one FP32 inner solve (PF_FP32_IR) */
   int max_newton;    /* [50] Newton iterations per u-solve */
   int max_stag;      /* [1000] staggered iterations per load step */
   int max_lin;       /* [200000] Krylov iterations per linear solve */

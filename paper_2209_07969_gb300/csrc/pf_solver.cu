@@ -810,7 +810,7 @@ void pf_default_options(pf_options *o) {
   if (!o) return;
   o->tol_nr = 1e-7;
   o->tol_lin = 1e-10;
-  o->tol_inner = 1e-4;
+  o->tol_inner = 1e-3;
   o->max_newton = 50;
   o->max_stag = 1000;
   o->max_lin = 200000;
