@@ -19,7 +19,7 @@ constexpr int GMG_MAX_LEVELS = 16;
 constexpr int GMG_COARSE_MAX = 8;   // coarsen while max(nx, ny) > this
 constexpr int CHEB_DEGREE = 2;
 constexpr int COARSE_THREADS = 1024;  // threads of the single-CTA coarse cycle
-constexpr int GMG_CTA_NODES = 300;    // levels with at most this many nodes run in that CTA
+constexpr int GMG_CTA_NODES = 1100;   // levels with at most this many nodes run in that CTA
 
 template <class T>
 struct GmgLevel {

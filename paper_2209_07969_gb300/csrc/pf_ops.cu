@@ -1,13 +1,15 @@
 // Matrix-free Q1 operators and per-Gauss-point kernels of the staggered phase-field
 // method (arXiv 2209.07969), written for sm_103a.
 //
-// Operator kernels use one 256-thread CTA per tile of TX x TY = 32 x 8 nodes.  The CTA
-// stages the (TX+2) x (TY+2) node patch in shared memory, computes the element vectors
-// of the (TX+1) x (TY+1) elements that touch its nodes (the one-element halo is
-// recomputed by the neighbouring CTA as well), and sums the four element contributions
-// of every owned node.  No atomics: results are deterministic and independent of the
-// launch.  The CTAs are register-limited to fill the GPU in one wave at the 512 x 512
-// size (8 CTAs of 256 threads per SM).
+// Elasticity: the tangent product, the nonlinear internal force and the fused Krylov /
+// multigrid stages run in the strip kernel (k_elas_strip: a warp marches up a strip of
+// node columns, neighbours by warp shuffle, no shared memory); the tangent diagonal runs
+// in a tile kernel.  Phase field: K_dd products and fused stages in a tile kernel
+// (k_damage_op), diagonal and right-hand side in k_damage.  Tile kernels use one 256-thread
+// CTA per tile of TX x TY = 32 x 8 nodes, stage the node patch with a one-node halo in
+// shared memory, compute the element values of the (TX+1) x (TY+1) touching elements (the
+// halo elements are recomputed by the neighbouring CTA) and sum the four contributions of
+// every owned node.  No atomics: results are deterministic and independent of the launch.
 //
 // Element quantities (Sec. 2 and 3.2): 2x2 Gauss points at unit coordinates
 // s, t in {G0, G1} = {(1 - 1/sqrt3)/2, (1 + 1/sqrt3)/2}; N_a bilinear; weight hx hy/4.
@@ -120,71 +122,47 @@ __device__ __forceinline__ void elas_element(const ElemConst<T> &kc, T ux0, T ux
   f[7] = R2 + U2;
 }
 
-enum { EL_APPLY = 0, EL_DIAG = 1, EL_RESID = 2 };
-
-template <class T, int MODE>
+// Diagonal of the elasticity tangent (Jacobi preconditioner, multigrid smoother data for
+// the matrix-free level): one tile of TX x TY nodes per CTA, d staged in shared memory with
+// a one-node halo, element diagonals of the (TX+1) x (TY+1) touching elements summed per
+// node.
+template <class T>
 __global__ void __launch_bounds__(TILE_THREADS, sizeof(T) == 4 ? 8 : 4)
-k_elas(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restrict__ tens_in,
-       const T *__restrict__ x, T *__restrict__ y, uint8_t *__restrict__ tens_out,
-       KrylovScal *sc, RedWs ws, int epi) {
+k_elas_diag(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restrict__ tens,
+            T *__restrict__ y) {
   constexpr int PX = TX + 2, PY = TY + 2, EX = TX + 1, EY = TY + 1, NE = EX * EY;
-  __shared__ T sx[2][PY * PX];
   __shared__ T sd[PY * PX];
   __shared__ T ef[8][NE];
   const int nx = g.nx, ny = g.ny, ld = nx + 1;
   const int tbx = (nx + 1 + TX - 1) / TX, ntiles = tbx * ((ny + 1 + TY - 1) / TY);
-  T dot = T(0);
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-  const int i0 = (tile % tbx) * TX, j0 = (tile / tbx) * TY;
-
-  for (int t = threadIdx.x; t < PX * PY; t += TILE_THREADS) {
-    const int li = t % PX, lj = t / PX;
-    const int gi = i0 - 1 + li, gj = j0 - 1 + lj;
-    const bool in = gi >= 0 && gi <= nx && gj >= 0 && gj <= ny;
-    const size_t n = (size_t)gj * ld + gi;
-    T vx = T(0), vy = T(0), vd = T(0);
-    if (in) {
-      vd = ldg(d + n);
-      if (MODE != EL_DIAG) {
-        ld_pair(x, n, vx, vy);
-        if (MODE == EL_APPLY && g.dofm) {
-          const uint8_t mk = ldg(g.dofm + n);
-          if (mk & 1) vx = T(0);
-          if (mk & 2) vy = T(0);
-        }
-      }
-    }
-    sx[0][t] = vx;
-    sx[1][t] = vy;
-    sd[t] = vd;
-  }
-  __syncthreads();
-
   const T ihx = kc.ihx, ihy = kc.ihy, w = kc.w;
   const T mu = kc.mu, K = kc.K, cd = kc.cd, eta = kc.eta;
   const T G0 = kc.G0, G1 = kc.G1;
-  for (int t = threadIdx.x; t < NE; t += TILE_THREADS) {
-    const int le = t % EX, me = t / EX;
-    const int ei = i0 - 1 + le, ej = j0 - 1 + me;
-    T f[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) f[k] = T(0);
-    bool live = ei >= 0 && ei < nx && ej >= 0 && ej < ny;
-    size_t e = 0;
-    if (live) {
-      e = (size_t)ej * nx + ei;
-      if (g.active && !ldg(g.active + e)) live = false;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int i0 = (tile % tbx) * TX, j0 = (tile / tbx) * TY;
+    for (int t = threadIdx.x; t < PX * PY; t += TILE_THREADS) {
+      const int li = t % PX, lj = t / PX;
+      const int gi = i0 - 1 + li, gj = j0 - 1 + lj;
+      const bool in = gi >= 0 && gi <= nx && gj >= 0 && gj <= ny;
+      sd[t] = in ? ldg(d + (size_t)gj * ld + gi) : T(0);
     }
-    if (live) {
-      const int p0 = me * PX + le, p1 = p0 + 1, p2 = p0 + PX, p3 = p2 + 1;
-      const T d0 = sd[p0], d1 = sd[p1], d2 = sd[p2], d3 = sd[p3];
-      T ux0 = 0, ux1 = 0, ux2 = 0, ux3 = 0, uy0 = 0, uy1 = 0, uy2 = 0, uy3 = 0;
-      if (MODE != EL_DIAG) {
-        ux0 = sx[0][p0]; ux1 = sx[0][p1]; ux2 = sx[0][p2]; ux3 = sx[0][p3];
-        uy0 = sx[1][p0]; uy1 = sx[1][p1]; uy2 = sx[1][p2]; uy3 = sx[1][p3];
+    __syncthreads();
+    for (int t = threadIdx.x; t < NE; t += TILE_THREADS) {
+      const int le = t % EX, me = t / EX;
+      const int ei = i0 - 1 + le, ej = j0 - 1 + me;
+      T f[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) f[k] = T(0);
+      bool live = ei >= 0 && ei < nx && ej >= 0 && ej < ny;
+      size_t e = 0;
+      if (live) {
+        e = (size_t)ej * nx + ei;
+        if (g.active && !ldg(g.active + e)) live = false;
       }
-      uint8_t tb = (MODE == EL_RESID) ? 0 : ldg(tens_in + e);
-      if (MODE == EL_DIAG) {
+      if (live) {
+        const int p0 = me * PX + le, p1 = p0 + 1, p2 = p0 + PX, p3 = p2 + 1;
+        const T d0 = sd[p0], d1 = sd[p1], d2 = sd[p2], d3 = sd[p3];
+        const uint8_t tb = ldg(tens + e);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const T s = (q & 1) ? G1 : G0, tt = (q & 2) ? G1 : G0;
@@ -204,42 +182,28 @@ k_elas(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restr
             f[2 * a + 1] += w * (Dn * ay[a] * ay[a] + Ds * ax[a] * ax[a]);
           }
         }
-      } else {
-        elas_element<T, MODE == EL_RESID>(kc, ux0, ux1, ux2, ux3, uy0, uy1, uy2, uy3, d0, d1, d2,
-                                          d3, tb, f);
       }
-      if (MODE == EL_RESID && tens_out) tens_out[e] = tb;
-    }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) ef[k][t] = f[k];
-  }
-  __syncthreads();
-
-  const int li = threadIdx.x % TX, lj = threadIdx.x / TX;
-  const int gi = i0 + li, gj = j0 + lj;
-  if (lj < TY && gi <= nx && gj <= ny) {
-    const int e00 = lj * EX + li, e10 = e00 + 1, e01 = e00 + EX, e11 = e01 + 1;
-    T fx = ef[6][e00] + ef[4][e10] + ef[2][e01] + ef[0][e11];
-    T fy = ef[7][e00] + ef[5][e10] + ef[3][e01] + ef[1][e11];
-    const size_t n = (size_t)gj * ld + gi;
-    if (MODE != EL_RESID && g.dofm) {
-      const uint8_t mk = ldg(g.dofm + n);
-      if (mk & 1) fx = T(0);
-      if (mk & 2) fy = T(0);
+      for (int k = 0; k < 8; ++k) ef[k][t] = f[k];
     }
-    y[2 * n] = fx;
-    y[2 * n + 1] = fy;
-    if (MODE == EL_APPLY && epi != EPI_NONE) {
-      const int p = (lj + 1) * PX + li + 1;
-      dot += sx[0][p] * fx + sx[1][p] * fy;
+    __syncthreads();
+    const int li = threadIdx.x % TX, lj = threadIdx.x / TX;
+    const int gi = i0 + li, gj = j0 + lj;
+    if (lj < TY && gi <= nx && gj <= ny) {
+      const int e00 = lj * EX + li, e10 = e00 + 1, e01 = e00 + EX, e11 = e01 + 1;
+      T fx = ef[6][e00] + ef[4][e10] + ef[2][e01] + ef[0][e11];
+      T fy = ef[7][e00] + ef[5][e10] + ef[3][e01] + ef[1][e11];
+      const size_t n = (size_t)gj * ld + gi;
+      if (g.dofm) {
+        const uint8_t mk = ldg(g.dofm + n);
+        if (mk & 1) fx = T(0);
+        if (mk & 2) fy = T(0);
+      }
+      y[2 * n] = fx;
+      y[2 * n + 1] = fy;
     }
-  }
-  __syncthreads();
+    __syncthreads();
   }  // tiles
-  if (MODE == EL_APPLY && epi != EPI_NONE) {
-    double v[1] = {(double)dot}, tot[1];
-    if (grid_reduce<1>(v, ws, tot)) krylov_epilogue(epi, sc, tot[0]);
-  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -256,9 +220,11 @@ constexpr int STRIP_WARPS = 4;  // warps per CTA
 
 // SR node rows per warp: short strips on small grids (more warps to hide latency), long
 // strips on large ones (less halo re-reading).
-template <class T, int SR, class Op>
+// RESID: internal force of the nonlinear stress law instead of the tangent product; the
+// element's tension bits are computed and stored (by the lane and row that own the element).
+template <class T, int SR, class Op, bool RESID = false>
 __global__ void __launch_bounds__(32 * STRIP_WARPS)
-k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *__restrict__ tens,
+k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, uint8_t *__restrict__ tens,
              Op op, RedWs ws) {
   constexpr int NR = Op::NR > 0 ? Op::NR : 1;
   const unsigned FULL = 0xffffffffu;
@@ -308,8 +274,14 @@ k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, const uint8_t *_
       if (lane < 31 && i >= 0 && i < nx && j >= 0 && j < ny) {
         const size_t e = (size_t)j * nx + i;
         if (!g.active || ldg(g.active + e)) {
-          uint8_t tb = ldg(tens + e);
-          elas_element<T, false>(kc, cx, rx0, nxv, rx1, cy, ry0, nyv, ry1, cdv, rd0, ndv, rd1, tb, f);
+          if (RESID) {
+            uint8_t tb = 0;
+            elas_element<T, true>(kc, cx, rx0, nxv, rx1, cy, ry0, nyv, ry1, cdv, rd0, ndv, rd1, tb, f);
+            if (tens && j >= r0 && lane >= 1) tens[e] = tb;   // tens may be NULL
+          } else {
+            uint8_t tb = ldg(tens + e);
+            elas_element<T, false>(kc, cx, rx0, nxv, rx1, cy, ry0, nyv, ry1, cdv, rd0, ndv, rd1, tb, f);
+          }
         }
       }
       const T lx1 = __shfl_up_sync(FULL, f[2], 1), ly1 = __shfl_up_sync(FULL, f[3], 1);
@@ -716,9 +688,10 @@ static inline unsigned elem_blocks(size_t n) {
   return (unsigned)(b < 1 ? 1 : (b > 65535u * 8u ? 65535u * 8u : b));
 }
 
-template <class T, class Op>
-static void strip_launch(const GridD &g, const MatD &m, const T *d, const uint8_t *tens,
+template <class T, class Op, bool RESID = false>
+static void strip_launch(const GridD &g, const MatD &m, const T *d, const uint8_t *tens_c,
                          const Op &op, const RedWs &w, cudaStream_t st) {
+  uint8_t *tens = const_cast<uint8_t *>(tens_c);  // written only by the RESID form
   const size_t nn = (size_t)(g.nx + 1) * (g.ny + 1);
   const unsigned strips = (unsigned)((g.nx + 1 + SW - 1) / SW);
   auto blocks = [&](int sr) {
@@ -726,12 +699,17 @@ static void strip_launch(const GridD &g, const MatD &m, const T *d, const uint8_
     return (warps + STRIP_WARPS - 1) / STRIP_WARPS;
   };
   const ElemConst<T> kc = elem_const<T>(g, m);
-  if (nn < (size_t)1500000)
-    k_elas_strip<T, 2, Op><<<blocks(2), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
+  // A warp also evaluates the element row below its chunk: SR rows cost SR + 1 element rows.
+  // FP32 launches are latency-bound at small sizes (short strips, more warps); FP64 ones
+  // are bound by the FP64 pipe, so they take long strips to waste little arithmetic.
+  if (sizeof(T) == 8 && nn >= (size_t)100000)
+    k_elas_strip<T, 8, Op, RESID><<<blocks(8), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
+  else if (nn < (size_t)1500000)
+    k_elas_strip<T, 2, Op, RESID><<<blocks(2), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
   else if (nn < (size_t)6000000)
-    k_elas_strip<T, 4, Op><<<blocks(4), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
+    k_elas_strip<T, 4, Op, RESID><<<blocks(4), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
   else
-    k_elas_strip<T, 8, Op><<<blocks(8), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
+    k_elas_strip<T, 8, Op, RESID><<<blocks(8), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
 }
 
 template <class T>
@@ -787,14 +765,16 @@ void elas_mg_stage(int stage, const GridD &g, const MatD &m, const T *d, const u
 template <class T>
 void elas_diag(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, T *diag,
                cudaStream_t st) {
-  k_elas<T, EL_DIAG><<<tile_grid(g), TILE_THREADS, 0, st>>>(g, elem_const<T>(g, m), d, tens,
-                                                            nullptr, diag, nullptr, nullptr,
-                                                            RedWs{}, EPI_NONE);
+  k_elas_diag<T><<<tile_grid(g), TILE_THREADS, 0, st>>>(g, elem_const<T>(g, m), d, tens, diag);
 }
 void elas_residual(const GridD &g, const MatD &m, const double *u, const double *d, double *F,
                    uint8_t *tens, cudaStream_t st) {
-  k_elas<double, EL_RESID><<<tile_grid(g), TILE_THREADS, 0, st>>>(
-      g, elem_const<double>(g, m), d, nullptr, u, F, tens, nullptr, RedWs{}, EPI_NONE);
+  // u carries the Dirichlet values and F the forces on constrained DOFs too: no masking
+  GridD gu = g;
+  gu.dofm = nullptr;
+  strip_launch<double, OpApply<double, 2>, true>(gu, m, d, tens,
+                                                 OpApply<double, 2>{u, F, nullptr, EPI_NONE},
+                                                 RedWs{nullptr, nullptr, 0}, st);
 }
 
 template <class T>
