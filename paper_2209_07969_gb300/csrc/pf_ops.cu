@@ -257,13 +257,33 @@ k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, uint8_t *__restr
         }
       }
     };
+    // Short strips (SR <= 4) load all SR + 2 input rows up front, so the chunk pays one
+    // memory round trip instead of one per row; long strips stream the rows.
+    constexpr int PF = SR <= 4 ? SR + 2 : 1;
+    T px[PF], py[PF], pd[PF];
+    if (PF > 1) {
+#pragma unroll
+      for (int r = 0; r < PF; ++r) load(r0 - 1 + r, px[r], py[r], pd[r]);
+    }
     T cx, cy, cdv;
-    load(r0 - 1, cx, cy, cdv);
+    if (PF > 1) {
+      cx = px[0];
+      cy = py[0];
+      cdv = pd[0];
+    } else {
+      load(r0 - 1, cx, cy, cdv);
+    }
     T carry_x = T(0), carry_y = T(0);
 #pragma unroll
     for (int j = r0 - 1; j < r0 + SR; ++j) {
       T nxv, nyv, ndv;
-      load(j + 1, nxv, nyv, ndv);
+      if (PF > 1) {
+        nxv = px[j - r0 + 2];
+        nyv = py[j - r0 + 2];
+        ndv = pd[j - r0 + 2];
+      } else {
+        load(j + 1, nxv, nyv, ndv);
+      }
       const T rx0 = __shfl_down_sync(FULL, cx, 1), ry0 = __shfl_down_sync(FULL, cy, 1);
       const T rd0 = __shfl_down_sync(FULL, cdv, 1);
       const T rx1 = __shfl_down_sync(FULL, nxv, 1), ry1 = __shfl_down_sync(FULL, nyv, 1);
