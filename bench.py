@@ -52,6 +52,13 @@ def parse():
                    help="time one operator kernel on the --grid tensile mesh and exit")
     p.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     p.add_argument("--reps", type=int, default=20)
+    p.add_argument("--serve", action="store_true",
+                   help="served-batch mode: a seeded mix of full load paths through the "
+                        "continuous-batching server; prints served paths/s and p50/p99 latencies")
+    p.add_argument("--requests", type=int, default=24)
+    p.add_argument("--grids", default="64,128")
+    p.add_argument("--rate", type=float, default=4.0, help="Poisson arrival rate, requests/s")
+    p.add_argument("--slots", type=int, default=8)
     p.add_argument("--host-loop", action="store_true",
                    help="host-checked Krylov batches instead of device-side loops (same "
                         "kernels; for profilers that cannot see inside conditional graph nodes)")
@@ -437,6 +444,50 @@ def run_full_path(args):
             s.close()
 
 
+def run_serve(args):
+    """The served-batch workload at reduced grid sizes: requests (tensile or shear notched
+    square, random material, scheme ST/S1/S2, full 100/150-step paths) arrive as a Poisson
+    process and are admitted by the server by slot and HBM footprint; FP32 CG + FP64
+    refinement, multigrid.  Reports completed load paths per second of wall time and
+    p50/p99 latency per load step (device time) and per path (arrival to completion)."""
+    import torch
+    from paper_2209_07969_gb300 import binding, build, server, specimens as S
+    build.build()
+    torch.cuda.set_device(0)
+    grids = tuple(int(g) for g in args.grids.split(","))
+    mix = S.served_batch(args.requests, seed=0, rate_per_s=args.rate, grids=grids)
+    reqs = [server.Request(sp, scheme=sch, precision=binding.FP32_IR,
+                           precond=binding.PRECOND_GMG, tol=1e-5) for _, sp, sch in mix]
+    free, _ = torch.cuda.mem_get_info()
+    srv = server.Server(hbm_budget=int(0.8 * free), slots=args.slots, device=0)
+    t0 = time.perf_counter()
+    for (t, _, _), r in zip(mix, reqs):
+        wait = t0 + t - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        srv.submit(r)
+    srv.drain()
+    wall = time.perf_counter() - t0
+    srv.close()
+    res = srv.results
+    done = [r for r in res.values() if r.ok]
+    steps, paths = server.latency_percentiles(res)
+    conv = sum(sum(r.converged) for r in done) / max(1, sum(len(r.converged) for r in done))
+    line = {"mode": "serve", "metric": METRIC, "value": len(done) / wall, "unit": UNIT,
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "served batch: tensile/shear notched squares, random "
+                                   "E, nu, G_c, l in [2h, 4h], scheme ST/S1/S2, full paths "
+                                   "(100/150 steps)",
+                       "requests": args.requests, "grids": list(grids), "rate_per_s": args.rate,
+                       "slots": args.slots, "seed": 0},
+            "wall_s": wall, "completed": len(done), "failed": len(res) - len(done),
+            "steps_converged_fraction": conv,
+            "step_latency_ms": steps, "path_latency_s": paths,
+            "queue_s_p50": float(statistics.median(r.queue_s for r in done)) if done else None,
+            "peak_running": srv.peak_running, "peak_hbm_bytes": srv.peak_in_use}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
@@ -445,5 +496,7 @@ if __name__ == "__main__":
         run_kernel(a)
     elif a.full_path:
         run_full_path(a)
+    elif a.serve:
+        run_serve(a)
     else:
         run_ours(a)
