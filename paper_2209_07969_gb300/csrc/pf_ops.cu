@@ -122,6 +122,73 @@ __device__ __forceinline__ void elas_element(const ElemConst<T> &kc, T ux0, T ux
   f[7] = R2 + U2;
 }
 
+// FP32 tangent element in packed FP32x2 arithmetic (sm_100 family: one FFMA2 / FADD2 /
+// FMUL2 instruction does two FP32 operations).  Same operations as elas_element<float,false>
+// with the Gauss points paired by equal t: lo = (q0, q1), hi = (q2, q3); .x has s = G0, .y
+// has s = G1.  The kernel is issue-bound at large grids, so halving the arithmetic
+// instructions shortens it.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2b(float a) { return make_float2(a, a); }
+__device__ __forceinline__ void elas_element_tangent_f2(const ElemConst<float> &kc, float ux0,
+                                                        float ux1, float ux2, float ux3,
+                                                        float uy0, float uy1, float uy2,
+                                                        float uy3, float d0, float d1, float d2,
+                                                        float d3, uint8_t tb, float (&f)[8]) {
+  const float G0 = kc.G0, G1 = kc.G1;
+  const float2 Ga = f2(G1, G0), Gb = f2(G0, G1), m1 = f2b(-1.f);
+  // nodal differences: (dxb, dxt), (dyl, dyr), (uyb, uyt), (uxl, uxr)
+  const float2 dx = __ffma2_rn(m1, f2(ux0, ux2), f2(ux1, ux3));
+  const float2 dy = __ffma2_rn(m1, f2(uy0, uy1), f2(uy2, uy3));
+  const float2 duy = __ffma2_rn(m1, f2(uy0, uy2), f2(uy1, uy3));
+  const float2 dux = __ffma2_rn(m1, f2(ux0, ux1), f2(ux2, ux3));
+  // (lo, hi) or (l, r) pairs of the separable strain interpolants
+  const float2 exx = __fmul2_rn(__ffma2_rn(Ga, f2b(dx.x), __fmul2_rn(Gb, f2b(dx.y))), f2b(kc.ihx));
+  const float2 eyy = __fmul2_rn(__ffma2_rn(Ga, f2b(dy.x), __fmul2_rn(Gb, f2b(dy.y))), f2b(kc.ihy));
+  const float2 uxy = __fmul2_rn(__ffma2_rn(Ga, f2b(dux.x), __fmul2_rn(Gb, f2b(dux.y))), f2b(kc.ihy));
+  const float2 uyx = __fmul2_rn(__ffma2_rn(Ga, f2b(duy.x), __fmul2_rn(Gb, f2b(duy.y))), f2b(kc.ihx));
+  // d at the points: db = (dbl, dbr), dt = (dtl, dtr); lo = G1 db + G0 dt, hi = G0 db + G1 dt
+  const float2 db = __ffma2_rn(Ga, f2b(d0), __fmul2_rn(Gb, f2b(d1)));
+  const float2 dt = __ffma2_rn(Ga, f2b(d2), __fmul2_rn(Gb, f2b(d3)));
+  const float2 dq[2] = {__ffma2_rn(f2b(G1), db, __fmul2_rn(f2b(G0), dt)),
+                        __ffma2_rn(f2b(G0), db, __fmul2_rn(f2b(G1), dt))};
+  const float2 exv[2] = {f2b(exx.x), f2b(exx.y)};
+  const float2 gxv[2] = {__fadd2_rn(uxy, f2b(uyx.x)), __fadd2_rn(uxy, f2b(uyx.y))};
+  const float2 wx = f2b(kc.w * kc.ihx), wy = f2b(kc.w * kc.ihy);
+  const float2 one = f2b(1.f), eta = f2b(kc.eta), Kv = f2b(kc.K), mcd = f2b(-kc.cd);
+  const float2 mu2 = f2b(2.f * kc.mu), muv = f2b(kc.mu);
+  float2 P[2], Q[2], R[2], U[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float2 om = __ffma2_rn(m1, dq[h], one);
+    const float2 gq = __ffma2_rn(om, om, eta);
+    const float2 tr = __fadd2_rn(exv[h], eyy);
+    const float2 gsel = f2(((tb >> (2 * h)) & 1) ? gq.x : 1.f, ((tb >> (2 * h + 1)) & 1) ? gq.y : 1.f);
+    const float2 vol = __fmul2_rn(__fmul2_rn(Kv, tr), gsel);
+    const float2 gm2 = __fmul2_rn(gq, mu2);
+    const float2 sxy = __fmul2_rn(__fmul2_rn(gq, muv), gxv[h]);
+    P[h] = __fmul2_rn(wx, __ffma2_rn(gm2, __ffma2_rn(mcd, tr, exv[h]), vol));
+    U[h] = __fmul2_rn(wy, __ffma2_rn(gm2, __ffma2_rn(mcd, tr, eyy), vol));
+    Q[h] = __fmul2_rn(wy, sxy);
+    R[h] = __fmul2_rn(wx, sxy);
+  }
+  // t-sums over the pair (.x + .y), s-sums across the pairs (lo + hi)
+  const float Plo = P[0].x + P[0].y, Phi = P[1].x + P[1].y;
+  const float Rlo = R[0].x + R[0].y, Rhi = R[1].x + R[1].y;
+  const float2 QlQr = __fadd2_rn(Q[0], Q[1]), UlUr = __fadd2_rn(U[0], U[1]);
+  const float2 P12 = __ffma2_rn(Ga, f2b(Plo), __fmul2_rn(Gb, f2b(Phi)));    // (P1, P2)
+  const float2 R12 = __ffma2_rn(Ga, f2b(Rlo), __fmul2_rn(Gb, f2b(Rhi)));
+  const float2 Q12 = __ffma2_rn(Ga, f2b(QlQr.x), __fmul2_rn(Gb, f2b(QlQr.y)));
+  const float2 U12 = __ffma2_rn(Ga, f2b(UlUr.x), __fmul2_rn(Gb, f2b(UlUr.y)));
+  f[0] = -P12.x - Q12.x;
+  f[1] = -R12.x - U12.x;
+  f[2] = P12.x - Q12.y;
+  f[3] = R12.x - U12.y;
+  f[4] = -P12.y + Q12.x;
+  f[5] = -R12.y + U12.x;
+  f[6] = P12.y + Q12.y;
+  f[7] = R12.y + U12.y;
+}
+
 // Diagonal of the elasticity tangent (Jacobi preconditioner, multigrid smoother data for
 // the matrix-free level): one tile of TX x TY nodes per CTA, d staged in shared memory with
 // a one-node halo, element diagonals of the (TX+1) x (TY+1) touching elements summed per
@@ -300,7 +367,12 @@ k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, uint8_t *__restr
             if (tens && j >= r0 && lane >= 1) tens[e] = tb;   // tens may be NULL
           } else {
             uint8_t tb = ldg(tens + e);
-            elas_element<T, false>(kc, cx, rx0, nxv, rx1, cy, ry0, nyv, ry1, cdv, rd0, ndv, rd1, tb, f);
+            if constexpr (sizeof(T) == 4)
+              elas_element_tangent_f2(kc, cx, rx0, nxv, rx1, cy, ry0, nyv, ry1, cdv, rd0, ndv, rd1,
+                                      tb, f);
+            else
+              elas_element<T, false>(kc, cx, rx0, nxv, rx1, cy, ry0, nyv, ry1, cdv, rd0, ndv, rd1,
+                                     tb, f);
           }
         }
       }
