@@ -20,7 +20,9 @@ Degraded stress (Sec. 2, constitutive equation for sigma)::
 
     sigma = g(d) [2 mu eps_dev + K <tr>_+ I] + K <tr>_- I
 
-AT2 model (Table 1): g(d) = (1-d)^2 + eta, w(d) = d^2, c_w = 2.
+AT2 model (Table 1): g(d) = (1-d)^2 + eta, w(d) = d^2, c_w = 2 (history field).
+AT1 model (Table 1): same g, w(d) = d, c_w = 8/3, irreversibility by the penalty term of
+the evolution equation (Sec. 2, penalty parameter gamma = 27 G_c / (64 l tol_ir^2)).
 """
 import numpy as np
 
@@ -177,6 +179,44 @@ def fixed_stress_Q(tr, ee, scheme, m):
     if scheme == S3:
         return dev + tp2
     return np.zeros_like(tr)
+
+
+# ---- AT1 with penalty (Sec. 2, Table 1) -------------------------------------------------
+AT2, AT1 = 0, 1
+CW_AT1 = 8.0 / 3.0
+
+
+def at1_constants(m, tol_ir):
+    """(a, kappa, gamma) of the AT1 evolution equation (Sec. 2)
+
+        -2 (1-d) Psi+ + a + gamma <d - d_{n-1}>_- - kappa lap d = 0,
+
+    a = G_c / (c_w l) (the w'(d) = 1 term), kappa = 2 G_c l / c_w, gamma = 27 G_c /
+    (64 l tol_ir^2).  a is also Psi_crit of the softening test for AT1 (Sec. 3.5)."""
+    a = m.Gc / (CW_AT1 * m.l)
+    kappa = 2.0 * m.Gc * m.l / CW_AT1
+    gamma = 27.0 * m.Gc / (64.0 * m.l * tol_ir ** 2)
+    return a, kappa, gamma
+
+
+def at1_mass_coefficient(psi, d_q, dprev_q, gamma):
+    """Per-point mass coefficient of the AT1 Jacobian: g''/2-term 2 Psi+ plus gamma where
+    the penalty is active (d < d_{n-1}, strict)."""
+    return 2.0 * psi + np.where(d_q < dprev_q, gamma, 0.0)
+
+
+def at1_augmented_coefficient(c_J, k_extra, m, floor=True):
+    """AT1 counterpart of ``augmented_coefficient``.  At activated points (K~ < 0) the
+    augmented mass coefficient is limited below by 2 G_c / (c_w l), the expression that
+    gives the AT2 limit G_c / l.  AT1 has no w'' term in its tangent (w = d), so without a
+    positive limit K~ can remove the whole mass term and leave the pure gradient term,
+    singular wherever no phase-field Dirichlet value anchors it (the homogeneous bar).
+    Inactive points keep the Jacobian coefficient."""
+    c = c_J + k_extra
+    if not floor:
+        return c
+    lim = np.minimum(c_J, 2.0 * m.Gc / (CW_AT1 * m.l))
+    return np.where(k_extra < 0.0, np.maximum(c, lim), c_J)
 
 
 def activation(psi, H_prev, d_q, m, psi_crit=None):

@@ -37,7 +37,7 @@ from . import model, q1
 
 class Options:
     def __init__(self, tol_nr=1e-7, tol_st=1e-6, max_newton=50, max_stag=1000,
-                 psi_crit=None, project=False, kt_floor=True):
+                 psi_crit=None, project=False, kt_floor=True, model=0, tol_ir=0.01):
         self.tol_nr = tol_nr          # TOL_NR (Sec. 4 intro: 1e-7)
         self.tol_st = tol_st          # TOL_ST (Sec. 4 intro: 1e-6)
         self.max_newton = max_newton
@@ -45,6 +45,8 @@ class Options:
         self.psi_crit = psi_crit      # override of Psi_crit (None: G_c/(c_w l))
         self.project = project        # clamp d into [d_{n-1}, 1] after each d-solve
         self.kt_floor = kt_floor      # augmented coefficient >= G_c/l (model.augmented_coefficient)
+        self.model = model            # model.AT2 (history field) or model.AT1 (penalty)
+        self.tol_ir = tol_ir          # AT1 irreversibility tolerance (Sec. 2: 0.01)
 
 
 class State:
@@ -171,6 +173,86 @@ def stag_residual(grid, m, u, d, H_prev):
     return float(np.max(np.abs(R[free] / K.diagonal()[free])))
 
 
+# ---- AT1 with penalty irreversibility --------------------------------------------------
+def at1_residual(grid, m, psi, d, d_prev, opts):
+    """R_d(d) = int [-2(1-d) Psi + a + gamma <d - d_{n-1}>_-] N + kappa int grad N . grad d
+    (Sec. 2) at per-point energy ``psi``; also returns the Jacobian coefficient and kappa."""
+    a, kappa, gamma = model.at1_constants(m, opts.tol_ir)
+    d_q = q1.interp_qp(grid, d)
+    dp_q = q1.interp_qp(grid, d_prev)
+    K = q1.assemble_damage(grid, 2.0 * psi, kappa)        # 2 Psi d N + kappa grad grad
+    src = -2.0 * psi + a + gamma * np.minimum(d_q - dp_q, 0.0)
+    R = K @ d + q1.damage_rhs(grid, 0.5 * src)            # damage_rhs integrates 2 (.) N
+    return R, model.at1_mass_coefficient(psi, d_q, dp_q, gamma), kappa
+
+
+def at1_newton(grid, m, psi, d, d_prev, opts, c_first=None):
+    """Semismooth Newton for the AT1 evolution equation at fixed energy ``psi``.
+
+    c_first: per-point mass coefficient of the first iteration's matrix (the fixed-stress
+    augmented tangent), None for the exact Jacobian.  Stop: ||R_free|| <= TOL_NR *
+    max(||R^0_free||, ||int a N||).  Returns (d, first increment, iterations).
+    """
+    a, kappa, _ = model.at1_constants(m, opts.tol_ir)
+    cd = grid.d_constrained()
+    free = ~cd
+    d = d.copy()
+    fscale = np.linalg.norm(q1.damage_rhs(grid, np.full((grid.ne, 4), 0.5 * a))[free])
+    r0 = None
+    first = np.zeros(grid.nn)
+    for it in range(opts.max_newton + 1):
+        R, cJ, _ = at1_residual(grid, m, psi, d, d_prev, opts)
+        rn = np.linalg.norm(R[free])
+        if r0 is None:
+            r0 = rn
+        if rn == 0.0 or rn <= opts.tol_nr * max(r0, fscale):
+            return d, first, it
+        if it == opts.max_newton:
+            break
+        c = c_first if (it == 0 and c_first is not None) else cJ
+        J = q1.assemble_damage(grid, c, kappa)
+        dd = np.zeros(grid.nn)
+        dd[free] = _lu_solve(J[free][:, free], -R[free])
+        if it == 0:
+            first = dd
+        d = d + dd
+    return d, first, opts.max_newton
+
+
+def at1_d_step(grid, m, u_k, d_k, d_prev, H_prev, scheme, opts):
+    """AT1 d-step.  ST: Newton with Psi+(u^k).  S1/S2/S3 (Sec. 3.3-3.5): the first NR
+    iteration with the augmented tangent gives Delta d; the active energy is predicted from
+    it where the softening test holds and frozen; the NR iterations continue with it."""
+    exx, eyy, exy = q1.strains_qp(grid, u_k)
+    psi = model.psi_plus(exx, eyy, exy, m)
+    if scheme == model.ST:
+        return at1_newton(grid, m, psi, d_k, d_prev, opts)[0]
+    a, kappa, gamma = model.at1_constants(m, opts.tol_ir)
+    tr, ee = model.invariants(exx, eyy, exy, m.cdim)
+    d_q = q1.interp_qp(grid, d_k)
+    pc = a if opts.psi_crit is None else opts.psi_crit
+    act = model.activation(psi, H_prev, d_q, m, pc) & grid.elem_active[:, None]
+    k_extra = np.where(act, model.extra_stiffness(tr, ee, d_q, scheme, m), 0.0)
+    cJ = model.at1_mass_coefficient(psi, d_q, q1.interp_qp(grid, d_prev), gamma)
+    c_aug = model.at1_augmented_coefficient(cJ, k_extra, m, opts.kt_floor)
+    opts1 = Options(tol_nr=opts.tol_nr, max_newton=1, model=opts.model, tol_ir=opts.tol_ir)
+    d_half, dd, _ = at1_newton(grid, m, psi, d_k, d_prev, opts1, c_first=c_aug)
+    dd_q = q1.interp_qp(grid, dd)
+    psi_hat = np.where(act, model.predict_psi(tr, ee, d_q, dd_q, scheme, m), psi)
+    return at1_newton(grid, m, psi_hat, d_k + dd, d_prev, opts)[0]
+
+
+def at1_stag_residual(grid, m, u, d, d_prev, opts):
+    """max_i |R_d,i / J_ii| over free d-DOFs with Psi+(u^{k+1}) and the penalty at d."""
+    psi = psi_plus_qp(grid, u, m)
+    R, cJ, kappa = at1_residual(grid, m, psi, d, d_prev, opts)
+    J = q1.assemble_damage(grid, cJ, kappa)
+    free = ~grid.d_constrained()
+    if not np.any(free):
+        return 0.0
+    return float(np.max(np.abs(R[free] / J.diagonal()[free])))
+
+
 def load_step(grid, m, state, dubar, scheme, opts, reaction_dir=1, trace=None):
     """Advance ``state`` by one load increment ``dubar`` with the given scheme.
 
@@ -188,7 +270,10 @@ def load_step(grid, m, state, dubar, scheme, opts, reaction_dir=1, trace=None):
     u, nn, ok = solve_u(grid, m, u, d, opts)
     res.newton_u += nn
     for k in range(opts.max_stag):
-        if scheme == model.ST:
+        if opts.model == model.AT1:
+            d = at1_d_step(grid, m, u, d, d_prev, H_prev, scheme, opts)
+            res.d_solves += 1 if scheme == model.ST else 2
+        elif scheme == model.ST:
             H_k = np.maximum(H_prev, psi_plus_qp(grid, u, m))
             d = d_step_standard(grid, m, H_k)
             res.d_solves += 1
@@ -199,7 +284,10 @@ def load_step(grid, m, state, dubar, scheme, opts, reaction_dir=1, trace=None):
             d = np.clip(d, d_prev, 1.0)
         u, nn, ok = solve_u(grid, m, u, d, opts)
         res.newton_u += nn
-        r = stag_residual(grid, m, u, d, H_prev)
+        if opts.model == model.AT1:
+            r = at1_stag_residual(grid, m, u, d, d_prev, opts)
+        else:
+            r = stag_residual(grid, m, u, d, H_prev)
         res.stag_iters = k + 1
         res.stag_residual = r
         if trace is not None:

@@ -1,0 +1,103 @@
+"""Pins of the checker's AT1 model with penalty irreversibility (Sec. 2, Table 1).
+
+AT1: g(d) = (1-d)^2 + eta, w(d) = d, c_w = 8/3; the evolution equation
+
+    -2 (1-d) Psi+ + G_c/(c_w l) + gamma <d - d_{n-1}>_- - (2 G_c l / c_w) lap d = 0,
+
+gamma = 27 G_c / (64 l tol_ir^2), is nonlinear through the penalty term and is solved by
+semismooth Newton.  Pinned against closed forms:
+- the homogeneous uniaxial-strain bar, where the strain is prescribed by the boundary and
+  d solves the scalar stationarity equation at every load step (also across unloading,
+  where the penalty keeps d_n >= d_{n-1} - (8/9) tol_ir^2);
+- the 1D profile (1 - x/(2l))^2 of a crack at x = 0 with no elastic energy (second-order
+  convergence with h);
+- S1/S2/S3 equal ST bit for bit when the softening test never holds.
+"""
+import numpy as np
+import pytest
+
+from oracle import model, q1, staggered as stg
+from paper_2209_07969_gb300 import specimens as S
+
+
+def _grid(sp):
+    return q1.Grid(sp.nx, sp.ny, sp.Lx, sp.Ly, sp.node_flags, sp.elem_active)
+
+
+def _mat(sp):
+    return model.material_from_E_nu(sp.E, sp.nu, sp.Gc, sp.l, sp.eta, sp.plane)
+
+
+def _scalar_d(psi, d_prev, a, gamma):
+    """Solution of -2(1-d) psi + a + gamma <d - d_prev>_- = 0 (homogeneous state)."""
+    d_free = 1.0 - a / (2.0 * psi) if psi > 0 else -np.inf
+    if d_free >= d_prev:
+        return d_free
+    return (2.0 * psi - a + gamma * d_prev) / (2.0 * psi + gamma)
+
+
+@pytest.mark.parametrize("scheme", [model.ST, model.S1, model.S3])
+def test_at1_homogeneous_bar(scheme):
+    lam, mu, Gc, l, eta = 121.15, 80.77, 2.7e-3, 0.03, 1e-9
+    M = lam + 2 * mu
+    tol_ir = 0.01
+    opts = stg.Options(tol_st=1e-10, tol_nr=1e-11, max_stag=300, model=model.AT1,
+                       tol_ir=tol_ir)
+    sp = S.uniaxial_bar(3, 4, Lx=0.5, Ly=1.0, lam=lam, mu=mu, Gc=Gc, l=l, eta=eta)
+    g, m = _grid(sp), _mat(sp)
+    a, kappa, gamma = model.at1_constants(m, tol_ir)
+    eps_c = np.sqrt(2 * a / M)                    # Psi+ reaches a / 2 = 3 G_c / (16 l)
+    # load past the elastic limit, unload, reload
+    ubars = np.concatenate([np.linspace(0.2, 2.0, 7), [1.5, 1.0], [1.8, 2.4]]) * eps_c * sp.Ly
+    st = stg.State(g)
+    d_ref = 0.0
+    for ub in ubars:
+        r = stg.load_step(g, m, st, ub - st.ubar, scheme, opts, reaction_dir=1)
+        assert r.converged
+        eps = st.ubar / sp.Ly
+        psi = 0.5 * M * eps ** 2
+        d_new = _scalar_d(psi, d_ref, a, gamma)
+        assert d_new >= d_ref - (8.0 / 9.0) * tol_ir ** 2 * (1 + 1e-12)
+        d_ref = d_new
+        assert np.allclose(st.d, d_ref, rtol=1e-8, atol=1e-11)
+        F = ((1 - d_ref) ** 2 + eta) * M * eps * sp.Lx
+        assert r.reaction == pytest.approx(F, rel=1e-8)
+    # the softening branch was reached (d well above the penalty's O(tol_ir^2) range)
+    assert d_ref > 0.3
+
+
+def test_at1_profile_second_order():
+    L, l = 1.0, 0.1
+    errs = []
+    for nx in (40, 80, 160):
+        sp = S.strip_1d(nx, ny=2, L=L, l=l)
+        g, m = _grid(sp), _mat(sp)
+        # a tight irreversibility tolerance makes the penalised solution the d >= 0 one;
+        # from the Dirichlet start the free boundary x = 2l advances a node per iteration
+        opts = stg.Options(tol_nr=1e-10, max_newton=400, model=model.AT1, tol_ir=1e-4)
+        d0 = g.d_dirichlet_values().astype(float)
+        d, _, it = stg.at1_newton(g, m, np.zeros((g.ne, 4)), d0, np.zeros(g.nn), opts)
+        assert it < opts.max_newton
+        s, _ = q1.gauss_points_unit()
+        ej, ei = np.divmod(np.arange(g.ne), g.nx)
+        xq = (ei[:, None] + s[None]) * g.hx
+        exact = np.where(xq < 2 * l, (1.0 - xq / (2 * l)) ** 2, 0.0)
+        err = q1.interp_qp(g, d) - exact
+        errs.append(np.sqrt(np.sum(err ** 2) * q1.qp_weight(g) / (g.Lx * g.Ly)))
+    errs = np.array(errs)
+    orders = np.log2(errs[:-1] / errs[1:])
+    assert errs[-1] < 1e-4
+    assert np.all(orders > 1.8), orders
+
+
+@pytest.mark.parametrize("scheme", [model.S1, model.S2, model.S3])
+def test_at1_fixed_stress_equals_standard_without_softening(scheme):
+    sp = S.tensile(12, l=0.2, steps=3, u_max=6e-3)
+    g, m = _grid(sp), _mat(sp)
+    out = []
+    for sch in (model.ST, scheme):
+        opts = stg.Options(tol_st=1e-8, model=model.AT1, psi_crit=np.inf)
+        res, st = stg.load_path(g, m, sp.increments, sch, opts, reaction_dir=1)
+        out.append(([r.reaction for r in res], [r.stag_iters for r in res], st.d))
+    (Fa, ka, da), (Fb, kb, db) = out
+    assert Fa == Fb and ka == kb and np.array_equal(da, db)
