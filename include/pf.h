@@ -79,7 +79,17 @@ typedef struct {
   int precision;               /* PF_FP64 or PF_FP32_IR */
   int reaction_dir;            /* 0: x, 1: y -- component summed over LOAD nodes */
   int precond;                 /* PF_PRECOND_JACOBI or PF_PRECOND_GMG */
+  int model;                   /* PF_AT2_HISTORY (0): AT2, w = d^2, c_w = 2, history field
+                                  H = max Psi+ drives the (linear) evolution equation;
+                                  PF_AT1_PENALTY (1): AT1, w = d, c_w = 8/3, current Psi+ and
+                                  the penalty gamma <d - d_{n-1}>_- (Sec. 2, Table 1),
+                                  semismooth Newton per d-solve */
+  double tol_ir;               /* AT1 irreversibility tolerance: gamma = 27 G_c / (64 l
+                                  tol_ir^2) (Sec. 2); <= 0 selects 0.01 */
 } pf_mesh;
+
+#define PF_AT2_HISTORY 0
+#define PF_AT1_PENALTY 1
 
 /* Solver controls.  pf_default_options fills the defaults given in brackets. */
 typedef struct {

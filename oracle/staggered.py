@@ -37,7 +37,8 @@ from . import model, q1
 
 class Options:
     def __init__(self, tol_nr=1e-7, tol_st=1e-6, max_newton=50, max_stag=1000,
-                 psi_crit=None, project=False, kt_floor=True, model=0, tol_ir=0.01):
+                 psi_crit=None, project=False, kt_floor=True, model=0, tol_ir=0.01,
+                 tol_d=1e-10):
         self.tol_nr = tol_nr          # TOL_NR (Sec. 4 intro: 1e-7)
         self.tol_st = tol_st          # TOL_ST (Sec. 4 intro: 1e-6)
         self.max_newton = max_newton
@@ -47,6 +48,8 @@ class Options:
         self.kt_floor = kt_floor      # augmented coefficient >= G_c/l (model.augmented_coefficient)
         self.model = model            # model.AT2 (history field) or model.AT1 (penalty)
         self.tol_ir = tol_ir          # AT1 irreversibility tolerance (Sec. 2: 0.01)
+        self.tol_d = tol_d            # AT1 d-Newton stop (relative; the equation is piecewise
+                                      # linear, so Newton is exact once the penalty set settles)
 
 
 class State:
@@ -190,8 +193,11 @@ def at1_newton(grid, m, psi, d, d_prev, opts, c_first=None):
     """Semismooth Newton for the AT1 evolution equation at fixed energy ``psi``.
 
     c_first: per-point mass coefficient of the first iteration's matrix (the fixed-stress
-    augmented tangent), None for the exact Jacobian.  Stop: ||R_free|| <= TOL_NR *
-    max(||R^0_free||, ||int a N||).  Returns (d, first increment, iterations).
+    augmented tangent), None for the exact Jacobian.  Stop: ||R_free|| <= tol_d *
+    max(||R^0_free||, ||int a N||).  The equation is piecewise linear (the penalty), so once
+    the penalised set stops changing the next iterate is exact; tol_d (1e-10) is therefore
+    tighter than TOL_NR, which would leave a d-residual above the staggered test's
+    tolerance.  Returns (d, first increment, iterations).
     """
     a, kappa, _ = model.at1_constants(m, opts.tol_ir)
     cd = grid.d_constrained()
@@ -205,7 +211,7 @@ def at1_newton(grid, m, psi, d, d_prev, opts, c_first=None):
         rn = np.linalg.norm(R[free])
         if r0 is None:
             r0 = rn
-        if rn == 0.0 or rn <= opts.tol_nr * max(r0, fscale):
+        if rn == 0.0 or rn <= opts.tol_d * max(r0, fscale):
             return d, first, it
         if it == opts.max_newton:
             break
@@ -235,7 +241,8 @@ def at1_d_step(grid, m, u_k, d_k, d_prev, H_prev, scheme, opts):
     k_extra = np.where(act, model.extra_stiffness(tr, ee, d_q, scheme, m), 0.0)
     cJ = model.at1_mass_coefficient(psi, d_q, q1.interp_qp(grid, d_prev), gamma)
     c_aug = model.at1_augmented_coefficient(cJ, k_extra, m, opts.kt_floor)
-    opts1 = Options(tol_nr=opts.tol_nr, max_newton=1, model=opts.model, tol_ir=opts.tol_ir)
+    opts1 = Options(tol_nr=opts.tol_nr, max_newton=1, model=opts.model, tol_ir=opts.tol_ir,
+                    tol_d=opts.tol_d)
     d_half, dd, _ = at1_newton(grid, m, psi, d_k, d_prev, opts1, c_first=c_aug)
     dd_q = q1.interp_qp(grid, dd)
     psi_hat = np.where(act, model.predict_psi(tr, ee, d_q, dd_q, scheme, m), psi)

@@ -16,6 +16,7 @@ ST, S1, S2, S3 = 0, 1, 2, 3
 SCHEMES = {"ST": ST, "standard": ST, "S1": S1, "S2": S2, "S3": S3}
 FP64, FP32_IR = 0, 1
 PRECOND_JACOBI, PRECOND_GMG = 0, 1
+AT2_HISTORY, AT1_PENALTY = 0, 1
 F64, F32 = 0, 1
 
 
@@ -32,7 +33,8 @@ class PfError(RuntimeError):
 class Mesh(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("Lx", C.c_double), ("Ly", C.c_double),
                 ("elem_active", C.c_void_p), ("node_flags", C.c_void_p), ("plane", C.c_int),
-                ("precision", C.c_int), ("reaction_dir", C.c_int), ("precond", C.c_int)]
+                ("precision", C.c_int), ("reaction_dir", C.c_int), ("precond", C.c_int),
+                ("model", C.c_int), ("tol_ir", C.c_double)]
 
 
 class Options(C.Structure):
@@ -145,18 +147,19 @@ def grid(nx, ny, hx, hy, elem_active_ptr=None, dof_mask_ptr=None):
     return Grid(nx, ny, hx, hy, elem_active_ptr, dof_mask_ptr)
 
 
-def footprint_bytes(spec, precision=FP64, precond=PRECOND_JACOBI):
+def footprint_bytes(spec, precision=FP64, precond=PRECOND_JACOBI, model=AT2_HISTORY):
     """Device bytes pf_create would allocate for the specimen (admission control)."""
     active = None if spec.elem_active is None or np.all(spec.elem_active) else 1
     mesh = Mesh(spec.nx, spec.ny, spec.Lx, spec.Ly, active, 1, spec.plane, precision,
-                spec.reaction_dir, precond)
+                spec.reaction_dir, precond, model, 0.0)
     return int(lib().pf_footprint_bytes(C.byref(mesh)))
 
 
 class Simulation:
     """One fracture simulation resident on the current CUDA device (pf_create)."""
 
-    def __init__(self, spec, precision=FP64, precond=PRECOND_JACOBI, options=None):
+    def __init__(self, spec, precision=FP64, precond=PRECOND_JACOBI, options=None,
+                 model=AT2_HISTORY, tol_ir=0.01):
         self.spec = spec
         self._flags = np.ascontiguousarray(spec.node_flags, dtype=np.uint8)
         self._active = None
@@ -164,7 +167,8 @@ class Simulation:
             self._active = np.ascontiguousarray(spec.elem_active, dtype=np.uint8)
         mesh = Mesh(spec.nx, spec.ny, spec.Lx, spec.Ly,
                     self._active.ctypes.data if self._active is not None else None,
-                    self._flags.ctypes.data, spec.plane, precision, spec.reaction_dir, precond)
+                    self._flags.ctypes.data, spec.plane, precision, spec.reaction_dir, precond,
+                    model, tol_ir)
         ctx = P()
         check(lib().pf_create(C.byref(mesh), spec.E, spec.nu, spec.Gc, spec.l, spec.eta,
                               C.byref(ctx)), "pf_create")

@@ -162,12 +162,22 @@ void damage_diag(const GridD &g, const T *c, double kappa, T *diag, cudaStream_t
 void damage_rhs(const GridD &g, const double *H, double *b, cudaStream_t st);
 void qp_energy(const GridD &g, const MatD &m, const double *u, const double *Hprev,
                double *psi, double *Hout, cudaStream_t st);
+// AT1 mode of the fixed-stress kernels (on = 0: AT2 with history).
+struct At1D {
+  int on = 0;
+  const double *dprev = nullptr;  // d_{n-1} (nodal) for the penalty indicator
+  double gamma = 0.0;             // penalty parameter
+  double floor = 0.0;             // lower limit of the augmented coefficient, 2 G_c/(c_w l)
+};
 void fs_coeff(const GridD &g, const MatD &m, int scheme, double psi_crit, const double *u,
               const double *d, const double *Hprev, double *c_aug, uint8_t *active,
-              cudaStream_t st);
+              cudaStream_t st, const At1D &at1 = At1D());
 void fs_predict(const GridD &g, const MatD &m, int scheme, const double *u, const double *d,
                 const double *dd, const double *Hprev, const uint8_t *active, double *Hhalf,
-                cudaStream_t st);
+                cudaStream_t st, int at1 = 0);
+// AT1 per-point arrays c0 = 2 psi, cJ, bhalf (pf_ops.cu, k_at1_coef).
+void at1_coef(const GridD &g, const double *psi, const double *d, const double *dprev, double a,
+              double gamma, double *c0, double *cJ, double *bhalf, cudaStream_t st);
 void dof_mask(int nx, int ny, const uint8_t *flags, const uint8_t *active, uint8_t *mask,
               cudaStream_t st);
 

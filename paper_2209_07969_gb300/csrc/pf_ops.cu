@@ -652,39 +652,70 @@ __device__ __forceinline__ double scheme_Q(const MatD &m, int scheme, double tr,
   return scheme == PF_S1 ? vol : scheme == PF_S2 ? dev : scheme == PF_S3 ? vol + dev : 0.0;
 }
 
+// AT1 with penalty (Sec. 2): per-point arrays of the evolution equation at energy psi,
+//   R_d = K(c0) d - b,  c0 = 2 psi,  b = int (2 psi - a - gamma <d - d_{n-1}>_-) N,
+//   Jacobian mass coefficient cJ = 2 psi + gamma [d < d_{n-1}]  (d at the point, strict),
+// with bhalf = b's integrand / 2 (damage_rhs integrates 2 (.) N).
+__global__ void k_at1_coef(GridD g, const double *__restrict__ psi, const double *__restrict__ d,
+                           const double *__restrict__ dprev, double a, double gamma,
+                           double *__restrict__ c0, double *__restrict__ cJ,
+                           double *__restrict__ bhalf) {
+  const size_t ne = (size_t)g.nx * g.ny;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ne;
+       e += (size_t)gridDim.x * blockDim.x) {
+    size_t n[4];
+    element_nodes(g, e, n);
+    double dq[4], dpq[4];
+    element_interp(d, n, dq);
+    element_interp(dprev, n, dpq);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double ps = __ldg(psi + 4 * e + q);
+      const double diff = dq[q] - dpq[q];
+      c0[4 * e + q] = 2.0 * ps;
+      cJ[4 * e + q] = 2.0 * ps + (diff < 0.0 ? gamma : 0.0);
+      bhalf[4 * e + q] = 0.5 * (2.0 * ps - a - gamma * (diff < 0.0 ? diff : 0.0));
+    }
+  }
+}
+
 __global__ void k_fs_coeff(GridD g, MatD m, int scheme, double psi_crit,
                            const double *__restrict__ u, const double *__restrict__ d,
                            const double *__restrict__ Hprev, double *__restrict__ c_aug,
-                           uint8_t *__restrict__ active) {
+                           uint8_t *__restrict__ active, At1D at1) {
   const size_t ne = (size_t)g.nx * g.ny;
-  const double floor_c = m.Gc / m.l;
+  const double floor_c = at1.on ? at1.floor : m.Gc / m.l;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ne;
        e += (size_t)gridDim.x * blockDim.x) {
     const bool live = !g.active || g.active[e];
     size_t n[4];
     element_nodes(g, e, n);
     QpStrain S;
-    double dq[4];
+    double dq[4], dpq[4];
     if (live) {
       element_strains(g, u, n, S);
       element_interp(d, n, dq);
+      if (at1.on) element_interp(at1.dprev, n, dpq);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const double hp = __ldg(Hprev + 4 * e + q);
-      double c = floor_c + 2.0 * hp;
+      double c = at1.on ? 0.0 : floor_c + 2.0 * hp;
       uint8_t a = 0;
       if (live) {
         double tr, ee;
         invariants(m, S.exx[q], S.eyy[q], S.exy[q], tr, ee);
         const double ps = psi_plus(m, tr, ee);
-        const double H = fmax(hp, ps);
-        c = floor_c + 2.0 * H;
+        // Jacobian mass coefficient: AT2 G_c/l + 2H; AT1 2 Psi+ (+ gamma where penalised)
+        const double cJ = at1.on ? 2.0 * ps + (dq[q] < dpq[q] ? at1.gamma : 0.0)
+                                 : floor_c + 2.0 * fmax(hp, ps);
+        c = cJ;
         a = (ps > psi_crit) && (ps > hp) && (dq[q] < 0.95);
         if (a) {
           const double om = 1.0 - dq[q];
           const double gq = om * om + m.eta;
-          c = fmax(c - 4.0 * om * om / gq * scheme_Q(m, scheme, tr, ee), floor_c);
+          const double lim = at1.on ? fmin(cJ, floor_c) : floor_c;
+          c = fmax(cJ - 4.0 * om * om / gq * scheme_Q(m, scheme, tr, ee), lim);
         }
       }
       c_aug[4 * e + q] = c;
@@ -696,7 +727,8 @@ __global__ void k_fs_coeff(GridD g, MatD m, int scheme, double psi_crit,
 __global__ void k_fs_predict(GridD g, MatD m, int scheme, const double *__restrict__ u,
                              const double *__restrict__ d, const double *__restrict__ dd,
                              const double *__restrict__ Hprev,
-                             const uint8_t *__restrict__ active, double *__restrict__ Hhalf) {
+                             const uint8_t *__restrict__ active, double *__restrict__ Hhalf,
+                             int at1) {
   const size_t ne = (size_t)g.nx * g.ny;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ne;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -728,7 +760,7 @@ __global__ void k_fs_predict(GridD g, MatD m, int scheme, const double *__restri
           const double een = (scheme == PF_S2 || scheme == PF_S3) ? sc * sc * ee : ee;
           ps = m.mu * een + 0.5 * m.K * tpn * tpn;
         }
-        h = fmax(hp, ps);
+        h = at1 ? ps : fmax(hp, ps);   // AT1 drives d with the (predicted) energy itself
       }
       Hhalf[4 * e + q] = h;
     }
@@ -938,15 +970,22 @@ void qp_energy(const GridD &g, const MatD &m, const double *u, const double *Hpr
 }
 void fs_coeff(const GridD &g, const MatD &m, int scheme, double psi_crit, const double *u,
               const double *d, const double *Hprev, double *c_aug, uint8_t *active,
-              cudaStream_t st) {
+              cudaStream_t st, const At1D &at1) {
   k_fs_coeff<<<elem_blocks((size_t)g.nx * g.ny), VEC_THREADS, 0, st>>>(g, m, scheme, psi_crit, u,
-                                                                       d, Hprev, c_aug, active);
+                                                                        d, Hprev, c_aug, active,
+                                                                        at1);
 }
 void fs_predict(const GridD &g, const MatD &m, int scheme, const double *u, const double *d,
                 const double *dd, const double *Hprev, const uint8_t *active, double *Hhalf,
-                cudaStream_t st) {
+                cudaStream_t st, int at1) {
   k_fs_predict<<<elem_blocks((size_t)g.nx * g.ny), VEC_THREADS, 0, st>>>(g, m, scheme, u, d, dd,
-                                                                         Hprev, active, Hhalf);
+                                                                          Hprev, active, Hhalf,
+                                                                          at1);
+}
+void at1_coef(const GridD &g, const double *psi, const double *d, const double *dprev, double a,
+              double gamma, double *c0, double *cJ, double *bhalf, cudaStream_t st) {
+  k_at1_coef<<<elem_blocks((size_t)g.nx * g.ny), VEC_THREADS, 0, st>>>(g, psi, d, dprev, a, gamma,
+                                                                        c0, cJ, bhalf);
 }
 void dof_mask(int nx, int ny, const uint8_t *flags, const uint8_t *active, uint8_t *mask,
               cudaStream_t st) {

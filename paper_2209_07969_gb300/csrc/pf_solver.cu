@@ -64,6 +64,11 @@ struct pf_ctx {
   MatD m{};
   size_t nn = 0, ne = 0, nq = 0;
   int precision = PF_FP64, reaction_dir = 1, precond = PF_PRECOND_JACOBI, plane = 0;
+  int model = PF_AT2_HISTORY;
+  // AT1 (Sec. 2): a = G_c/(c_w l), kappa = 2 G_c l / c_w, gamma = 27 G_c/(64 l tol_ir^2),
+  // floor = 2 G_c/(c_w l) (lower limit of the augmented coefficient)
+  double at1_a = 0.0, at1_kappa = 0.0, at1_gamma = 0.0, at1_floor = 0.0;
+  double *bhalf = nullptr;   // AT1 right-hand-side integrand / 2 (per Gauss point)
   pf_options opt{};
   double ubar = 0.0;
   int64_t step = 0;
@@ -714,7 +719,126 @@ pf_status d_solve_from(pf_ctx *ctx, const double *c, const double *Hdrive, int *
   return PF_OK;
 }
 
+// ---- AT1 with penalty (Sec. 2) -------------------------------------------------------
+// Evolution equation at per-point energy psi: R_d = K(c0) d - b (k_at1_coef writes c0 to
+// Hhalf, the Jacobian coefficient cJ to cq and b's integrand / 2 to bhalf).  at1_rhs puts
+// -R (free DOFs) into bd and returns ||R_free||.
+pf_status at1_rhs(pf_ctx *ctx, const double *psi, double *rnorm) {
+  cudaStream_t st = ctx->st;
+  const size_t n = ctx->nn;
+  at1_coef(ctx->g, psi, ctx->d, ctx->d_prev, ctx->at1_a, ctx->at1_gamma, ctx->Hhalf, ctx->cq,
+           ctx->bhalf, st);
+  damage_rhs(ctx->g, ctx->bhalf, ctx->bd, st);
+  damage_apply<double>(grid_nomask(ctx), ctx->Hhalf, ctx->at1_kappa, ctx->d, ctx->Kd, st);
+  masked_comb(n, 1, ctx->g.dofm, 1.0, ctx->bd, 1.0, ctx->Kd, ctx->bd, st);
+  norms(n, 1, ctx->g.dofm, ctx->bd, ctx->dscal, ctx->ws, st);
+  ctx->launches += 5;
+  CKS(check_launch(ctx));
+  CKS(read_scalars(ctx, ctx->dscal, sizeof(double)));
+  *rnorm = sqrt(ctx->hbuf[0]);
+  return PF_OK;
+}
+
+// ||int a N||_free: the scale of the Newton test of the AT1 evolution equation.
+pf_status at1_scale(pf_ctx *ctx, double *fscale) {
+  cudaStream_t st = ctx->st;
+  fill(ctx->nq, 0.5 * ctx->at1_a, ctx->bhalf, st);
+  damage_rhs(ctx->g, ctx->bhalf, ctx->bd, st);
+  norms(ctx->nn, 1, ctx->g.dofm, ctx->bd, ctx->dscal, ctx->ws, st);
+  ctx->launches += 3;
+  CKS(check_launch(ctx));
+  CKS(read_scalars(ctx, ctx->dscal, sizeof(double)));
+  *fscale = sqrt(ctx->hbuf[0]);
+  return PF_OK;
+}
+
+// Semismooth Newton for the AT1 evolution equation at per-point energy psi: solve
+// K(cJ) dd = -R on the free DOFs, d += dd, until ||R_free|| <= tol_lin max(||R^0_free||,
+// ||int a N||_free).  The equation is piecewise linear (the penalty), so the iterate after
+// the penalised set settles is exact to the linear tolerance; stopping at tol_nr instead
+// would leave a d-residual above the staggered test's tolerance.
+pf_status at1_newton(pf_ctx *ctx, const double *psi, double fscale, int *lin, int *refines,
+                     int *dsolves, bool *ok) {
+  double r0 = -1.0;
+  *ok = false;
+  for (int it = 0; it <= ctx->opt.max_newton; ++it) {
+    double rn;
+    CKS(at1_rhs(ctx, psi, &rn));
+    if (r0 < 0.0) r0 = rn;
+    if (rn == 0.0 || rn <= ctx->opt.tol_lin * fmax(r0, fscale)) {
+      *ok = true;
+      return PF_OK;
+    }
+    if (!isfinite(rn)) return set_err(ctx, PF_ENOTCONV, "d residual is not finite");
+    if (it == ctx->opt.max_newton) break;
+    bool lok = false;
+    CKS(solve_damage(ctx, ctx->cq, ctx->bd, ctx->dd, lin, refines, &lok));
+    (*dsolves)++;
+    add(ctx->nn, ctx->dd, ctx->d, ctx->st);
+    ctx->launches++;
+    if (!lok) return set_err(ctx, PF_ENOTCONV, "d linear solve did not converge");
+  }
+  return PF_OK;
+}
+
+// AT1 d-step.  ST: Newton with Psi+(u^k) (Hk).  S1/S2/S3 (Sec. 3.3-3.5): the first NR
+// iteration with the augmented tangent gives Delta d (dd), the active energy is predicted
+// from it where the softening test holds and frozen (Hk), and the NR iterations continue
+// from d^k + Delta d with it.
+pf_status at1_d_step(pf_ctx *ctx, int scheme, int *lin, int *refines, int *dsolves, bool *ok) {
+  cudaStream_t st = ctx->st;
+  // current energy into Hk (csolve takes the unused history output)
+  qp_energy(ctx->g, ctx->m, ctx->u, ctx->H, ctx->Hk, ctx->csolve, st);
+  ctx->launches++;
+  double fscale;
+  CKS(at1_scale(ctx, &fscale));
+  if (scheme == PF_ST) return at1_newton(ctx, ctx->Hk, fscale, lin, refines, dsolves, ok);
+  const double pc = ctx->opt.psi_crit < 0.0 ? ctx->at1_a : ctx->opt.psi_crit;
+  At1D at1;
+  at1.on = 1;
+  at1.dprev = ctx->d_prev;
+  at1.gamma = ctx->at1_gamma;
+  at1.floor = ctx->at1_floor;
+  // augmented coefficient into csolve (solve_damage uses it in place)
+  fs_coeff(ctx->g, ctx->m, scheme, pc, ctx->u, ctx->d, ctx->H, ctx->csolve, ctx->act, st, at1);
+  ctx->launches++;
+  double rn;
+  CKS(at1_rhs(ctx, ctx->Hk, &rn));
+  if (rn == 0.0 || rn <= ctx->opt.tol_lin * fscale) {
+    *ok = true;   // already at the solution of the evolution equation
+    return PF_OK;
+  }
+  bool ok1 = false;
+  CKS(solve_damage(ctx, ctx->csolve, ctx->bd, ctx->dd, lin, refines, &ok1));
+  (*dsolves)++;
+  fs_predict(ctx->g, ctx->m, scheme, ctx->u, ctx->d, ctx->dd, ctx->H, ctx->act, ctx->Hk, st, 1);
+  add(ctx->nn, ctx->dd, ctx->d, st);
+  ctx->launches += 2;
+  CKS(at1_newton(ctx, ctx->Hk, fscale, lin, refines, dsolves, ok));
+  *ok = *ok && ok1;
+  return PF_OK;
+}
+
+// AT1 staggered residual: max |R_d,i / J_ii| over free d-DOFs with Psi+(u^{k+1}) and the
+// penalty at d^{k+1}.
+pf_status at1_stag_residual(pf_ctx *ctx, double *out) {
+  cudaStream_t st = ctx->st;
+  qp_energy(ctx->g, ctx->m, ctx->u, ctx->H, ctx->Hk, ctx->csolve, st);
+  at1_coef(ctx->g, ctx->Hk, ctx->d, ctx->d_prev, ctx->at1_a, ctx->at1_gamma, ctx->Hhalf, ctx->cq,
+           ctx->bhalf, st);
+  damage_rhs(ctx->g, ctx->bhalf, ctx->bd, st);
+  damage_apply<double>(grid_nomask(ctx), ctx->Hhalf, ctx->at1_kappa, ctx->d, ctx->Kd, st);
+  damage_diag<double>(grid_nomask(ctx), ctx->cq, ctx->at1_kappa, ctx->kz, st);
+  stag_max(ctx->nn, ctx->g.dofm, ctx->Kd, ctx->bd, ctx->kz, ctx->dscal, ctx->ws, st);
+  ctx->launches += 6;
+  CKS(check_launch(ctx));
+  CKS(read_scalars(ctx, ctx->dscal, sizeof(double)));
+  *out = ctx->hbuf[0];
+  return PF_OK;
+}
+
 pf_status d_step(pf_ctx *ctx, int scheme, int *lin, int *refines, int *dsolves, bool *ok) {
+  if (ctx->model == PF_AT1_PENALTY) return at1_d_step(ctx, scheme, lin, refines, dsolves, ok);
   cudaStream_t st = ctx->st;
   const double gcl = ctx->m.Gc / ctx->m.l;
   const double kappa = ctx->m.Gc * ctx->m.l;
@@ -752,6 +876,7 @@ pf_status d_step(pf_ctx *ctx, int scheme, int *lin, int *refines, int *dsolves, 
 
 pf_status stag_residual(pf_ctx *ctx, double *out) {
   PhaseTimer tm(&ctx->prof[PF_PROF_STAG]);
+  if (ctx->model == PF_AT1_PENALTY) return at1_stag_residual(ctx, out);
   cudaStream_t st = ctx->st;
   const double gcl = ctx->m.Gc / ctx->m.l;
   const double kappa = ctx->m.Gc * ctx->m.l;
@@ -782,7 +907,7 @@ void free_all(pf_ctx *c) {
                   c->bd, c->Kd, c->dd, c->flags,  c->active, c->dofm, c->tens, c->kb, c->kx,
                   c->kr, c->kz, c->kp, c->kq, c->kinv, c->kres, c->fb, c->fx, c->fr, c->fz,
                   c->fp, c->fq, c->finv, c->fd, c->fc, c->sc, c->ws.partials, c->ws.counter,
-                  c->dscal, c->csolve};
+                  c->dscal, c->csolve, c->bhalf};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   gmg_free<double>(c->gu);
@@ -863,7 +988,9 @@ pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double 
   if (!mesh || !mesh->node_flags || mesh->nx < 1 || mesh->ny < 1 || !(mesh->Lx > 0) ||
       !(mesh->Ly > 0) || (mesh->precision != PF_FP64 && mesh->precision != PF_FP32_IR) ||
       (mesh->reaction_dir != 0 && mesh->reaction_dir != 1) ||
-      (mesh->precond != PF_PRECOND_JACOBI && mesh->precond != PF_PRECOND_GMG))
+      (mesh->precond != PF_PRECOND_JACOBI && mesh->precond != PF_PRECOND_GMG) ||
+      (mesh->model != PF_AT2_HISTORY && mesh->model != PF_AT1_PENALTY) ||
+      !(mesh->tol_ir == mesh->tol_ir))
     return PF_EINVAL;
   if ((double)(mesh->nx + 1) * (double)(mesh->ny + 1) > 4.0e8) return PF_EINVAL;
   pf_material mat;
@@ -880,6 +1007,14 @@ pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double 
   ctx->precond = mesh->precond;
   ctx->plane = mesh->plane;
   ctx->m = MatD{mat.mu, mat.K, mat.cdim, mat.eta, mat.Gc, mat.l};
+  ctx->model = mesh->model;
+  if (ctx->model == PF_AT1_PENALTY) {
+    const double cw = 8.0 / 3.0, tir = mesh->tol_ir > 0.0 ? mesh->tol_ir : 0.01;
+    ctx->at1_a = Gc / (cw * l);
+    ctx->at1_kappa = 2.0 * Gc * l / cw;
+    ctx->at1_gamma = 27.0 * Gc / (64.0 * l * tir * tir);
+    ctx->at1_floor = 2.0 * Gc / (cw * l);
+  }
   pf_status s = PF_OK;
   auto fail = [&](pf_status st) {
     free_all(ctx);
@@ -898,6 +1033,7 @@ pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double 
   AL(u, 2 * nn); AL(d, nn); AL(H, nq); AL(d_prev, nn); AL(F, 2 * nn);
   AL(Hk, nq); AL(cq, nq); AL(Hhalf, nq); AL(act, nq);
   AL(bd, nn); AL(Kd, nn); AL(dd, nn); AL(csolve, nq);
+  if (ctx->model == PF_AT1_PENALTY) AL(bhalf, nq);
   AL(flags, nn); AL(dofm, nn); AL(tens, ne);
   if (mesh->elem_active) AL(active, ne);
   AL(kb, 2 * nn); AL(kx, 2 * nn); AL(kr, 2 * nn); AL(kz, 2 * nn); AL(kp, 2 * nn);
@@ -984,6 +1120,7 @@ size_t pf_footprint_bytes(const pf_mesh *mesh) {
              + 2 * nn + ne * (mesh->elem_active ? 2 : 1)  // flags, dofm, tens, active
              + 8 * 2 * nn * D;                          // Krylov work (FP64)
   if (mesh->precision == PF_FP32_IR) b += 7 * 2 * nn * F + nn * F + nq * F;
+  if (mesh->model == PF_AT1_PENALTY) b += nq * D;          // bhalf
   const size_t tiles = (size_t)tile_blocks_x(mesh->nx) * tile_blocks_y(mesh->ny);
   const size_t mb = tiles > 4096 ? tiles : 4096;
   b += 4 * mb * D + red_counters((int)mb) * sizeof(unsigned) + sizeof(KrylovScal) + 8 * D;

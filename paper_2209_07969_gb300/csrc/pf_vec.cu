@@ -187,6 +187,12 @@ __global__ void k_masked_comb(size_t n, int ncomp, const uint8_t *__restrict__ d
   }
 }
 
+__global__ void k_fill(size_t n, double v, double *__restrict__ y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    y[i] = v;
+}
+
 // y += x
 __global__ void k_add(size_t n, const double *__restrict__ x, double *__restrict__ y) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
@@ -344,6 +350,9 @@ void pcg_rz(size_t n, const T *r, const T *z, T *p, int first, KrylovScal *sc, c
 template <class T>
 void invert(size_t n, const T *diag, T *inv, cudaStream_t st) {
   k_invert<T><<<vblocks(n, 1 << 16), VEC_THREADS, 0, st>>>(n, diag, inv);
+}
+void fill(size_t n, double v, double *y, cudaStream_t st) {
+  k_fill<<<vblocks(n, 1 << 16), VEC_THREADS, 0, st>>>(n, v, y);
 }
 void krylov_while(cudaGraphConditionalHandle h, KrylovScal *sc, cudaStream_t st) {
   k_krylov_while<<<1, 1, 0, st>>>(h, sc);

@@ -21,6 +21,7 @@ void pcg_update(size_t n, T *x, T *r, const T *p, const T *q, KrylovScal *sc, co
 template <class T>
 void pcg_rz(size_t n, const T *r, const T *z, T *p, int first, KrylovScal *sc, const RedWs &ws,
             cudaStream_t st);
+void fill(size_t n, double v, double *y, cudaStream_t st);
 // Condition kernel ending each pass of a device-side Krylov loop (k_krylov_while).
 void krylov_while(cudaGraphConditionalHandle h, KrylovScal *sc, cudaStream_t st);
 void masked_comb(size_t n, int ncomp, const uint8_t *dofm, double s, const double *a, double t,

@@ -74,7 +74,7 @@ def test_at1_profile_second_order():
         g, m = _grid(sp), _mat(sp)
         # a tight irreversibility tolerance makes the penalised solution the d >= 0 one;
         # from the Dirichlet start the free boundary x = 2l advances a node per iteration
-        opts = stg.Options(tol_nr=1e-10, max_newton=400, model=model.AT1, tol_ir=1e-4)
+        opts = stg.Options(tol_d=1e-10, max_newton=400, model=model.AT1, tol_ir=1e-4)
         d0 = g.d_dirichlet_values().astype(float)
         d, _, it = stg.at1_newton(g, m, np.zeros((g.ne, 4)), d0, np.zeros(g.nn), opts)
         assert it < opts.max_newton
