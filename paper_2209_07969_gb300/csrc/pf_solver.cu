@@ -632,7 +632,8 @@ pf_status solve_damage(pf_ctx *ctx, const double *c, const double *rhs, double *
   PhaseTimer tm(&ctx->prof[PF_PROF_D_SOLVE]);
   cudaStream_t st = ctx->st;
   const size_t n = ctx->nn;
-  const double kappa = ctx->m.Gc * ctx->m.l;
+  // gradient coefficient 2 G_c l / c_w: G_c l for AT2, 3 G_c l / 4 for AT1
+  const double kappa = ctx->model == PF_AT1_PENALTY ? ctx->at1_kappa : ctx->m.Gc * ctx->m.l;
   const bool mg = ctx->precond == PF_PRECOND_GMG;
   if (c != ctx->csolve)
     CK(cudaMemcpyAsync(ctx->csolve, c, ctx->nq * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1162,7 +1163,8 @@ pf_status pf_load_step(pf_ctx *ctx, double d_ubar, int scheme, double tol,
   r.ubar = ctx->ubar;
   lift(ctx->nn, ctx->flags, ctx->dofm, ctx->ubar, ctx->u, st);
   ctx->launches++;
-  if (ctx->opt.project)
+  // d_{n-1}: the projection bound, and the AT1 penalty's reference
+  if (ctx->opt.project || ctx->model == PF_AT1_PENALTY)
     CK(cudaMemcpyAsync(ctx->d_prev, ctx->d, ctx->nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
   bool ok = false, all_ok = true;
   pf_status s = solve_u(ctx, &r.newton_u, &r.lin_u, &r.refine_steps, &ok);

@@ -37,7 +37,7 @@ def test_at1_bar_closed_form(gpu, scheme, precision, precond):
     m = model.material_from_E_nu(sp.E, sp.nu, sp.Gc, sp.l, sp.eta, sp.plane)
     a, kappa, gamma = model.at1_constants(m, TOL_IR)
     eps_c = np.sqrt(2 * a / M)
-    ubars = np.concatenate([np.linspace(0.2, 2.0, 7), [1.5, 1.0], [1.8, 2.4]]) * eps_c * sp.Ly
+    ubars = np.concatenate([np.linspace(0.2, 2.0, 7), [1.5, 1.0, 1.8]]) * eps_c * sp.Ly
     sim = binding.Simulation(sp, precision=precision, precond=precond,
                              model=binding.AT1_PENALTY, tol_ir=TOL_IR)
     sim.set_options(tol_lin=1e-12, max_stag=300)
@@ -54,6 +54,10 @@ def test_at1_bar_closed_form(gpu, scheme, precision, precond):
         assert r["reaction"] == pytest.approx(F, rel=1e-7)
     assert d_ref > 0.3
     sim.close()
+    # (reloading past the previous maximum re-enters the softening branch, where the
+    # homogeneous state is unstable under displacement control: a rounding difference can
+    # seed a localized solution of the same discrete equations -- a damaging band with the
+    # rest unloading elastically -- so the closed form stops below the maximum)
 
 
 def _mirror_nodes(g, f):
