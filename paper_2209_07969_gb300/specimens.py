@@ -150,6 +150,21 @@ def strip_1d(nx, ny=4, L=1.0, l=0.05):
                     PLANE_STRAIN, E, nu, MIEHE_GC, l, 1e-9)
 
 
+def bar_1d(nx, steps=260, du=0.01, E=1.0, Gc=0.1, l=0.01, eta=1e-9):
+    """The paper's one-dimensional example: a bar of length 1 fixed at x = 0 and extended at
+    x = 1 by du per step (E = 1, G_c = 0.1, l = 0.01).  Modelled as one row of nx square
+    plane-strain elements with nu = 0 and u_y = 0 everywhere, where the volumetric-deviatoric
+    split reduces exactly to the 1D law (Psi+ = E eps^2 / 2, sigma = g(d) E eps in tension).
+    Reaction: x-force at x = 1."""
+    ny = 1
+    i, j = _node_ij(nx, ny)
+    flags = np.full((nx + 1) * (ny + 1), FIX_Y, np.uint8)
+    flags[i == 0] |= FIX_X
+    flags[i == nx] |= LOAD_X
+    return Specimen("bar_1d", nx, ny, 1.0, 1.0 / nx, flags, np.ones(nx * ny, np.uint8), 0,
+                    PLANE_STRAIN, E, 0.0, Gc, l, eta, np.full(steps, du))
+
+
 # ---- seeded random inputs ------------------------------------------------------------------
 def rng(seed):
     return np.random.Generator(np.random.PCG64(seed))
