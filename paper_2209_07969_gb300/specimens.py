@@ -56,6 +56,38 @@ class Specimen:
         return self.nx * self.ny
 
 
+# Two-rate loading schedules of the paper's benchmarks: the load point moves at a constant
+# rate, in steps of dt1 up to time t1 and of dt2 from there up to t2 (Sec. 4.1 tensile,
+# Sec. 4.2 shear, Sec. 4.3 L-shape; rate in mm/s, times in s).
+PAPER_SCHEDULES = {
+    "tensile": dict(rate=3e-5, dt1=170.0, t1=170.0, dt2=1.0, t2=220.0),
+    "shear": dict(rate=3e-5, dt1=250.0, t1=250.0, dt2=1.0, t2=380.0),
+    "l_shape": dict(rate=1e-3, dt1=0.01, t1=0.2, dt2=0.001, t2=0.6),
+}
+
+
+def two_rate_schedule(rate, dt1, t1, dt2, t2):
+    """(times, increments) of a two-rate schedule: t_n after each step and the prescribed
+    displacement increment rate * dt_n of each step."""
+    n1 = int(round(t1 / dt1))
+    n2 = int(round((t2 - t1) / dt2))
+    dt = np.concatenate([np.full(n1, dt1), np.full(n2, dt2)])
+    return np.cumsum(dt), rate * dt
+
+
+def paper_schedule(kind):
+    """(times, increments) of the paper's schedule for ``kind`` in PAPER_SCHEDULES."""
+    return two_rate_schedule(**PAPER_SCHEDULES[kind])
+
+
+def _increments(kind, schedule, steps, u_max):
+    if schedule == "paper":
+        return paper_schedule(kind)[1]
+    if schedule not in (None, "uniform"):
+        raise ValueError(f"unknown schedule {schedule!r}")
+    return np.full(steps, u_max / steps)
+
+
 def _node_ij(nx, ny):
     j, i = np.divmod(np.arange((nx + 1) * (ny + 1)), nx + 1)
     return i, j
@@ -69,8 +101,11 @@ def _slit(flags, nx, ny):
     flags[(j == ny // 2) & (i <= nx // 2)] |= D_FIX1
 
 
-def tensile(n, l=None, steps=20, u_max=6e-3, eta=1e-9):
-    """Tensile notched unit square: bottom fixed, top pulled up (u_x = 0 on top)."""
+def tensile(n, l=None, steps=20, u_max=6e-3, eta=1e-9, schedule=None):
+    """Tensile notched unit square: bottom fixed, top pulled up (u_x = 0 on top).
+
+    ``schedule``: None or "uniform" gives ``steps`` equal increments to ``u_max``;
+    "paper" gives the two-rate schedule of Sec. 4.1 (steps and u_max ignored)."""
     nx = ny = int(n)
     i, j = _node_ij(nx, ny)
     flags = np.zeros((nx + 1) * (ny + 1), np.uint8)
@@ -80,11 +115,12 @@ def tensile(n, l=None, steps=20, u_max=6e-3, eta=1e-9):
     E, nu = lame_to_E_nu(MIEHE_LAMBDA, MIEHE_MU)
     return Specimen("tensile", nx, ny, 1.0, 1.0, flags, np.ones(nx * ny, np.uint8), 1,
                     PLANE_STRAIN, E, nu, MIEHE_GC, 0.03 if l is None else l, eta,
-                    np.full(steps, u_max / steps))
+                    _increments("tensile", schedule, steps, u_max))
 
 
-def shear(n, l=None, steps=150, u_max=1.5e-2, eta=1e-9):
-    """Shear notched unit square: bottom fixed, top moved in x (u_y = 0), rollers on sides."""
+def shear(n, l=None, steps=150, u_max=1.5e-2, eta=1e-9, schedule=None):
+    """Shear notched unit square: bottom fixed, top moved in x (u_y = 0), rollers on sides.
+    ``schedule="paper"``: the two-rate schedule of Sec. 4.2."""
     nx = ny = int(n)
     i, j = _node_ij(nx, ny)
     flags = np.zeros((nx + 1) * (ny + 1), np.uint8)
@@ -96,10 +132,10 @@ def shear(n, l=None, steps=150, u_max=1.5e-2, eta=1e-9):
     E, nu = lame_to_E_nu(MIEHE_LAMBDA, MIEHE_MU)
     return Specimen("shear", nx, ny, 1.0, 1.0, flags, np.ones(nx * ny, np.uint8), 0,
                     PLANE_STRAIN, E, nu, MIEHE_GC, 0.03 if l is None else l, eta,
-                    np.full(steps, u_max / steps))
+                    _increments("shear", schedule, steps, u_max))
 
 
-def l_shape(n, steps=200, u_max=1.0, l=2.5, eta=1e-9, patch=30.0):
+def l_shape(n, steps=200, u_max=1.0, l=2.5, eta=1e-9, patch=30.0, schedule=None):
     """L-shaped panel: 500 x 500 mm with the top-right quadrant masked out, plane stress.
 
     The bottom edge under the upright part (x <= 250 mm) is clamped; the lower arm
@@ -122,7 +158,7 @@ def l_shape(n, steps=200, u_max=1.0, l=2.5, eta=1e-9, patch=30.0):
     flags[(j <= max(1, int(round(patch / h)))) & (x >= L - patch - 1e-9)] |= D_FIX0
     return Specimen("l_shape", nx, ny, L, L, flags, active.astype(np.uint8), 1,
                     PLANE_STRESS, 25.85, 0.18, 8.9e-5, l, eta,
-                    np.full(steps, u_max / steps))
+                    _increments("l_shape", schedule, steps, u_max))
 
 
 def uniaxial_bar(nx, ny, Lx=1.0, Ly=1.0, lam=MIEHE_LAMBDA, mu=MIEHE_MU, Gc=MIEHE_GC,

@@ -257,3 +257,24 @@ def test_fp32_refinement_is_scale_invariant(gpu, precond):
     assert abs(ra["lin_u"] - rb["lin_u"]) <= 0.1 * ra["lin_u"] + 16
     assert np.allclose(ua, ub, rtol=1e-6, atol=1e-6 * np.abs(ua).max())
     assert rb["reaction"] * 2.0 ** 60 == pytest.approx(ra["reaction"], rel=1e-6)
+
+
+@pytest.mark.parametrize("precision", [binding.FP64, binding.FP32_IR])
+@pytest.mark.parametrize("scheme", [0, 1, 3])
+def test_paper_schedule_tensile(gpu, scheme, precision):
+    # the two-rate schedule of Sec. 4.1: one 5.1e-3 mm step from the unloaded state (the
+    # longest step of the path in staggered passes), then 3e-5 mm steps
+    spec = S.tensile(32, l=0.06, schedule="paper")
+    fp64 = precision == binding.FP64
+    g, m, out = _run_both(spec, scheme, tol=1e-7, precision=precision, steps=4,
+                          tol_lin=1e-12 if fp64 else 1e-10, precond=binding.PRECOND_GMG)
+    peak = max(abs(o[0].reaction) for o in out)
+    for r_ref, r, st_ref, (u, d, H) in out:
+        assert r["converged"] == 1 and r_ref.converged
+        if fp64:
+            assert abs(r["reaction"] - r_ref.reaction) <= 1e-6 * peak
+            assert _max_diff(g, d, H, st_ref)[0] < 1e-5
+        else:
+            assert abs(r["reaction"] - r_ref.reaction) <= 1e-4 * peak
+            assert _d_rms(g, d, st_ref.d) <= 1e-3
+        assert abs(r["stag_iters"] - r_ref.stag_iters) <= max(2, 0.2 * r_ref.stag_iters)
