@@ -23,6 +23,21 @@ Degraded stress (Sec. 2, constitutive equation for sigma)::
 AT2 model (Table 1): g(d) = (1-d)^2 + eta, w(d) = d^2, c_w = 2 (history field).
 AT1 model (Table 1): same g, w(d) = d, c_w = 8/3, irreversibility by the penalty term of
 the evolution equation (Sec. 2, penalty parameter gamma = 27 G_c / (64 l tol_ir^2)).
+
+Spectral split (the alternative split that Sec. 2 names; the paper runs the VD split).
+With lam = K - 2 mu cdim (the Lame constant of the plane mode: lambda in plane strain,
+E nu / (1 - nu^2) in plane stress) and e1 >= e2 the in-plane principal strains (the
+out-of-plane principal strain of plane strain is 0 and adds nothing)::
+
+    Psi+ = (lam/2) <tr>_+^2 + mu (<e1>_+^2 + <e2>_+^2)
+    Psi- = (lam/2) <tr>_-^2 + mu (<e1>_-^2 + <e2>_-^2)
+    sigma = g(d) [lam <tr>_+ I + 2 mu eps+] + lam <tr>_- I + 2 mu eps-,
+    eps+- = sum_i <e_i>_+- n_i (x) n_i
+
+Both splits write Psi+ = Psi_a + Psi_b with a trace part Psi_a (VD: K/2 <tr>_+^2; spectral:
+lam/2 <tr>_+^2) and a second part Psi_b (VD: mu e.e; spectral: mu sum <e_i>_+^2).  The
+fixed-stress schemes act on these parts (``psi_parts``, ``extra_stiffness_parts``,
+``predict_psi_parts``).
 """
 import numpy as np
 
@@ -30,6 +45,7 @@ PLANE_STRAIN = 0
 PLANE_STRESS = 1
 
 C_W_AT2 = 2.0  # Table 1, AT2 row
+VD, SPECTRAL = 0, 1  # energy splits (Sec. 2)
 
 
 class Material:
@@ -40,13 +56,19 @@ class Material:
     (Table 1), ``cdim`` deviatoric factor (see module docstring).
     """
 
-    def __init__(self, mu, K, Gc, l, eta, cdim):
+    def __init__(self, mu, K, Gc, l, eta, cdim, split=VD):
         self.mu = float(mu)
         self.K = float(K)
         self.Gc = float(Gc)
         self.l = float(l)
         self.eta = float(eta)
         self.cdim = float(cdim)
+        self.split = int(split)
+
+    @property
+    def lam(self):
+        """Lame constant of the plane mode, K - 2 mu cdim."""
+        return self.K - 2.0 * self.mu * self.cdim
 
     @property
     def psi_crit(self):
@@ -54,7 +76,7 @@ class Material:
         return self.Gc / (C_W_AT2 * self.l)
 
 
-def material_from_E_nu(E, nu, Gc, l, eta, plane=PLANE_STRAIN):
+def material_from_E_nu(E, nu, Gc, l, eta, plane=PLANE_STRAIN, split=VD):
     """Lame constants from (E, nu); bulk modulus K per plane mode.
 
     Plane strain keeps the 3D bulk modulus K = lambda + 2 mu / 3.  Plane stress uses
@@ -64,8 +86,8 @@ def material_from_E_nu(E, nu, Gc, l, eta, plane=PLANE_STRAIN):
     mu = E / (2.0 * (1.0 + nu))
     lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
     if plane == PLANE_STRAIN:
-        return Material(mu, lam + 2.0 * mu / 3.0, Gc, l, eta, 1.0 / 3.0)
-    return Material(mu, E / (2.0 * (1.0 - nu)), Gc, l, eta, 0.5)
+        return Material(mu, lam + 2.0 * mu / 3.0, Gc, l, eta, 1.0 / 3.0, split)
+    return Material(mu, E / (2.0 * (1.0 - nu)), Gc, l, eta, 0.5, split)
 
 
 def E_nu_from_lame(lam, mu):
@@ -100,20 +122,70 @@ def invariants(exx, eyy, exy, cdim):
     return tr, ee
 
 
+def principal(exx, eyy, exy):
+    """In-plane principal strains e1 >= e2 and (cos 2t, sin 2t) of the direction n1 =
+    (cos t, sin t) of e1, from the eigenvalue problem of the symmetric 2 x 2 strain.
+    Where e1 = e2 the direction is arbitrary and (1, 0) is returned."""
+    exx, eyy, exy = np.broadcast_arrays(*(np.asarray(a, dtype=float) for a in (exx, eyy, exy)))
+    mean = 0.5 * (exx + eyy)
+    half = 0.5 * (exx - eyy)
+    R = np.hypot(half, exy)
+    safe = np.where(R > 0.0, R, 1.0)
+    c2 = np.where(R > 0.0, half / safe, 1.0)
+    s2 = np.where(R > 0.0, exy / safe, 0.0)
+    return mean + R, mean - R, c2, s2
+
+
+def psi_parts(exx, eyy, exy, m):
+    """(Psi_a, Psi_b): trace part and second part of Psi+ for the material's split."""
+    tr = exx + eyy
+    if m.split == SPECTRAL:
+        e1, e2, _, _ = principal(exx, eyy, exy)
+        return 0.5 * m.lam * pos(tr) ** 2, m.mu * (pos(e1) ** 2 + pos(e2) ** 2)
+    _, ee = invariants(exx, eyy, exy, m.cdim)
+    return 0.5 * m.K * pos(tr) ** 2, m.mu * ee
+
+
 def psi_plus(exx, eyy, exy, m):
-    """Active strain energy Psi+ = mu e.e + K/2 <tr>_+^2 (Sec. 2)."""
+    """Active strain energy (Sec. 2): VD Psi+ = mu e.e + K/2 <tr>_+^2; spectral split as in
+    the module docstring."""
+    if m.split == SPECTRAL:
+        a, b = psi_parts(exx, eyy, exy, m)
+        return a + b
     tr, ee = invariants(exx, eyy, exy, m.cdim)
     return m.mu * ee + 0.5 * m.K * pos(tr) ** 2
 
 
 def psi_minus(exx, eyy, exy, m):
-    """Inactive strain energy Psi- = K/2 <tr>_-^2 (Sec. 2)."""
+    """Inactive strain energy: VD Psi- = K/2 <tr>_-^2 (Sec. 2); spectral split as in the
+    module docstring."""
     tr, _ = invariants(exx, eyy, exy, m.cdim)
+    if m.split == SPECTRAL:
+        e1, e2, _, _ = principal(exx, eyy, exy)
+        return 0.5 * m.lam * neg(tr) ** 2 + m.mu * (neg(e1) ** 2 + neg(e2) ** 2)
     return 0.5 * m.K * neg(tr) ** 2
+
+
+def _spectral_stress(exx, eyy, exy, d, m):
+    tr = exx + eyy
+    gd = g(d, m.eta)
+    e1, e2, c2, s2 = principal(exx, eyy, exy)
+    # n1 (x) n1 = [(1 + c2)/2, s2/2; s2/2, (1 - c2)/2], n2 (x) n2 = I - n1 (x) n1
+    m1 = (0.5 * (1 + c2), 0.5 * (1 - c2), 0.5 * s2)
+    m2 = (0.5 * (1 - c2), 0.5 * (1 + c2), -0.5 * s2)
+    vol = m.lam * (gd * pos(tr) + neg(tr))
+    w1 = 2.0 * m.mu * (gd * pos(e1) + neg(e1))
+    w2 = 2.0 * m.mu * (gd * pos(e2) + neg(e2))
+    sxx = vol + w1 * m1[0] + w2 * m2[0]
+    syy = vol + w1 * m1[1] + w2 * m2[1]
+    sxy = w1 * m1[2] + w2 * m2[2]
+    return sxx, syy, sxy
 
 
 def stress(exx, eyy, exy, d, m):
     """In-plane components (sxx, syy, sxy) of the degraded stress (Sec. 2)."""
+    if m.split == SPECTRAL:
+        return _spectral_stress(exx, eyy, exy, d, m)
     tr = exx + eyy
     gd = g(d, m.eta)
     vol = gd * m.K * pos(tr) + m.K * neg(tr)
@@ -131,6 +203,8 @@ def stress_zz(exx, eyy, d, m):
     """
     tr = exx + eyy
     gd = g(d, m.eta)
+    if m.split == SPECTRAL:       # principal strain 0 along z: only the trace term
+        return m.lam * (gd * pos(tr) + neg(tr))
     return gd * 2.0 * m.mu * (-m.cdim * tr) + gd * m.K * pos(tr) + m.K * neg(tr)
 
 
@@ -157,6 +231,60 @@ def tangent_voigt(d, ip, m):
     D[..., 1, 0] = -two_mu_g * c + kv
     D[..., 2, 2] = m.mu * gd  # sxy = g 2 mu exy = g mu gamma
     return D
+
+
+def tangent_spectral(exx, eyy, exy, d, m):
+    """Consistent tangent of the spectral-split stress in Voigt form (xx, yy, engineering
+    xy) at the strain (exx, eyy, exy).
+
+    d sigma = lam [g H(tr) + 1 - H(tr)] tr(d eps) I + 2 mu [g P+ + (I - P+)] d eps with
+    H(x) = 1 for x > 0 (strict, as the VD indicator), and P+ = d eps+ / d eps, which in
+    the principal frame keeps the normal components with weights H(e1), H(e2) and the
+    shear component with the divided difference c12 = (<e1>_+ - <e2>_+)/(e1 - e2)
+    (H(e1) where e1 = e2): the derivative of an isotropic tensor function of a
+    symmetric 2 x 2 tensor.  Returns shape d.shape + (3, 3).
+    """
+    exx, eyy, exy, d = np.broadcast_arrays(*(np.asarray(a, dtype=float)
+                                             for a in (exx, eyy, exy, d)))
+    gd = g(d, m.eta)
+    tr = exx + eyy
+    e1, e2, c2, s2 = principal(exx, eyy, exy)
+    h1 = (e1 > 0.0).astype(float)
+    h2 = (e2 > 0.0).astype(float)
+    gap = e1 - e2
+    c12 = np.where(gap > 0.0, (pos(e1) - pos(e2)) / np.where(gap > 0.0, gap, 1.0), h1)
+    # unit strain tensors of the three Voigt components (engineering shear)
+    basis = [np.array([[1.0, 0.0], [0.0, 0.0]]), np.array([[0.0, 0.0], [0.0, 1.0]]),
+             np.array([[0.0, 0.5], [0.5, 0.0]])]
+    ct = np.sqrt(0.5 * (1.0 + c2))                       # cos t, t in [-pi/2, pi/2]
+    st_ = np.where(ct > 0.0, 0.5 * s2 / np.where(ct > 0.0, ct, 1.0), 1.0)
+    n1 = np.stack([ct, st_], axis=-1)
+    n2 = np.stack([-st_, ct], axis=-1)
+    M1 = n1[..., :, None] * n1[..., None, :]
+    M2 = n2[..., :, None] * n2[..., None, :]
+    N12 = n1[..., :, None] * n2[..., None, :] + n2[..., :, None] * n1[..., None, :]
+    kv = m.lam * np.where(tr > 0.0, gd, 1.0)
+    D = np.zeros(np.shape(d) + (3, 3))
+    for c, E in enumerate(basis):
+        a1 = np.einsum('...ij,ij->...', M1, E)
+        a2 = np.einsum('...ij,ij->...', M2, E)
+        a12 = np.einsum('...i,ij,...j->...', n1, E, n2)
+        Pp = (h1 * a1)[..., None, None] * M1 + (h2 * a2)[..., None, None] * M2 \
+            + (c12 * a12)[..., None, None] * N12
+        dsig = 2.0 * m.mu * ((gd - 1.0)[..., None, None] * Pp + E) \
+            + (kv * np.trace(E))[..., None, None] * np.eye(2)
+        D[..., 0, c] = dsig[..., 0, 0]
+        D[..., 1, c] = dsig[..., 1, 1]
+        D[..., 2, c] = dsig[..., 0, 1]
+    return D
+
+
+def tangent_at(exx, eyy, exy, d, m):
+    """Newton tangent of the stress at the strain (exx, eyy, exy) for the material's split
+    (VD: the frozen-indicator form ``tangent_voigt``)."""
+    if m.split == SPECTRAL:
+        return tangent_spectral(exx, eyy, exy, d, m)
+    return tangent_voigt(d, tension(exx, eyy), m)
 
 
 # --------------------------------------------------------------------------------------
@@ -299,3 +427,32 @@ def predict_psi(tr, ee, d_q, dd_q, scheme, m):
     else:
         ee_new = ee
     return m.mu * ee_new + 0.5 * m.K * tp_new ** 2
+
+
+# ---- fixed-stress forms on the energy parts (both splits) ----------------------------------
+def fixed_stress_Q_parts(pa, pb, scheme):
+    """Q_S on the energy parts: S1 2 Psi_a, S2 2 Psi_b, S3 2 (Psi_a + Psi_b), ST 0.  With
+    the VD parts these are the three forms after Table 2 (K <tr>_+^2, 2 mu e.e, sum); the
+    spectral split takes the same rule (the paper derives the schemes for VD only)."""
+    if scheme == S1:
+        return 2.0 * pa
+    if scheme == S2:
+        return 2.0 * pb
+    if scheme == S3:
+        return 2.0 * (pa + pb)
+    return np.zeros_like(pa)
+
+
+def extra_stiffness_parts(pa, pb, d_q, scheme, m):
+    """K~ = -4 (1-d)^2 / g(d) Q_S with Q_S from ``fixed_stress_Q_parts``."""
+    return -4.0 * (1.0 - d_q) ** 2 / g(d_q, m.eta) * fixed_stress_Q_parts(pa, pb, scheme)
+
+
+def predict_psi_parts(pa, pb, d_q, dd_q, scheme, m):
+    """Predicted active energy on the parts: the part(s) the scheme fixes are scaled by
+    s^2, s = 1 + 2(1-d)/g(d) max(Delta d, 0) -- the VD update of ``predict_psi``
+    (<tr>_+ and e.e^(1/2) scaled by s), written for any split with trace and second part."""
+    s = 1.0 + 2.0 * (1.0 - d_q) / g(d_q, m.eta) * np.where(dd_q > 0.0, dd_q, 0.0)
+    sa = s if scheme in (S1, S3) else 1.0
+    sb = s if scheme in (S2, S3) else 1.0
+    return pa * sa * sa + pb * sb * sb

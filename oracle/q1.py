@@ -129,13 +129,15 @@ def _elem_dofs(grid):
 
 
 # ---- elasticity (momentum balance) ------------------------------------------------------
-def assemble_elasticity(grid, d_q, ip, m):
+def assemble_elasticity(grid, d_q, ip, m, D=None):
     """Tangent K_uu = sum_e sum_q w B_q^T D_q B_q (CSR, 2N x 2N), all DOFs, no constraints.
 
-    ``d_q`` (ne, 4) phase field at the points, ``ip`` (ne, 4) frozen tension indicator.
+    ``d_q`` (ne, 4) phase field at the points, ``ip`` (ne, 4) frozen tension indicator of
+    the VD split; ``D`` (ne, 4, 3, 3) gives the point tangents directly instead.
     """
     B = _bmat(grid)
-    D = model.tangent_voigt(d_q, ip, m)                      # (ne, 4, 3, 3)
+    if D is None:
+        D = model.tangent_voigt(d_q, ip, m)                  # (ne, 4, 3, 3)
     Ke = np.einsum('qia,eqij,qjb->eab', B, D, B) * qp_weight(grid)
     Ke *= grid.elem_active[:, None, None]
     dofs = _elem_dofs(grid)
@@ -143,6 +145,13 @@ def assemble_elasticity(grid, d_q, ip, m):
     cols = np.tile(dofs, (1, 8)).ravel()
     n = 2 * grid.nn
     return sp.csr_matrix((Ke.ravel(), (rows, cols)), shape=(n, n))
+
+
+def assemble_elasticity_at(grid, u, d_q, m):
+    """Newton tangent of the internal force at u for the material's split
+    (model.tangent_at at every point)."""
+    exx, eyy, exy = strains_qp(grid, u)
+    return assemble_elasticity(grid, d_q, None, m, D=model.tangent_at(exx, eyy, exy, d_q, m))
 
 
 def internal_force(grid, u, d_q, m):

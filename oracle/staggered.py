@@ -21,6 +21,9 @@ the augmented tangent gives Delta d; the active energy is predicted from Delta d
 (Sec. 3.3, Delta d > 0 rule of Sec. 3.5); the energy is then frozen (footnote of
 Sec. 3.3) and the now linear evolution equation is solved once more, exactly.
 
+Both energy splits of Sec. 2 are supported (model.VD, model.SPECTRAL); the spectral split
+uses the consistent tangent of its stress in the Newton iteration (model.tangent_spectral).
+
 Readings where the paper is silent (the same readings are used by the CUDA path):
   * Newton stop: ||R_free||_2 <= TOL_NR * max(||R_free^0||_2, ||F_int on constrained||_2)
   * staggered residual: max over free d-DOFs of |R_d_i / (K_dd)_ii| with H from u^{k+1}
@@ -109,9 +112,12 @@ def solve_u(grid, m, u, d, opts):
             return u, it, True
         if it == opts.max_newton:
             break
-        exx, eyy, _ = q1.strains_qp(grid, u)
-        ip = model.tension(exx, eyy)
-        K = q1.assemble_elasticity(grid, d_q, ip, m)
+        if m.split == model.SPECTRAL:
+            K = q1.assemble_elasticity_at(grid, u, d_q, m)
+        else:
+            exx, eyy, _ = q1.strains_qp(grid, u)
+            ip = model.tension(exx, eyy)
+            K = q1.assemble_elasticity(grid, d_q, ip, m)
         Kff = K[free][:, free]
         u[free] += _lu_solve(Kff, -F[free])
     return u, opts.max_newton, False
@@ -134,15 +140,38 @@ def d_step_standard(grid, m, H_k):
     return _solve_damage_dirichlet(grid, c_q, m.Gc * m.l, q1.damage_rhs(grid, H_k))
 
 
+class _FixedStressTerms:
+    """K~ and the prediction at the points of u^k: the VD forms on (tr, e.e) for the VD
+    split, the forms on the energy parts for the spectral split (model module docstring)."""
+
+    def __init__(self, grid, m, u_k):
+        exx, eyy, exy = q1.strains_qp(grid, u_k)
+        self.m = m
+        self.psi = model.psi_plus(exx, eyy, exy, m)
+        if m.split == model.SPECTRAL:
+            self.pa, self.pb = model.psi_parts(exx, eyy, exy, m)
+        else:
+            self.tr, self.ee = model.invariants(exx, eyy, exy, m.cdim)
+
+    def extra(self, d_q, scheme):
+        if self.m.split == model.SPECTRAL:
+            return model.extra_stiffness_parts(self.pa, self.pb, d_q, scheme, self.m)
+        return model.extra_stiffness(self.tr, self.ee, d_q, scheme, self.m)
+
+    def predict(self, d_q, dd_q, scheme):
+        if self.m.split == model.SPECTRAL:
+            return model.predict_psi_parts(self.pa, self.pb, d_q, dd_q, scheme, self.m)
+        return model.predict_psi(self.tr, self.ee, d_q, dd_q, scheme, self.m)
+
+
 def d_step_fixed_stress(grid, m, u_k, d_k, H_prev, scheme, opts, info=None):
     """S1/S2/S3 d-step (Sec. 3.3-3.5): augmented NR iteration, prediction, frozen solve."""
-    exx, eyy, exy = q1.strains_qp(grid, u_k)
-    tr, ee = model.invariants(exx, eyy, exy, m.cdim)
-    psi = model.psi_plus(exx, eyy, exy, m)
+    fs = _FixedStressTerms(grid, m, u_k)
+    psi = fs.psi
     H_k = np.maximum(H_prev, psi)
     d_q = q1.interp_qp(grid, d_k)
     act = model.activation(psi, H_prev, d_q, m, opts.psi_crit) & grid.elem_active[:, None]
-    k_extra = np.where(act, model.extra_stiffness(tr, ee, d_q, scheme, m), 0.0)
+    k_extra = np.where(act, fs.extra(d_q, scheme), 0.0)
     c_std = m.Gc / m.l + 2.0 * H_k
     kappa = m.Gc * m.l
     # residual of the evolution equation at (d^k, H^k)
@@ -156,7 +185,7 @@ def d_step_fixed_stress(grid, m, u_k, d_k, H_prev, scheme, opts, info=None):
     dd[free] = _lu_solve(K_aug[free][:, free], -R[free])
     # predicted active energy, then the frozen (linear) solve
     dd_q = q1.interp_qp(grid, dd)
-    psi_hat = np.where(act, model.predict_psi(tr, ee, d_q, dd_q, scheme, m), psi)
+    psi_hat = np.where(act, fs.predict(d_q, dd_q, scheme), psi)
     H_half = np.maximum(H_prev, psi_hat)
     if info is not None:
         info['active'] = act
@@ -229,23 +258,22 @@ def at1_d_step(grid, m, u_k, d_k, d_prev, H_prev, scheme, opts):
     """AT1 d-step.  ST: Newton with Psi+(u^k).  S1/S2/S3 (Sec. 3.3-3.5): the first NR
     iteration with the augmented tangent gives Delta d; the active energy is predicted from
     it where the softening test holds and frozen; the NR iterations continue with it."""
-    exx, eyy, exy = q1.strains_qp(grid, u_k)
-    psi = model.psi_plus(exx, eyy, exy, m)
+    fs = _FixedStressTerms(grid, m, u_k)
+    psi = fs.psi
     if scheme == model.ST:
         return at1_newton(grid, m, psi, d_k, d_prev, opts)[0]
     a, kappa, gamma = model.at1_constants(m, opts.tol_ir)
-    tr, ee = model.invariants(exx, eyy, exy, m.cdim)
     d_q = q1.interp_qp(grid, d_k)
     pc = a if opts.psi_crit is None else opts.psi_crit
     act = model.activation(psi, H_prev, d_q, m, pc) & grid.elem_active[:, None]
-    k_extra = np.where(act, model.extra_stiffness(tr, ee, d_q, scheme, m), 0.0)
+    k_extra = np.where(act, fs.extra(d_q, scheme), 0.0)
     cJ = model.at1_mass_coefficient(psi, d_q, q1.interp_qp(grid, d_prev), gamma)
     c_aug = model.at1_augmented_coefficient(cJ, k_extra, m, opts.kt_floor)
     opts1 = Options(tol_nr=opts.tol_nr, max_newton=1, model=opts.model, tol_ir=opts.tol_ir,
                     tol_d=opts.tol_d)
     d_half, dd, _ = at1_newton(grid, m, psi, d_k, d_prev, opts1, c_first=c_aug)
     dd_q = q1.interp_qp(grid, dd)
-    psi_hat = np.where(act, model.predict_psi(tr, ee, d_q, dd_q, scheme, m), psi)
+    psi_hat = np.where(act, fs.predict(d_q, dd_q, scheme), psi)
     return at1_newton(grid, m, psi_hat, d_k + dd, d_prev, opts)[0]
 
 

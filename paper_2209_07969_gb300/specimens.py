@@ -175,6 +175,21 @@ def uniaxial_bar(nx, ny, Lx=1.0, Ly=1.0, lam=MIEHE_LAMBDA, mu=MIEHE_MU, Gc=MIEHE
                     PLANE_STRAIN, E, nu, Gc, l, eta, np.full(steps, u_max / steps))
 
 
+def uniaxial_stress_bar(nx, ny, Lx=0.5, Ly=1.0, lam=MIEHE_LAMBDA, mu=MIEHE_MU, Gc=MIEHE_GC,
+                        l=0.03, eta=1e-9, steps=10, u_max=1e-2):
+    """Plane-strain bar pulled along y with free sides: bottom u_y = 0, u_x = 0 at the
+    bottom-left node only, top u_y = ubar, no slit.  The exact state is uniform, with the
+    lateral strain set by sigma_xx = 0 (closed form per energy split)."""
+    i, j = _node_ij(nx, ny)
+    flags = np.zeros((nx + 1) * (ny + 1), np.uint8)
+    flags[j == 0] |= FIX_Y
+    flags[(j == 0) & (i == 0)] |= FIX_X
+    flags[j == ny] |= LOAD_Y
+    E, nu = lame_to_E_nu(lam, mu)
+    return Specimen("uniaxial_stress", nx, ny, Lx, Ly, flags, np.ones(nx * ny, np.uint8), 1,
+                    PLANE_STRAIN, E, nu, Gc, l, eta, np.full(steps, u_max / steps))
+
+
 def strip_1d(nx, ny=4, L=1.0, l=0.05):
     """Phase-field strip [0, L] x [0, L ny / nx] with d = 1 held on x = 0 and no load."""
     i, j = _node_ij(nx, ny)
