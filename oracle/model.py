@@ -256,10 +256,9 @@ def tangent_spectral(exx, eyy, exy, d, m):
     # unit strain tensors of the three Voigt components (engineering shear)
     basis = [np.array([[1.0, 0.0], [0.0, 0.0]]), np.array([[0.0, 0.0], [0.0, 1.0]]),
              np.array([[0.0, 0.5], [0.5, 0.0]])]
-    ct = np.sqrt(0.5 * (1.0 + c2))                       # cos t, t in [-pi/2, pi/2]
-    st_ = np.where(ct > 0.0, 0.5 * s2 / np.where(ct > 0.0, ct, 1.0), 1.0)
-    n1 = np.stack([ct, st_], axis=-1)
-    n2 = np.stack([-st_, ct], axis=-1)
+    t = 0.5 * np.arctan2(s2, c2)                          # direction of e1
+    n1 = np.stack([np.cos(t), np.sin(t)], axis=-1)
+    n2 = np.stack([-np.sin(t), np.cos(t)], axis=-1)
     M1 = n1[..., :, None] * n1[..., None, :]
     M2 = n2[..., :, None] * n2[..., None, :]
     N12 = n1[..., :, None] * n2[..., None, :] + n2[..., :, None] * n1[..., None, :]
