@@ -67,6 +67,14 @@ enum { PF_PLANE_STRAIN = 0, PF_PLANE_STRESS = 1 };
 enum { PF_FP64 = 0, PF_FP32_IR = 1 };          /* linear-solve precision */
 enum { PF_PRECOND_JACOBI = 0, PF_PRECOND_GMG = 1 };
 enum { PF_F64 = 0, PF_F32 = 1 };                /* element type of operator-level arrays */
+/* Energy split (Sec. 2).  VD: Psi+ = mu e.e + K/2 <tr>_+^2, the split the paper runs.
+ * SPECTRAL: the alternative split Sec. 2 names, Psi+ = lam/2 <tr>_+^2 + mu sum <e_i>_+^2
+ * over the in-plane principal strains e_i, lam = K - 2 mu cdim.  The fixed-stress schemes
+ * act on the trace part (S1), the second part (S2) or both (S3) of Psi+ for either split;
+ * with VD these are the forms of Sec. 3.4.  The spectral split's Newton tangent depends
+ * on the strain, not on a sign bit: its u-solves run on an assembled nodal stencil of the
+ * per-point tangents (FP64 and FP32 copies) instead of the matrix-free operator. */
+enum { PF_SPLIT_VD = 0, PF_SPLIT_SPECTRAL = 1 };
 
 /* Structured Q1 mesh; host pointers, copied by pf_create. */
 typedef struct {
@@ -86,6 +94,7 @@ typedef struct {
                                   semismooth Newton per d-solve */
   double tol_ir;               /* AT1 irreversibility tolerance: gamma = 27 G_c / (64 l
                                   tol_ir^2) (Sec. 2); <= 0 selects 0.01 */
+  int split;                   /* PF_SPLIT_VD (0) or PF_SPLIT_SPECTRAL (1) */
 } pf_mesh;
 
 #define PF_AT2_HISTORY 0
@@ -210,9 +219,11 @@ typedef struct {
 } pf_grid;
 
 /* Material in the notation of Sec. 2: shear modulus mu, bulk modulus K, deviatoric
- * factor cdim (1/3 plane strain, 1/2 plane stress), eta, G_c, l. */
+ * factor cdim (1/3 plane strain, 1/2 plane stress), eta, G_c, l, and the energy split
+ * (PF_SPLIT_VD or PF_SPLIT_SPECTRAL; pf_material_make sets PF_SPLIT_VD). */
 typedef struct {
   double mu, K, cdim, eta, Gc, l;
+  int split;
 } pf_material;
 
 pf_status pf_material_make(double E, double nu, double Gc, double l, double k_res,
@@ -225,20 +236,37 @@ pf_status pf_op_dof_mask(int nx, int ny, const uint8_t *node_flags,
                          const uint8_t *elem_active, uint8_t *dof_mask, void *stream);
 
 /* Internal force of the momentum balance, F = sum_e sum_q w B^T sigma(eps(u), d)
- * (weak form F_u of Sec. 3.2 without the boundary term), over all 2N DOFs, FP64.
- * `tension` (may be NULL) receives one byte per element, bit q set where
- * tr eps > 0 at Gauss point q (the indicator I_+ of Sec. 3.3).  dof_mask ignored. */
+ * (weak form F_u of Sec. 3.2 without the boundary term), over all 2N DOFs, FP64, for the
+ * material's split.  VD: `tension` (may be NULL) receives one byte per element, bit q set
+ * where tr eps > 0 at Gauss point q (the indicator I_+ of Sec. 3.3).  SPECTRAL: `tension`
+ * is not written; the call allocates and frees device scratch (12 doubles per element)
+ * and synchronises `stream`.  dof_mask ignored. */
 pf_status pf_op_elas_residual(const pf_grid *g, const pf_material *m, const double *u,
                               const double *d, double *F, uint8_t *tension, void *stream);
 
 /* y = K_uu x, the tangent of F for a frozen indicator `tension` (stress increment of
- * Sec. 3.3 at fixed d).  Rows/columns of constrained DOFs (dof_mask) are zeroed. dtype
- * PF_F64 or PF_F32 for d, x, y. */
+ * Sec. 3.3 at fixed d), VD split (the material's split is not read).  Rows/columns of
+ * constrained DOFs (dof_mask) are zeroed. dtype PF_F64 or PF_F32 for d, x, y. */
 pf_status pf_op_elas_apply(const pf_grid *g, const pf_material *m, int dtype, const void *d,
                            const uint8_t *tension, const void *x, void *y, void *stream);
 /* diag[i] = (K_uu)_ii for free DOFs, 0 for constrained ones. */
 pf_status pf_op_elas_diag(const pf_grid *g, const pf_material *m, int dtype, const void *d,
                           const uint8_t *tension, void *diag, void *stream);
+
+/* Newton tangent of the stress at every Gauss point for the material's split, FP64:
+ * Dq[k * 4 ne + 4 e + q], k = 0..5 the entries D00, D01, D02, D11, D12, D22 of the
+ * symmetric 3 x 3 Voigt matrix (xx, yy, engineering xy) mapping a strain increment to a
+ * stress increment.  VD: the frozen-indicator form at the sign of tr eps(u); SPECTRAL: the
+ * consistent tangent (principal-frame derivative of eps+).  Masked elements get 0. */
+pf_status pf_op_elas_tangent_qp(const pf_grid *g, const pf_material *m, const double *u,
+                                const double *d, double *Dq, void *stream);
+/* y = K(Dq) x = sum_e sum_q w B^T D_q B x with Dq as written by pf_op_elas_tangent_qp,
+ * through the assembled nodal stencil (9 neighbours x 2 x 2 blocks per node) that the
+ * spectral-split u-solves use.  Rows/columns of constrained DOFs (dof_mask) zeroed.
+ * dtype PF_F64 or PF_F32 for x and y (and the stencil); allocates and frees the stencil
+ * (36 values per node) and synchronises `stream`. */
+pf_status pf_op_elas_apply_qp(const pf_grid *g, int dtype, const double *Dq, const void *x,
+                              void *y, void *stream);
 
 /* y = K_dd x = sum_q w [c_q N N^T + kappa grad N . grad N^T] x (evolution equation
  * tangent, Sec. 3.2; AT2: c_q = G_c/l + 2 H_q (+ K~_q), kappa = G_c l).  c: 4*ne per
@@ -250,22 +278,24 @@ pf_status pf_op_damage_diag(const pf_grid *g, int dtype, const void *c, double k
 /* b = sum_q w 2 H_q N (AT2 driving term), all N DOFs, FP64. */
 pf_status pf_op_damage_rhs(const pf_grid *g, const double *H, double *b, void *stream);
 
-/* Per Gauss point (FP64): psi = Psi+(eps(u)) (Sec. 2) and Hout = max(Hprev, psi)
- * (history update).  psi may be NULL. */
+/* Per Gauss point (FP64): psi = Psi+(eps(u)) (Sec. 2, the material's split) and
+ * Hout = max(Hprev, psi) (history update).  psi may be NULL. */
 pf_status pf_op_qp_energy(const pf_grid *g, const pf_material *m, const double *u,
                           const double *Hprev, double *psi, double *Hout, void *stream);
 
 /* Fixed-stress coefficient (Sec. 3.4-3.5), per Gauss point, FP64:
  *   active = Psi+ > psi_crit && Psi+ > Hprev && d_q < 0.95 (strict),
  *   c_aug  = G_c/l + 2 max(Hprev, Psi+) + (active ? -4 (1-d_q)^2/g(d_q) Q_S : 0),
- * Q_S1 = K<tr>_+^2, Q_S2 = 2 mu e.e, Q_S3 = sum.  active: one byte per Gauss point. */
+ * Q_S1 = K<tr>_+^2, Q_S2 = 2 mu e.e, Q_S3 = sum (VD; SPECTRAL: Q_S1 = lam <tr>_+^2,
+ * Q_S2 = 2 mu sum <e_i>_+^2, Q_S3 = sum).  active: one byte per Gauss point. */
 pf_status pf_op_fs_coeff(const pf_grid *g, const pf_material *m, int scheme,
                          double psi_crit, const double *u, const double *d,
                          const double *Hprev, double *c_aug, uint8_t *active,
                          void *stream);
 /* Predicted history (Sec. 3.3 with the Delta d > 0 rule of Sec. 3.5), FP64:
  *   s = 1 + 2(1-d_q)/g(d_q) max(Delta d_q, 0); S1: <tr>_+ -> s<tr>_+; S2: e.e -> s^2 e.e;
- *   S3: both; Hhalf = max(Hprev, active ? Psi_hat : Psi+). */
+ *   S3: both (SPECTRAL: S1 scales the trace part, S2 the part mu sum <e_i>_+^2, by s^2);
+ *   Hhalf = max(Hprev, active ? Psi_hat : Psi+). */
 pf_status pf_op_fs_predict(const pf_grid *g, const pf_material *m, int scheme,
                            const double *u, const double *d, const double *dd,
                            const double *Hprev, const uint8_t *active, double *Hhalf,

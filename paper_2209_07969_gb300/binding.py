@@ -17,6 +17,7 @@ SCHEMES = {"ST": ST, "standard": ST, "S1": S1, "S2": S2, "S3": S3}
 FP64, FP32_IR = 0, 1
 PRECOND_JACOBI, PRECOND_GMG = 0, 1
 AT2_HISTORY, AT1_PENALTY = 0, 1
+SPLIT_VD, SPLIT_SPECTRAL = 0, 1
 F64, F32 = 0, 1
 
 
@@ -34,7 +35,7 @@ class Mesh(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("Lx", C.c_double), ("Ly", C.c_double),
                 ("elem_active", C.c_void_p), ("node_flags", C.c_void_p), ("plane", C.c_int),
                 ("precision", C.c_int), ("reaction_dir", C.c_int), ("precond", C.c_int),
-                ("model", C.c_int), ("tol_ir", C.c_double)]
+                ("model", C.c_int), ("tol_ir", C.c_double), ("split", C.c_int)]
 
 
 class Options(C.Structure):
@@ -62,7 +63,7 @@ class Grid(C.Structure):
 
 class Material(C.Structure):
     _fields_ = [("mu", C.c_double), ("K", C.c_double), ("cdim", C.c_double),
-                ("eta", C.c_double), ("Gc", C.c_double), ("l", C.c_double)]
+                ("eta", C.c_double), ("Gc", C.c_double), ("l", C.c_double), ("split", C.c_int)]
 
 
 _LIB = None
@@ -94,6 +95,8 @@ _PROTOS = {
     "pf_op_elas_residual": (S, [C.POINTER(Grid), C.POINTER(Material), P, P, P, P, P]),
     "pf_op_elas_apply": (S, [C.POINTER(Grid), C.POINTER(Material), I, P, P, P, P, P]),
     "pf_op_elas_diag": (S, [C.POINTER(Grid), C.POINTER(Material), I, P, P, P, P]),
+    "pf_op_elas_tangent_qp": (S, [C.POINTER(Grid), C.POINTER(Material), P, P, P, P]),
+    "pf_op_elas_apply_qp": (S, [C.POINTER(Grid), I, P, P, P, P]),
     "pf_op_damage_apply": (S, [C.POINTER(Grid), I, P, D, P, P, P]),
     "pf_op_damage_diag": (S, [C.POINTER(Grid), I, P, D, P, P]),
     "pf_op_damage_rhs": (S, [C.POINTER(Grid), P, P, P]),
@@ -137,9 +140,10 @@ def default_options():
     return o
 
 
-def material(E, nu, Gc, l, k_res, plane=0):
+def material(E, nu, Gc, l, k_res, plane=0, split=SPLIT_VD):
     m = Material()
     check(lib().pf_material_make(E, nu, Gc, l, k_res, plane, C.byref(m)), "pf_material_make")
+    m.split = split
     return m
 
 
@@ -147,11 +151,12 @@ def grid(nx, ny, hx, hy, elem_active_ptr=None, dof_mask_ptr=None):
     return Grid(nx, ny, hx, hy, elem_active_ptr, dof_mask_ptr)
 
 
-def footprint_bytes(spec, precision=FP64, precond=PRECOND_JACOBI, model=AT2_HISTORY):
+def footprint_bytes(spec, precision=FP64, precond=PRECOND_JACOBI, model=AT2_HISTORY,
+                    split=SPLIT_VD):
     """Device bytes pf_create would allocate for the specimen (admission control)."""
     active = None if spec.elem_active is None or np.all(spec.elem_active) else 1
     mesh = Mesh(spec.nx, spec.ny, spec.Lx, spec.Ly, active, 1, spec.plane, precision,
-                spec.reaction_dir, precond, model, 0.0)
+                spec.reaction_dir, precond, model, 0.0, split)
     return int(lib().pf_footprint_bytes(C.byref(mesh)))
 
 
@@ -159,7 +164,7 @@ class Simulation:
     """One fracture simulation resident on the current CUDA device (pf_create)."""
 
     def __init__(self, spec, precision=FP64, precond=PRECOND_JACOBI, options=None,
-                 model=AT2_HISTORY, tol_ir=0.01):
+                 model=AT2_HISTORY, tol_ir=0.01, split=SPLIT_VD):
         self.spec = spec
         self._flags = np.ascontiguousarray(spec.node_flags, dtype=np.uint8)
         self._active = None
@@ -168,7 +173,7 @@ class Simulation:
         mesh = Mesh(spec.nx, spec.ny, spec.Lx, spec.Ly,
                     self._active.ctypes.data if self._active is not None else None,
                     self._flags.ctypes.data, spec.plane, precision, spec.reaction_dir, precond,
-                    model, tol_ir)
+                    model, tol_ir, split)
         ctx = P()
         check(lib().pf_create(C.byref(mesh), spec.E, spec.nu, spec.Gc, spec.l, spec.eta,
                               C.byref(ctx)), "pf_create")

@@ -4,6 +4,7 @@
 #include <mutex>
 
 #include "pf_internal.cuh"
+#include "pf_spectral.cuh"
 #include "pf_vec.cuh"
 
 using namespace pf;
@@ -15,10 +16,15 @@ bool grid_ok(const pf_grid *g) {
          (double)(g->nx + 1) * (double)(g->ny + 1) <= 4.0e8;
 }
 GridD to_dev(const pf_grid *g) { return GridD{g->nx, g->ny, g->hx, g->hy, g->elem_active, g->dof_mask}; }
-MatD to_dev(const pf_material *m) { return MatD{m->mu, m->K, m->cdim, m->eta, m->Gc, m->l}; }
-bool mat_ok(const pf_material *m) {
-  return m && m->mu > 0 && m->K > 0 && m->cdim > 0 && m->eta >= 0 && m->Gc > 0 && m->l > 0;
+MatD to_dev(const pf_material *m) {
+  return MatD{m->mu, m->K, m->cdim, m->eta, m->Gc, m->l, m->split};
 }
+bool mat_ok(const pf_material *m) {
+  return m && m->mu > 0 && m->K > 0 && m->cdim > 0 && m->eta >= 0 && m->Gc > 0 && m->l > 0 &&
+         (m->split == PF_SPLIT_VD || m->split == PF_SPLIT_SPECTRAL);
+}
+size_t n_nodes(const pf_grid *g) { return (size_t)(g->nx + 1) * (g->ny + 1); }
+size_t n_points(const pf_grid *g) { return 4 * (size_t)g->nx * g->ny; }
 pf_status launched() { return cudaGetLastError() == cudaSuccess ? PF_OK : PF_ECUDA; }
 
 // Scratch for a one-off reduction: partials for `blocks` CTAs, the counter and one
@@ -56,8 +62,46 @@ pf_status pf_op_dof_mask(int nx, int ny, const uint8_t *node_flags, const uint8_
 pf_status pf_op_elas_residual(const pf_grid *g, const pf_material *m, const double *u,
                               const double *d, double *F, uint8_t *tension, void *stream) {
   if (!grid_ok(g) || !mat_ok(m) || !u || !d || !F) return PF_EINVAL;
+  if (m->split == PF_SPLIT_SPECTRAL) {
+    double *Sq = nullptr;
+    if (cudaMalloc((void **)&Sq, 3 * n_points(g) * sizeof(double)) != cudaSuccess)
+      return PF_ENOMEM;
+    cudaStream_t cs = (cudaStream_t)stream;
+    sp_points(to_dev(g), to_dev(m), u, d, Sq, nullptr, cs);
+    sp_force(to_dev(g), Sq, F, cs);
+    const bool ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(cs) == cudaSuccess;
+    cudaFree(Sq);
+    return ok ? PF_OK : PF_ECUDA;
+  }
   elas_residual(to_dev(g), to_dev(m), u, d, F, tension, (cudaStream_t)stream);
   return launched();
+}
+
+pf_status pf_op_elas_tangent_qp(const pf_grid *g, const pf_material *m, const double *u,
+                                const double *d, double *Dq, void *stream) {
+  if (!grid_ok(g) || !mat_ok(m) || !u || !d || !Dq) return PF_EINVAL;
+  sp_points(to_dev(g), to_dev(m), u, d, nullptr, Dq, (cudaStream_t)stream);
+  return launched();
+}
+
+pf_status pf_op_elas_apply_qp(const pf_grid *g, int dtype, const double *Dq, const void *x,
+                              void *y, void *stream) {
+  if (!grid_ok(g) || !Dq || !x || !y || (dtype != PF_F64 && dtype != PF_F32)) return PF_EINVAL;
+  const size_t ts = dtype == PF_F64 ? sizeof(double) : sizeof(float);
+  void *S = nullptr;
+  if (cudaMalloc(&S, 36 * n_nodes(g) * ts) != cudaSuccess) return PF_ENOMEM;
+  cudaStream_t cs = (cudaStream_t)stream;
+  const GridD gd = to_dev(g);
+  if (dtype == PF_F64) {
+    sp_stencil<double>(gd, Dq, (double *)S, cs);
+    sp_apply<double>(gd, (const double *)S, (const double *)x, (double *)y, cs);
+  } else {
+    sp_stencil<float>(gd, Dq, (float *)S, cs);
+    sp_apply<float>(gd, (const float *)S, (const float *)x, (float *)y, cs);
+  }
+  const bool ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(cs) == cudaSuccess;
+  cudaFree(S);
+  return ok ? PF_OK : PF_ECUDA;
 }
 
 pf_status pf_op_elas_apply(const pf_grid *g, const pf_material *m, int dtype, const void *d,
@@ -123,7 +167,7 @@ pf_status pf_op_damage_rhs(const pf_grid *g, const double *H, double *b, void *s
 pf_status pf_op_qp_energy(const pf_grid *g, const pf_material *m, const double *u,
                           const double *Hprev, double *psi, double *Hout, void *stream) {
   if (!grid_ok(g) || !mat_ok(m) || !u || !Hprev || !Hout) return PF_EINVAL;
-  qp_energy(to_dev(g), to_dev(m), u, Hprev, psi, Hout, (cudaStream_t)stream);
+  point_energy(to_dev(g), to_dev(m), u, Hprev, psi, Hout, (cudaStream_t)stream);
   return launched();
 }
 
@@ -133,8 +177,8 @@ pf_status pf_op_fs_coeff(const pf_grid *g, const pf_material *m, int scheme, dou
   if (!grid_ok(g) || !mat_ok(m) || !u || !d || !Hprev || !c_aug || !active ||
       scheme < PF_ST || scheme > PF_S3)
     return PF_EINVAL;
-  fs_coeff(to_dev(g), to_dev(m), scheme, psi_crit, u, d, Hprev, c_aug, active,
-           (cudaStream_t)stream);
+  point_fs_coeff(to_dev(g), to_dev(m), scheme, psi_crit, u, d, Hprev, c_aug, active,
+                 (cudaStream_t)stream);
   return launched();
 }
 
@@ -144,7 +188,8 @@ pf_status pf_op_fs_predict(const pf_grid *g, const pf_material *m, int scheme, c
   if (!grid_ok(g) || !mat_ok(m) || !u || !d || !dd || !Hprev || !active || !Hhalf ||
       scheme < PF_ST || scheme > PF_S3)
     return PF_EINVAL;
-  fs_predict(to_dev(g), to_dev(m), scheme, u, d, dd, Hprev, active, Hhalf, (cudaStream_t)stream);
+  point_fs_predict(to_dev(g), to_dev(m), scheme, u, d, dd, Hprev, active, Hhalf,
+                   (cudaStream_t)stream);
   return launched();
 }
 
@@ -179,7 +224,7 @@ pf_status pf_op_stag_residual(const pf_grid *g, const pf_material *m, const doub
   if (cudaMalloc(&buf, (2 * nq + 3 * nn) * sizeof(double)) != cudaSuccess) return PF_ENOMEM;
   double *H = buf, *c = buf + nq, *Kd = buf + 2 * nq, *b = Kd + nn, *diag = b + nn;
   cudaStream_t cs = (cudaStream_t)stream;
-  qp_energy(gd, md, u, Hprev, nullptr, H, cs);
+  point_energy(gd, md, u, Hprev, nullptr, H, cs);
   coef<double>(nq, m->Gc / m->l, H, c, cs);
   damage_rhs(gd, H, b, cs);
   damage_apply<double>(gfull, c, m->Gc * m->l, d, Kd, cs);
@@ -259,7 +304,7 @@ extern "C" pf_status pf_op_stag_residual_noalloc(const pf_grid *g, const pf_mate
   GridD gfull = gd;
   gfull.dofm = nullptr;
   MatD md = to_dev(m);
-  qp_energy(gd, md, u, Hprev, nullptr, H, cs);
+  point_energy(gd, md, u, Hprev, nullptr, H, cs);
   coef<double>(nq, m->Gc / m->l, H, c, cs);
   damage_rhs(gd, H, b, cs);
   damage_apply<double>(gfull, c, m->Gc * m->l, d, Kd, cs);

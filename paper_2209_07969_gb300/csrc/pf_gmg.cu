@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "pf_gmg.cuh"
+#include "pf_spectral.cuh"
 
 namespace pf {
 
@@ -29,10 +30,9 @@ inline unsigned nblk(size_t n, int cap = 1 << 16) {
   return (unsigned)b;
 }
 
-// stencil entry index: neighbour k = (dj+1)*3 + (di+1), block (r, c)
 template <int B>
 __device__ __forceinline__ size_t sidx(int k, int r, int c, size_t node, size_t nn) {
-  return ((size_t)(k * B * B + r * B + c)) * nn + node;
+  return sten_idx<B>(k, r, c, node, nn);
 }
 
 // ---- fine stencils ---------------------------------------------------------------------
@@ -909,6 +909,12 @@ cudaError_t gmg_setup_elas(Gmg<T> &G, const GridD &g, const MatD &m, const T *d,
 }
 
 template <class T>
+cudaError_t gmg_setup_elas_qp(Gmg<T> &G, const GridD &g, const double *Dq, cudaStream_t st) {
+  sp_stencil<T>(g, Dq, G.lv[0].S, st);
+  return gmg_setup_common<T, 2>(G, g, st);
+}
+
+template <class T>
 cudaError_t gmg_setup_damage(Gmg<T> &G, const GridD &g, const T *c, double kappa,
                              cudaStream_t st) {
   k_fine_stencil_damage<T><<<nblk(G.lv[0].nn), 128, 0, st>>>(g, c, kappa, G.lv[0].S);
@@ -1019,6 +1025,8 @@ void gmg_coarse_cycle(const Gmg<T> &G, int lc, const T *b0, T *x0, cudaStream_t 
                                          const uint8_t *, cudaStream_t);                       \
   template cudaError_t gmg_setup_damage<T>(Gmg<T> &, const GridD &, const T *, double,         \
                                            cudaStream_t);                                      \
+  template cudaError_t gmg_setup_elas_qp<T>(Gmg<T> &, const GridD &, const double *,           \
+                                            cudaStream_t);                                     \
   template void gmg_sten_apply<T>(const Gmg<T> &, int, const T *, const T *, T *, int,         \
                                   cudaStream_t);                                               \
   template void gmg_cheb_first<T>(const Gmg<T> &, int, const T *, T *, T *, T *, cudaStream_t); \

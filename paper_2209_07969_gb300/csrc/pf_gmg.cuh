@@ -21,6 +21,13 @@ constexpr int CHEB_DEGREE = 2;
 constexpr int COARSE_THREADS = 1024;  // threads of the single-CTA coarse cycle
 constexpr int GMG_CTA_NODES = 1100;   // levels with at most this many nodes run in that CTA
 
+// Stencil entry index: neighbour k = (dj+1)*3 + (di+1), block (r, c), node; entry-major so
+// that consecutive nodes of one entry are contiguous.
+template <int B>
+__host__ __device__ __forceinline__ size_t sten_idx(int k, int r, int c, size_t node, size_t nn) {
+  return ((size_t)(k * B * B + r * B + c)) * nn + node;
+}
+
 template <class T>
 struct GmgLevel {
   int nx = 0, ny = 0;
@@ -64,6 +71,9 @@ cudaError_t gmg_setup_elas(Gmg<T> &G, const GridD &g, const MatD &m, const T *d,
 template <class T>
 cudaError_t gmg_setup_damage(Gmg<T> &G, const GridD &g, const T *c, double kappa,
                              cudaStream_t st);
+// Elasticity setup from per-point tangents Dq (6 x Q, FP64; spectral split), see sp_points.
+template <class T>
+cudaError_t gmg_setup_elas_qp(Gmg<T> &G, const GridD &g, const double *Dq, cudaStream_t st);
 
 // Launchers of the V-cycle building blocks (pf_gmg.cu).
 template <class T>

@@ -25,6 +25,7 @@ struct GridD {
 
 struct MatD {
   double mu, K, cdim, eta, Gc, l;
+  int split;   // PF_SPLIT_VD or PF_SPLIT_SPECTRAL
 };
 
 // Device scalars of one Krylov solve.  The last CTA of each fused reduction updates

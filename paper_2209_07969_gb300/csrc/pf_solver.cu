@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "pf_gmg.cuh"
+#include "pf_spectral.cuh"
 #include "pf_internal.cuh"
 #include "pf_vec.cuh"
 
@@ -90,6 +91,10 @@ struct pf_ctx {
   float *fb = nullptr, *fx = nullptr, *fr = nullptr, *fz = nullptr, *fp = nullptr,
         *fq = nullptr, *finv = nullptr, *fd = nullptr, *fc = nullptr;
   double *csolve = nullptr;  // Q: coefficient of the current d-solve
+  // spectral split: per-point stress (3Q) and tangent (6Q) at the last residual evaluation,
+  // nodal stencils of the tangent (36 N, FP64 and, for PF_FP32_IR, FP32)
+  double *sp_Sq = nullptr, *sp_Dq = nullptr, *sp_S64 = nullptr;
+  float *sp_S32 = nullptr;
   KrylovScal *sc = nullptr;
   RedWs ws{};
   Gmg<double> gu, gd;        // multigrid hierarchies (FP64 mode)
@@ -510,8 +515,91 @@ pf_status mg_solve(pf_ctx *ctx, MgState &S, bool mg, Setup setup0, Solve solve, 
 }
 
 // ---- u-solve ---------------------------------------------------------------------------
+// Internal force F at (u, d) for the material's split; VD also writes the tension bits,
+// the spectral split the per-point tangents of the next Newton correction.  Returns the
+// kernel launches issued.
+int u_residual(pf_ctx *ctx) {
+  if (ctx->m.split == PF_SPLIT_SPECTRAL) {
+    sp_points(ctx->g, ctx->m, ctx->u, ctx->d, ctx->sp_Sq, ctx->sp_Dq, ctx->st);
+    sp_force(ctx->g, ctx->sp_Sq, ctx->F, ctx->st);
+    return 2;
+  }
+  elas_residual(ctx->g, ctx->m, ctx->u, ctx->d, ctx->F, ctx->tens, ctx->st);
+  return 1;
+}
+
+// Spectral split: one Newton correction with the consistent tangent at u (the per-point
+// tangents of the last residual evaluation) assembled into nodal stencils, FP64 and, for
+// the FP32 inner solves, FP32; the multigrid hierarchy is built from the same tangents and
+// its fine level is the stencil.
+pf_status newton_correction_sp(pf_ctx *ctx, double tol, int *lin, int *refines, bool *ok) {
+  PhaseTimer tm(&ctx->prof[PF_PROF_U_SOLVE]);
+  cudaStream_t st = ctx->st;
+  const size_t n = 2 * ctx->nn;
+  const bool mg = ctx->precond == PF_PRECOND_GMG;
+  sp_stencil<double>(ctx->g, ctx->sp_Dq, ctx->sp_S64, st);
+  ctx->launches++;
+  if (ctx->precision == PF_FP64) {
+    auto A = [ctx, st](const double *xx, double *yy, int epi) {
+      sp_apply<double>(ctx->g, ctx->sp_S64, xx, yy, st, ctx->sc, &ctx->ws, epi);
+    };
+    auto Af = [ctx, st](const double *xx, double *yy) {
+      sp_apply<double>(ctx->g, ctx->sp_S64, xx, yy, st);
+    };
+    if (!mg) {
+      sp_diag<double>(ctx->g, ctx->sp_S64, ctx->kz, st);
+      invert<double>(n, ctx->kz, ctx->kinv, st);
+      ctx->launches += 2;
+    }
+    auto setup = [&]() -> pf_status {
+      cudaError_t e = gmg_setup_elas_qp<double>(ctx->gu, ctx->g, ctx->sp_Dq, st);
+      if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
+      return PF_OK;
+    };
+    auto solve = [&](int maxit, int *it, bool *sok) {
+      return pcg<double>(ctx, SL_U, A, Af, mg ? &ctx->gu : nullptr, n, ctx->kb, ctx->kx, ctx->kr,
+                         ctx->kz, ctx->kp, ctx->kq, ctx->kinv, tol, maxit, it, sok);
+    };
+    return mg_solve(ctx, ctx->mg_u, mg, setup, solve, lin, ok);
+  }
+  sp_stencil<float>(ctx->g, ctx->sp_Dq, ctx->sp_S32, st);
+  ctx->launches++;
+  auto Af32 = [ctx, st](const float *xx, float *yy, int epi) {
+    sp_apply<float>(ctx->g, ctx->sp_S32, xx, yy, st, ctx->sc, &ctx->ws, epi);
+  };
+  auto Ff32 = [ctx, st](const float *xx, float *yy) {
+    sp_apply<float>(ctx->g, ctx->sp_S32, xx, yy, st);
+  };
+  if (!mg) {
+    sp_diag<float>(ctx->g, ctx->sp_S32, ctx->fz, st);
+    invert<float>(n, ctx->fz, ctx->finv, st);
+    ctx->launches += 2;
+  }
+  auto setup = [&]() -> pf_status {
+    cudaError_t e = gmg_setup_elas_qp<float>(ctx->gu32, ctx->g, ctx->sp_Dq, st);
+    if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "multigrid setup: %s", cudaGetErrorString(e));
+    return PF_OK;
+  };
+  auto solve = [&](int maxit, int *it, bool *iok) {
+    return pcg<float>(ctx, SL_U, Af32, Ff32, mg ? &ctx->gu32 : nullptr, n, ctx->fb, ctx->fx,
+                      ctx->fr, ctx->fz, ctx->fp, ctx->fq, ctx->finv, ctx->opt.tol_inner, maxit,
+                      it, iok);
+  };
+  auto inner = [&](int *it, bool *iok) {
+    int cnt = 0;
+    pf_status s2 = mg_solve(ctx, ctx->mg_u, mg, setup, solve, &cnt, iok);
+    *it = cnt;
+    return s2;
+  };
+  auto AD = [ctx, st](const double *xx, double *yy) {
+    sp_apply<double>(ctx->g, ctx->sp_S64, xx, yy, st);
+  };
+  return refine(ctx, AD, inner, n, 2, ctx->kb, ctx->kx, tol, lin, refines, ok);
+}
+
 // One Newton correction: K_t(d, tension) kx = kb on free DOFs.
 pf_status newton_correction(pf_ctx *ctx, double tol, int *lin, int *refines, bool *ok) {
+  if (ctx->m.split == PF_SPLIT_SPECTRAL) return newton_correction_sp(ctx, tol, lin, refines, ok);
   PhaseTimer tm(&ctx->prof[PF_PROF_U_SOLVE]);
   cudaStream_t st = ctx->st;
   const size_t n = 2 * ctx->nn;
@@ -590,9 +678,9 @@ pf_status solve_u(pf_ctx *ctx, int *newton, int *lin, int *refines, bool *ok) {
   for (int it = 0; it <= ctx->opt.max_newton; ++it) {
     {
       PhaseTimer tm(&ctx->prof[PF_PROF_U_RESID]);
-      elas_residual(ctx->g, ctx->m, ctx->u, ctx->d, ctx->F, ctx->tens, st);
+      ctx->launches += u_residual(ctx);
       norms(n, 2, ctx->g.dofm, ctx->F, ctx->dscal, ctx->ws, st);
-      ctx->launches += 2;
+      ctx->launches++;
       CKS(check_launch(ctx));
       CKS(read_scalars(ctx, ctx->dscal, 2 * sizeof(double)));
     }
@@ -789,7 +877,7 @@ pf_status at1_newton(pf_ctx *ctx, const double *psi, double fscale, int *lin, in
 pf_status at1_d_step(pf_ctx *ctx, int scheme, int *lin, int *refines, int *dsolves, bool *ok) {
   cudaStream_t st = ctx->st;
   // current energy into Hk (csolve takes the unused history output)
-  qp_energy(ctx->g, ctx->m, ctx->u, ctx->H, ctx->Hk, ctx->csolve, st);
+  point_energy(ctx->g, ctx->m, ctx->u, ctx->H, ctx->Hk, ctx->csolve, st);
   ctx->launches++;
   double fscale;
   CKS(at1_scale(ctx, &fscale));
@@ -801,7 +889,7 @@ pf_status at1_d_step(pf_ctx *ctx, int scheme, int *lin, int *refines, int *dsolv
   at1.gamma = ctx->at1_gamma;
   at1.floor = ctx->at1_floor;
   // augmented coefficient into csolve (solve_damage uses it in place)
-  fs_coeff(ctx->g, ctx->m, scheme, pc, ctx->u, ctx->d, ctx->H, ctx->csolve, ctx->act, st, at1);
+  point_fs_coeff(ctx->g, ctx->m, scheme, pc, ctx->u, ctx->d, ctx->H, ctx->csolve, ctx->act, st, at1);
   ctx->launches++;
   double rn;
   CKS(at1_rhs(ctx, ctx->Hk, &rn));
@@ -812,7 +900,7 @@ pf_status at1_d_step(pf_ctx *ctx, int scheme, int *lin, int *refines, int *dsolv
   bool ok1 = false;
   CKS(solve_damage(ctx, ctx->csolve, ctx->bd, ctx->dd, lin, refines, &ok1));
   (*dsolves)++;
-  fs_predict(ctx->g, ctx->m, scheme, ctx->u, ctx->d, ctx->dd, ctx->H, ctx->act, ctx->Hk, st, 1);
+  point_fs_predict(ctx->g, ctx->m, scheme, ctx->u, ctx->d, ctx->dd, ctx->H, ctx->act, ctx->Hk, st, 1);
   add(ctx->nn, ctx->dd, ctx->d, st);
   ctx->launches += 2;
   CKS(at1_newton(ctx, ctx->Hk, fscale, lin, refines, dsolves, ok));
@@ -824,7 +912,7 @@ pf_status at1_d_step(pf_ctx *ctx, int scheme, int *lin, int *refines, int *dsolv
 // penalty at d^{k+1}.
 pf_status at1_stag_residual(pf_ctx *ctx, double *out) {
   cudaStream_t st = ctx->st;
-  qp_energy(ctx->g, ctx->m, ctx->u, ctx->H, ctx->Hk, ctx->csolve, st);
+  point_energy(ctx->g, ctx->m, ctx->u, ctx->H, ctx->Hk, ctx->csolve, st);
   at1_coef(ctx->g, ctx->Hk, ctx->d, ctx->d_prev, ctx->at1_a, ctx->at1_gamma, ctx->Hhalf, ctx->cq,
            ctx->bhalf, st);
   damage_rhs(ctx->g, ctx->bhalf, ctx->bd, st);
@@ -844,7 +932,7 @@ pf_status d_step(pf_ctx *ctx, int scheme, int *lin, int *refines, int *dsolves, 
   const double gcl = ctx->m.Gc / ctx->m.l;
   const double kappa = ctx->m.Gc * ctx->m.l;
   const size_t n = ctx->nn;
-  qp_energy(ctx->g, ctx->m, ctx->u, ctx->H, nullptr, ctx->Hk, st);
+  point_energy(ctx->g, ctx->m, ctx->u, ctx->H, nullptr, ctx->Hk, st);
   ctx->launches++;
   if (scheme == PF_ST) {
     coef<double>(ctx->nq, gcl, ctx->Hk, ctx->cq, st);
@@ -855,7 +943,7 @@ pf_status d_step(pf_ctx *ctx, int scheme, int *lin, int *refines, int *dsolves, 
   }
   // S1/S2/S3: augmented first NR iteration for Delta d (Sec. 3.4) ...
   const double pc = ctx->opt.psi_crit < 0.0 ? ctx->m.Gc / (2.0 * ctx->m.l) : ctx->opt.psi_crit;
-  fs_coeff(ctx->g, ctx->m, scheme, pc, ctx->u, ctx->d, ctx->H, ctx->Hhalf, ctx->act, st);
+  point_fs_coeff(ctx->g, ctx->m, scheme, pc, ctx->u, ctx->d, ctx->H, ctx->Hhalf, ctx->act, st);
   coef<double>(ctx->nq, gcl, ctx->Hk, ctx->cq, st);
   damage_rhs(ctx->g, ctx->Hk, ctx->bd, st);
   damage_apply<double>(grid_nomask(ctx), ctx->cq, kappa, ctx->d, ctx->Kd, st);
@@ -865,7 +953,7 @@ pf_status d_step(pf_ctx *ctx, int scheme, int *lin, int *refines, int *dsolves, 
   CKS(solve_damage(ctx, ctx->Hhalf, ctx->bd, ctx->dd, lin, refines, &ok1));
   (*dsolves)++;
   // ... predicted history (Sec. 3.3, Delta d > 0 rule of Sec. 3.5) ...
-  fs_predict(ctx->g, ctx->m, scheme, ctx->u, ctx->d, ctx->dd, ctx->H, ctx->act, ctx->Hhalf, st);
+  point_fs_predict(ctx->g, ctx->m, scheme, ctx->u, ctx->d, ctx->dd, ctx->H, ctx->act, ctx->Hhalf, st);
   // ... and the frozen, linear evolution equation.
   coef<double>(ctx->nq, gcl, ctx->Hhalf, ctx->cq, st);
   ctx->launches += 2;
@@ -881,7 +969,7 @@ pf_status stag_residual(pf_ctx *ctx, double *out) {
   cudaStream_t st = ctx->st;
   const double gcl = ctx->m.Gc / ctx->m.l;
   const double kappa = ctx->m.Gc * ctx->m.l;
-  qp_energy(ctx->g, ctx->m, ctx->u, ctx->H, nullptr, ctx->Hk, st);
+  point_energy(ctx->g, ctx->m, ctx->u, ctx->H, nullptr, ctx->Hk, st);
   coef<double>(ctx->nq, gcl, ctx->Hk, ctx->cq, st);
   damage_rhs(ctx->g, ctx->Hk, ctx->bd, st);
   damage_apply<double>(grid_nomask(ctx), ctx->cq, kappa, ctx->d, ctx->Kd, st);
@@ -908,7 +996,7 @@ void free_all(pf_ctx *c) {
                   c->bd, c->Kd, c->dd, c->flags,  c->active, c->dofm, c->tens, c->kb, c->kx,
                   c->kr, c->kz, c->kp, c->kq, c->kinv, c->kres, c->fb, c->fx, c->fr, c->fz,
                   c->fp, c->fq, c->finv, c->fd, c->fc, c->sc, c->ws.partials, c->ws.counter,
-                  c->dscal, c->csolve, c->bhalf};
+                  c->dscal, c->csolve, c->bhalf, c->sp_Sq, c->sp_Dq, c->sp_S64, c->sp_S32};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   gmg_free<double>(c->gu);
@@ -979,6 +1067,7 @@ pf_status pf_material_make(double E, double nu, double Gc, double l, double k_re
   out->eta = k_res;
   out->Gc = Gc;
   out->l = l;
+  out->split = PF_SPLIT_VD;
   return PF_OK;
 }
 
@@ -991,6 +1080,7 @@ pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double 
       (mesh->reaction_dir != 0 && mesh->reaction_dir != 1) ||
       (mesh->precond != PF_PRECOND_JACOBI && mesh->precond != PF_PRECOND_GMG) ||
       (mesh->model != PF_AT2_HISTORY && mesh->model != PF_AT1_PENALTY) ||
+      (mesh->split != PF_SPLIT_VD && mesh->split != PF_SPLIT_SPECTRAL) ||
       !(mesh->tol_ir == mesh->tol_ir))
     return PF_EINVAL;
   if ((double)(mesh->nx + 1) * (double)(mesh->ny + 1) > 4.0e8) return PF_EINVAL;
@@ -1007,7 +1097,7 @@ pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double 
   ctx->reaction_dir = mesh->reaction_dir;
   ctx->precond = mesh->precond;
   ctx->plane = mesh->plane;
-  ctx->m = MatD{mat.mu, mat.K, mat.cdim, mat.eta, mat.Gc, mat.l};
+  ctx->m = MatD{mat.mu, mat.K, mat.cdim, mat.eta, mat.Gc, mat.l, mesh->split};
   ctx->model = mesh->model;
   if (ctx->model == PF_AT1_PENALTY) {
     const double cw = 8.0 / 3.0, tir = mesh->tol_ir > 0.0 ? mesh->tol_ir : 0.01;
@@ -1035,6 +1125,10 @@ pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double 
   AL(Hk, nq); AL(cq, nq); AL(Hhalf, nq); AL(act, nq);
   AL(bd, nn); AL(Kd, nn); AL(dd, nn); AL(csolve, nq);
   if (ctx->model == PF_AT1_PENALTY) AL(bhalf, nq);
+  if (mesh->split == PF_SPLIT_SPECTRAL) {
+    AL(sp_Sq, 3 * nq); AL(sp_Dq, 6 * nq); AL(sp_S64, 36 * nn);
+    if (ctx->precision == PF_FP32_IR) AL(sp_S32, 36 * nn);
+  }
   AL(flags, nn); AL(dofm, nn); AL(tens, ne);
   if (mesh->elem_active) AL(active, ne);
   AL(kb, 2 * nn); AL(kx, 2 * nn); AL(kr, 2 * nn); AL(kz, 2 * nn); AL(kp, 2 * nn);
@@ -1122,6 +1216,8 @@ size_t pf_footprint_bytes(const pf_mesh *mesh) {
              + 8 * 2 * nn * D;                          // Krylov work (FP64)
   if (mesh->precision == PF_FP32_IR) b += 7 * 2 * nn * F + nn * F + nq * F;
   if (mesh->model == PF_AT1_PENALTY) b += nq * D;          // bhalf
+  if (mesh->split == PF_SPLIT_SPECTRAL)                     // point data, stencils
+    b += 9 * nq * D + 36 * nn * D + (mesh->precision == PF_FP32_IR ? 36 * nn * F : 0);
   const size_t tiles = (size_t)tile_blocks_x(mesh->nx) * tile_blocks_y(mesh->ny);
   const size_t mb = tiles > 4096 ? tiles : 4096;
   b += 4 * mb * D + red_counters((int)mb) * sizeof(unsigned) + sizeof(KrylovScal) + 8 * D;
@@ -1193,12 +1289,12 @@ pf_status pf_load_step(pf_ctx *ctx, double d_ubar, int scheme, double tol,
   }
   r.stag_residual = resid;
   // commit history and report the reaction force
-  qp_energy(ctx->g, ctx->m, ctx->u, ctx->H, nullptr, ctx->Hk, st);
+  point_energy(ctx->g, ctx->m, ctx->u, ctx->H, nullptr, ctx->Hk, st);
   ctx->launches++;
   CK(cudaMemcpyAsync(ctx->H, ctx->Hk, ctx->nq * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  elas_residual(ctx->g, ctx->m, ctx->u, ctx->d, ctx->F, ctx->tens, st);
+  ctx->launches += u_residual(ctx);
   reaction(ctx->nn, ctx->flags, ctx->reaction_dir, ctx->F, ctx->dscal, ctx->ws, st);
-  ctx->launches += 2;
+  ctx->launches++;
   CK(cudaEventRecord(ctx->ev1, st));
   CKS(check_launch(ctx));
   CKS(read_scalars(ctx, ctx->dscal, sizeof(double)));
