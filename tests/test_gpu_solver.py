@@ -262,12 +262,16 @@ def test_fp32_refinement_is_scale_invariant(gpu, precond):
 @pytest.mark.parametrize("precision", [binding.FP64, binding.FP32_IR])
 @pytest.mark.parametrize("scheme", [0, 1, 3])
 def test_paper_schedule_tensile(gpu, scheme, precision):
-    # the two-rate schedule of Sec. 4.1: one 5.1e-3 mm step from the unloaded state (the
-    # longest step of the path in staggered passes), then 3e-5 mm steps
+    # The two-rate schedule of Sec. 4.1: one 5.1e-3 mm step from the unloaded state, then
+    # 3e-5 mm steps.  In the first step the staggered iteration first approaches an unstable
+    # equilibrium of the un-cracked specimen (the residual falls to a few 1e-7) and then
+    # leaves it as the crack grows from the slit; where that plateau's minimum lands is set
+    # by rounding, so a tolerance near it stops either code at either state.  1e-9 lies two
+    # orders below the plateau: both codes go on to the same cracked state.
     spec = S.tensile(32, l=0.06, schedule="paper")
     fp64 = precision == binding.FP64
-    g, m, out = _run_both(spec, scheme, tol=1e-7, precision=precision, steps=4,
-                          tol_lin=1e-12 if fp64 else 1e-10, precond=binding.PRECOND_GMG)
+    g, m, out = _run_both(spec, scheme, tol=1e-9, precision=precision, steps=4,
+                          tol_lin=1e-12, precond=binding.PRECOND_GMG)
     peak = max(abs(o[0].reaction) for o in out)
     for r_ref, r, st_ref, (u, d, H) in out:
         assert r["converged"] == 1 and r_ref.converged

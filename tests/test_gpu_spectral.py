@@ -128,7 +128,7 @@ def test_point_kernels(case):
     dd = np.random.default_rng(3).standard_normal(g.nn) * 0.05
     ddq = q1.interp_qp(g, dd)
     # threshold between two well-separated energies near the median (no point at a tie)
-    v = np.sort(pref[live.ravel()])
+    v = np.sort(pref[np.broadcast_to(live, pref.shape)])
     k = len(v) // 2
     while v[k + 1] - v[k] < 1e-9 * v[k + 1]:
         k += 1
