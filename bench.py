@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--grids", default="64,128")
     p.add_argument("--rate", type=float, default=4.0, help="Poisson arrival rate, requests/s")
     p.add_argument("--slots", type=int, default=8)
+    p.add_argument("--split", default="vd", choices=["vd", "spectral"],
+                   help="energy split (Sec. 2): vd (the workload's) or spectral")
     p.add_argument("--host-loop", action="store_true",
                    help="host-checked Krylov batches instead of device-side loops (same "
                         "kernels; for profilers that cannot see inside conditional graph nodes)")
@@ -119,13 +121,13 @@ class Clocks:
 
 
 # ---- checker sample (CPU) ---------------------------------------------------------------
-def oracle_sample(grid):
+def oracle_sample(grid, split=0):
     """One exact phase-field solve of load step 1 (assembly + LU); returns seconds."""
     import numpy as np
     from oracle import model, q1, staggered as stg
     sp = workload(grid)
     g = q1.Grid(sp.nx, sp.ny, sp.Lx, sp.Ly, sp.node_flags, sp.elem_active)
-    m = model.material_from_E_nu(sp.E, sp.nu, sp.Gc, sp.l, sp.eta, sp.plane)
+    m = model.material_from_E_nu(sp.E, sp.nu, sp.Gc, sp.l, sp.eta, sp.plane, split)
     j = np.arange(g.nn) // (g.nx + 1)
     u = np.stack([np.zeros(g.nn), sp.increments[0] * j / g.ny], 1).ravel()
     t0 = time.perf_counter()
@@ -134,14 +136,14 @@ def oracle_sample(grid):
     return time.perf_counter() - t0
 
 
-def oracle_u_sample(grid):
+def oracle_u_sample(grid, split=0):
     """One exact Newton linear solve for u of load step 1 (residual, assembly, SuperLU);
     returns seconds."""
     import numpy as np
     from oracle import model, q1, staggered as stg
     sp = workload(grid)
     g = q1.Grid(sp.nx, sp.ny, sp.Lx, sp.Ly, sp.node_flags, sp.elem_active)
-    m = model.material_from_E_nu(sp.E, sp.nu, sp.Gc, sp.l, sp.eta, sp.plane)
+    m = model.material_from_E_nu(sp.E, sp.nu, sp.Gc, sp.l, sp.eta, sp.plane, split)
     u = g.u_dirichlet_values(sp.increments[0])
     d = g.d_dirichlet_values()
     t0 = time.perf_counter()
@@ -149,12 +151,12 @@ def oracle_u_sample(grid):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(grid):
+def cpu_baseline(grid, split=0):
     """The checker on a bounded sample of the workload: one exact u Newton solve and one
     exact phase-field solve, composed into the cost of a load step of the timed window
     (two u Newton solves and two phase-field solves per step under S1)."""
-    t_u = oracle_u_sample(grid)
-    t_d = oracle_sample(grid)
+    t_u = oracle_u_sample(grid, split)
+    t_d = oracle_sample(grid, split)
     step = 2 * t_u + 2 * t_d
     return {"value": 1.0 / (STEPS_PER_PATH * step), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": (f"one exact Newton solve for u ({t_u:.1f} s) and one exact phase-field "
@@ -274,8 +276,9 @@ def run_ours(args):
     spec = workload(args.grid)
     scheme = binding.SCHEMES[args.scheme]
     B = args.batch
-    sims = [binding.Simulation(spec, precision=binding.FP32_IR, precond=binding.PRECOND_GMG)
-            for _ in range(B)]
+    split = binding.SPLIT_SPECTRAL if args.split == "spectral" else binding.SPLIT_VD
+    sims = [binding.Simulation(spec, precision=binding.FP32_IR, precond=binding.PRECOND_GMG,
+                               split=split) for _ in range(B)]
     for s in sims:
         s.set_options(max_stag=1000, device_loop=0 if args.host_loop else 1)
     incs = spec.increments
@@ -353,9 +356,15 @@ def run_ours(args):
     out = None
     if rank == 0:
         pk, which = peaks()
-        roof = kernel_roofline(spec, sims, pk.get("hbm_gbs", 6800.0))
-        roof["peak_source"] = which
-        base = cpu_baseline(args.grid)
+        if split == binding.SPLIT_VD:
+            roof = kernel_roofline(spec, sims, pk.get("hbm_gbs", 6800.0))
+            roof["peak_source"] = which
+        else:   # the matrix-free VD kernel is not on this path
+            roof = {"bound": "hbm", "achieved": None, "peak": pk.get("hbm_gbs", 6800.0),
+                    "unit": "GB/s", "frac": None, "traffic": None,
+                    "note": "spectral split: u-solves apply the assembled stencil "
+                            "(k_sp_apply, 161 B/node in FP32); not timed by this leg"}
+        base = cpu_baseline(args.grid, split)
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -363,7 +372,8 @@ def run_ours(args):
                "config": {"workload": f"tensile notched square {args.grid}x{args.grid} Q1, l=0.0075 mm, "
                                       f"100 load steps to 6e-3 mm, TOL_ST 1e-5, scheme {args.scheme}, "
                                       "FP32 CG + FP64 refinement, GMG; batch of independent "
-                                      "simulations on separate streams",
+                                      "simulations on separate streams"
+                                      + ("; spectral energy split" if split else ""),
                           "batch": B, "timed_load_steps": f"{args.warmup}..{args.warmup + args.steps - 1}",
                           "l2": "working set per simulation ~0.2 GB, batch exceeds L2"},
                "dof_cg_iters_per_s": work * world / T,

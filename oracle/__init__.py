@@ -20,6 +20,8 @@ fracture based on the fixed-stress concept", arXiv 2209.07969):
                     staggered scheme (Sec. 3.1, Fig. 1) and the fixed-stress S1/S2/S3
                     schemes (Sec. 3.3-3.5, Table 2), solved with SciPy's sparse direct
                     LU (SuperLU).
+* ``monolithic`` -- Newton on the coupled system with the full Jacobian of Sec. 3.2
+                    (reference for the converged state of a load step).
 
 Everything is float64 and deliberately unoptimised: vectorised numpy over elements is
 the only liberty taken.  The oracle shares no code with the CUDA path.

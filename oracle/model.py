@@ -182,6 +182,22 @@ def _spectral_stress(exx, eyy, exy, d, m):
     return sxx, syy, sxy
 
 
+def stress_plus(exx, eyy, exy, m):
+    """Undegraded active stress sigma+ = d Psi+ / d eps (in-plane components): VD
+    2 mu eps_dev + K <tr>_+ I; spectral lam <tr>_+ I + 2 mu eps+."""
+    if m.split == SPECTRAL:
+        tr = exx + eyy
+        e1, e2, c2, s2 = principal(exx, eyy, exy)
+        vol = m.lam * pos(tr)
+        w1, w2 = 2.0 * m.mu * pos(e1), 2.0 * m.mu * pos(e2)
+        return (vol + 0.5 * (w1 * (1 + c2) + w2 * (1 - c2)),
+                vol + 0.5 * (w1 * (1 - c2) + w2 * (1 + c2)), 0.5 * s2 * (w1 - w2))
+    tr = exx + eyy
+    vol = m.K * pos(tr)
+    return (2.0 * m.mu * (exx - m.cdim * tr) + vol, 2.0 * m.mu * (eyy - m.cdim * tr) + vol,
+            2.0 * m.mu * exy)
+
+
 def stress(exx, eyy, exy, d, m):
     """In-plane components (sxx, syy, sxy) of the degraded stress (Sec. 2)."""
     if m.split == SPECTRAL:
