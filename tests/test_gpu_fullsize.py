@@ -24,10 +24,12 @@ pytestmark = pytest.mark.gpu
 TOL_ST = 1e-5
 
 
-def _check_state(spec, steps, scheme=binding.S1):
+def _check_state(spec, steps, scheme=binding.S1, split=binding.SPLIT_VD):
     g = q1.Grid(spec.nx, spec.ny, spec.Lx, spec.Ly, spec.node_flags, spec.elem_active)
-    m = model.material_from_E_nu(spec.E, spec.nu, spec.Gc, spec.l, spec.eta, spec.plane)
-    sim = binding.Simulation(spec, precision=binding.FP32_IR, precond=binding.PRECOND_GMG)
+    m = model.material_from_E_nu(spec.E, spec.nu, spec.Gc, spec.l, spec.eta, spec.plane,
+                                 split)
+    sim = binding.Simulation(spec, precision=binding.FP32_IR, precond=binding.PRECOND_GMG,
+                             split=split)
     ubar = 0.0
     H_prev = np.zeros((g.ne, 4))
     for k in range(steps):
@@ -78,3 +80,11 @@ def test_shear_1024():
 def test_lshape_2048_plane_stress():
     r = _check_state(S.l_shape(2048), 2)
     assert r["reaction"] != 0
+
+
+def test_tensile_512_spectral_split():
+    # the spectral split's stencil u-solves on the full-size multigrid hierarchy
+    r = _check_state(S.tensile(512, l=0.0075, steps=100, u_max=6e-3), 3,
+                     split=binding.SPLIT_SPECTRAL)
+    assert r["reaction"] > 0
+
