@@ -5,6 +5,8 @@ Sec. 4.1: 3e-5 mm/s, one step of 170 s, then 1 s steps up to 220 s.  Sec. 4.2: t
 rate, one step of 250 s, then 1 s steps up to 380 s.  Sec. 4.3: 1e-3 mm/s, 0.01 s steps
 up to 0.2 s, then 0.001 s steps up to 0.6 s.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -27,6 +29,15 @@ def test_paper_schedules(kind, n1, inc1, n2, inc2, t_end):
     # displacement = rate x time at every step
     rate = S.PAPER_SCHEDULES[kind]["rate"]
     assert np.allclose(np.cumsum(inc), rate * t, rtol=1e-12)
+
+
+def test_schedule_table_matches_the_printed_values():
+    path = os.path.join(os.path.dirname(__file__), "golden", "loading_schedules.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert {r[0] for r in rows} == set(S.PAPER_SCHEDULES)
+    for kind, *vals in rows:
+        want = dict(zip(("rate", "dt1", "t1", "dt2", "t2"), map(float, vals)))
+        assert S.PAPER_SCHEDULES[kind] == pytest.approx(want, rel=1e-15)
 
 
 def test_specimens_take_the_schedule():
