@@ -203,6 +203,64 @@ const char *pf_status_string(pf_status s);
 void pf_destroy(pf_ctx *ctx);
 
 /* ------------------------------------------------------------------------------------
+ * Serving.  A continuous-batching request server on the calling thread's CUDA device:
+ * `slots` host worker threads each run one simulation at a time (pf_create, one
+ * pf_load_step per load increment, pf_destroy), so up to `slots` simulations are resident
+ * and their kernels overlap on the device, each on its own stream.  Requests are admitted
+ * first come, first served when a slot is free and their device footprint
+ * (pf_footprint_bytes) fits in `hbm_budget` minus the footprints of the running
+ * simulations; the queue head blocks the requests behind it.  The kernels are
+ * deterministic, so a request gives the same results alone and in the mix.  The paper has
+ * no serving layer; this is the request loop of the served-batch workload.
+ * ------------------------------------------------------------------------------------ */
+typedef struct pf_server pf_server;
+
+typedef struct {
+  pf_mesh mesh;                 /* as for pf_create; node_flags / elem_active copied */
+  double E, nu, Gc, l, k_res;   /* as for pf_create */
+  const double *increments;     /* host, n_steps load increments (copied at submit) */
+  int n_steps;                  /* >= 1 */
+  int scheme;                   /* PF_ST .. PF_S3 */
+  double tol;                   /* staggered tolerance of every step, > 0 */
+  const pf_options *options;    /* NULL: pf_default_options (copied at submit) */
+} pf_request;
+
+enum { PF_REQ_QUEUED = 0, PF_REQ_RUNNING = 1, PF_REQ_DONE = 2, PF_REQ_FAILED = 3 };
+
+typedef struct {
+  int state;           /* PF_REQ_* */
+  int status;          /* PF_OK, or the status of the call that failed (PF_REQ_FAILED);
+                          a step that hit a cap (PF_ENOTCONV) does not fail the request */
+  int steps_done;      /* load steps completed */
+  int steps_converged; /* of those, steps whose staggered residual met tol */
+  int64_t admit_seq;   /* 0-based admission order, -1 while queued */
+  size_t footprint;    /* device bytes reserved for the request */
+  double queue_ms;     /* submit -> admission (host clock) */
+  double path_ms;      /* submit -> completion (host clock), 0 until done */
+  double step_ms_p50;  /* device time per load step (pf_step_result.ms), over done steps */
+  double step_ms_p99;
+} pf_request_info;
+
+/* hbm_budget > 0 bytes, slots >= 1.  Errors: PF_EINVAL, PF_ENOMEM. */
+pf_status pf_server_create(size_t hbm_budget, int slots, pf_server **out);
+/* Queue a request; *id receives its id (>= 1).  PF_EINVAL for an invalid request or one
+ * whose footprint exceeds the whole budget; PF_EBUSY after pf_server_destroy began. */
+pf_status pf_server_submit(pf_server *s, const pf_request *req, int64_t *id);
+/* State of request `id`.  reactions (double) and stag_iters (int), each n_steps long or
+ * NULL, receive the per-step reaction force and staggered passes of the steps done so
+ * far.  PF_EINVAL for an unknown id. */
+pf_status pf_server_poll(pf_server *s, int64_t id, pf_request_info *info, double *reactions,
+                         int *stag_iters);
+/* Wait until no request is queued or running; PF_ETIMEOUT after timeout_s seconds
+ * (timeout_s < 0 waits without limit). */
+pf_status pf_server_drain(pf_server *s, double timeout_s);
+/* Peaks since creation: device bytes reserved and simulations running at once. */
+pf_status pf_server_stats(pf_server *s, size_t *peak_bytes, int *peak_running);
+/* Stop: requests still queued are not started; running ones finish their load path;
+ * the worker threads are joined and all memory freed. */
+void pf_server_destroy(pf_server *s);
+
+/* ------------------------------------------------------------------------------------
  * Operator level.  Stateless single operations on caller-owned DEVICE arrays, enqueued
  * on `stream` (a cudaStream_t, NULL = legacy default stream) and not synchronised
  * unless stated.  These are the building blocks of pf_load_step, exposed for checking

@@ -56,6 +56,26 @@ class StepResult(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Request(C.Structure):
+    _fields_ = [("mesh", Mesh), ("E", C.c_double), ("nu", C.c_double), ("Gc", C.c_double),
+                ("l", C.c_double), ("k_res", C.c_double), ("increments", C.c_void_p),
+                ("n_steps", C.c_int), ("scheme", C.c_int), ("tol", C.c_double),
+                ("options", C.c_void_p)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("state", C.c_int), ("status", C.c_int), ("steps_done", C.c_int),
+                ("steps_converged", C.c_int), ("admit_seq", C.c_int64),
+                ("footprint", C.c_size_t), ("queue_ms", C.c_double), ("path_ms", C.c_double),
+                ("step_ms_p50", C.c_double), ("step_ms_p99", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
+
 class Grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("hx", C.c_double), ("hy", C.c_double),
                 ("elem_active", C.c_void_p), ("dof_mask", C.c_void_p)]
@@ -91,6 +111,12 @@ _PROTOS = {
     "pf_profile": (S, [P, P, I, I]),
     "pf_last_error": (C.c_char_p, [P]),
     "pf_destroy": (None, [P]),
+    "pf_server_create": (S, [C.c_size_t, I, C.POINTER(P)]),
+    "pf_server_submit": (S, [P, C.POINTER(Request), C.POINTER(C.c_int64)]),
+    "pf_server_poll": (S, [P, C.c_int64, C.POINTER(RequestInfo), P, P]),
+    "pf_server_drain": (S, [P, D]),
+    "pf_server_stats": (S, [P, C.POINTER(C.c_size_t), C.POINTER(I)]),
+    "pf_server_destroy": (None, [P]),
     "pf_op_dof_mask": (S, [I, I, P, P, P, P]),
     "pf_op_elas_residual": (S, [C.POINTER(Grid), C.POINTER(Material), P, P, P, P, P]),
     "pf_op_elas_apply": (S, [C.POINTER(Grid), C.POINTER(Material), I, P, P, P, P, P]),
@@ -259,3 +285,68 @@ class Simulation:
 
     def __exit__(self, *a):
         self.close()
+
+
+class NativeServer:
+    """The library's request server (pf_server_*, include/pf.h): FIFO admission by device
+    footprint, one host worker thread per slot, each simulation on its own stream."""
+
+    def __init__(self, hbm_budget, slots):
+        p = P()
+        check(lib().pf_server_create(int(hbm_budget), int(slots), C.byref(p)),
+              "pf_server_create")
+        self.s = p
+        self._steps = {}
+
+    def submit(self, spec, scheme=ST, tol=1e-5, precision=FP64, precond=PRECOND_JACOBI,
+               model=AT2_HISTORY, tol_ir=0.01, split=SPLIT_VD, options=None):
+        flags = np.ascontiguousarray(spec.node_flags, dtype=np.uint8)
+        active = None
+        if spec.elem_active is not None and not np.all(spec.elem_active):
+            active = np.ascontiguousarray(spec.elem_active, dtype=np.uint8)
+        inc = np.ascontiguousarray(spec.increments, dtype=np.float64)
+        mesh = Mesh(spec.nx, spec.ny, spec.Lx, spec.Ly,
+                    active.ctypes.data if active is not None else None, flags.ctypes.data,
+                    spec.plane, precision, spec.reaction_dir, precond, model, tol_ir, split)
+        opt = None
+        if options:
+            opt = default_options()
+            for k, v in options.items():
+                setattr(opt, k, v)
+        req = Request(mesh, spec.E, spec.nu, spec.Gc, spec.l, spec.eta, inc.ctypes.data,
+                      len(inc), int(scheme), float(tol),
+                      C.addressof(opt) if opt is not None else None)
+        rid = C.c_int64()
+        check(lib().pf_server_submit(self.s, C.byref(req), C.byref(rid)), "pf_server_submit")
+        self._steps[rid.value] = len(inc)
+        return rid.value
+
+    def poll(self, rid):
+        n = self._steps[rid]
+        info = RequestInfo()
+        reactions = np.zeros(n)
+        iters = np.zeros(n, dtype=np.int32)
+        check(lib().pf_server_poll(self.s, rid, C.byref(info), reactions.ctypes.data,
+                                   iters.ctypes.data), "pf_server_poll")
+        out = info.as_dict()
+        out["reactions"] = reactions[:info.steps_done]
+        out["stag_iters"] = iters[:info.steps_done]
+        return out
+
+    def drain(self, timeout=-1.0):
+        """True when every submitted request has finished within ``timeout`` seconds."""
+        s = lib().pf_server_drain(self.s, float(timeout))
+        if s not in (PF_OK, PF_ETIMEOUT):
+            check(s, "pf_server_drain")
+        return s == PF_OK
+
+    def stats(self):
+        b = C.c_size_t()
+        r = I()
+        check(lib().pf_server_stats(self.s, C.byref(b), C.byref(r)), "pf_server_stats")
+        return {"peak_bytes": b.value, "peak_running": r.value}
+
+    def close(self):
+        if self.s:
+            lib().pf_server_destroy(self.s)
+            self.s = None

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpf.so")
-SOURCES = ["pf_ops.cu", "pf_vec.cu", "pf_gmg.cu", "pf_spectral.cu", "pf_solver.cu", "pf_api.cu"]
+SOURCES = ["pf_ops.cu", "pf_vec.cu", "pf_gmg.cu", "pf_spectral.cu", "pf_solver.cu", "pf_api.cu",
+           "pf_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include")]
 

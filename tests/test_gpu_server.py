@@ -50,3 +50,25 @@ def test_results_alone_and_in_the_mix_agree(gpu):
         assert np.array_equal(mixed.d, alone.d)
     steps, paths = server.latency_percentiles(srv.results)
     assert steps["p50"] > 0 and paths["p99"] >= paths["p50"] > 0
+
+
+def test_native_server_results_alone_and_in_the_mix_agree(gpu):
+    # the library's own request loop (pf_server_*): same mix, same bitwise agreement
+    reqs = _requests()
+    fps = [binding.footprint_bytes(r.spec, r.precision, r.precond) for _, r in reqs]
+    srv = binding.NativeServer(2 * max(fps), 3)
+    ids = [srv.submit(r.spec, scheme=r.scheme, tol=r.tol, precision=r.precision,
+                      precond=r.precond) for _, r in reqs]
+    assert srv.drain(600.0)
+    st = srv.stats()
+    assert 1 <= st["peak_running"] <= 3 and st["peak_bytes"] <= 2 * max(fps)
+    infos = [srv.poll(i) for i in ids]
+    srv.close()
+    assert sorted(x["admit_seq"] for x in infos) == list(range(len(reqs)))
+    for (_, r), x in zip(reqs, infos):
+        assert x["state"] == binding.REQ_DONE and x["status"] == binding.PF_OK
+        assert x["steps_done"] == len(r.spec.increments) >= x["steps_converged"]
+        assert x["step_ms_p99"] >= x["step_ms_p50"] > 0 and x["path_ms"] > 0
+        alone = server.run_path(server.Request(r.spec, r.scheme, r.precision, r.precond, r.tol))
+        assert list(x["reactions"]) == alone.reactions
+        assert list(x["stag_iters"]) == alone.stag_iters
