@@ -225,7 +225,13 @@ typedef struct {
   const pf_options *options;    /* NULL: pf_default_options (copied at submit) */
 } pf_request;
 
-enum { PF_REQ_QUEUED = 0, PF_REQ_RUNNING = 1, PF_REQ_DONE = 2, PF_REQ_FAILED = 3 };
+enum {
+  PF_REQ_QUEUED = 0,
+  PF_REQ_RUNNING = 1,
+  PF_REQ_DONE = 2,
+  PF_REQ_FAILED = 3,
+  PF_REQ_CANCELLED = 4   /* withdrawn while queued, or stopped between load steps */
+};
 
 typedef struct {
   int state;           /* PF_REQ_* */
@@ -256,8 +262,15 @@ pf_status pf_server_poll(pf_server *s, int64_t id, pf_request_info *info, double
 pf_status pf_server_drain(pf_server *s, double timeout_s);
 /* Peaks since creation: device bytes reserved and simulations running at once. */
 pf_status pf_server_stats(pf_server *s, size_t *peak_bytes, int *peak_running);
+/* Cancel request `id`: a queued request is withdrawn without being started; a running
+ * one stops after its current load step (its results so far stay readable).  PF_EINVAL
+ * for an unknown id; a finished request is left as it is. */
+pf_status pf_server_cancel(pf_server *s, int64_t id);
+/* paused != 0: admit no further requests (running ones continue); 0: resume admission. */
+pf_status pf_server_pause(pf_server *s, int paused);
 /* Stop: requests still queued are not started; running ones finish their load path;
- * the worker threads are joined and all memory freed. */
+ * the worker threads are joined and all memory freed.  No other pf_server_* call on `s`
+ * may be in progress or follow. */
 void pf_server_destroy(pf_server *s);
 
 /* ------------------------------------------------------------------------------------

@@ -73,7 +73,7 @@ class RequestInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 
 
 class Grid(C.Structure):
@@ -116,6 +116,8 @@ _PROTOS = {
     "pf_server_poll": (S, [P, C.c_int64, C.POINTER(RequestInfo), P, P]),
     "pf_server_drain": (S, [P, D]),
     "pf_server_stats": (S, [P, C.POINTER(C.c_size_t), C.POINTER(I)]),
+    "pf_server_cancel": (S, [P, C.c_int64]),
+    "pf_server_pause": (S, [P, I]),
     "pf_server_destroy": (None, [P]),
     "pf_op_dof_mask": (S, [I, I, P, P, P, P]),
     "pf_op_elas_residual": (S, [C.POINTER(Grid), C.POINTER(Material), P, P, P, P, P]),
@@ -345,6 +347,12 @@ class NativeServer:
         r = I()
         check(lib().pf_server_stats(self.s, C.byref(b), C.byref(r)), "pf_server_stats")
         return {"peak_bytes": b.value, "peak_running": r.value}
+
+    def cancel(self, rid):
+        check(lib().pf_server_cancel(self.s, rid), "pf_server_cancel")
+
+    def pause(self, paused=True):
+        check(lib().pf_server_pause(self.s, 1 if paused else 0), "pf_server_pause")
 
     def close(self):
         if self.s:

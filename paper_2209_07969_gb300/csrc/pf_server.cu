@@ -41,6 +41,7 @@ struct Request {
   // progress, guarded by the server mutex
   int state = PF_REQ_QUEUED;
   int status = PF_OK;
+  bool cancel = false;
   int64_t admit_seq = -1;
   std::vector<double> reactions, step_ms;
   std::vector<int> stag_iters;
@@ -60,7 +61,7 @@ struct pf_server {
   size_t in_use = 0, peak_in_use = 0;
   int running = 0, peak_running = 0;
   int64_t next_id = 1, next_admit = 0;
-  bool closing = false;
+  bool closing = false, paused = false;
   std::vector<std::thread> workers;
 };
 
@@ -72,8 +73,16 @@ void run_request(pf_server *s, Request *r) {
   pf_ctx *ctx = nullptr;
   pf_status st = pf_create(&r->mesh, r->E, r->nu, r->Gc, r->l, r->k_res, &ctx);
   if (st == PF_OK) st = pf_set_options(ctx, &r->opt);
+  bool stopped = false;
   if (st == PF_OK) {
     for (size_t k = 0; k < r->increments.size(); ++k) {
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (r->cancel) {
+          stopped = true;
+          break;
+        }
+      }
       pf_step_result res{};
       const pf_status ss = pf_load_step(ctx, r->increments[k], r->scheme, r->tol, &res);
       if (ss != PF_OK && ss != PF_ENOTCONV) {
@@ -90,7 +99,7 @@ void run_request(pf_server *s, Request *r) {
   if (ctx) pf_destroy(ctx);
   std::lock_guard<std::mutex> lk(s->mu);
   r->status = st;
-  r->state = st == PF_OK ? PF_REQ_DONE : PF_REQ_FAILED;
+  r->state = st != PF_OK ? PF_REQ_FAILED : stopped ? PF_REQ_CANCELLED : PF_REQ_DONE;
   r->t_end = Clock::now();
 }
 
@@ -101,7 +110,8 @@ void worker(pf_server *s) {
       std::unique_lock<std::mutex> lk(s->mu);
       for (;;) {
         if (s->closing) return;
-        if (!s->queue.empty() && s->in_use + s->queue.front()->footprint <= s->budget) {
+        if (!s->paused && !s->queue.empty() &&
+            s->in_use + s->queue.front()->footprint <= s->budget) {
           r = s->queue.front();
           s->queue.pop_front();
           s->in_use += r->footprint;
@@ -201,11 +211,12 @@ pf_status pf_server_submit(pf_server *s, const pf_request *req, int64_t *id) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->closing) return PF_EBUSY;
-    r->id = s->next_id++;
+    const int64_t rid = s->next_id++;
+    r->id = rid;
     r->t_submit = Clock::now();
-    *id = r->id;
+    *id = rid;
     s->queue.push_back(r.get());
-    s->reqs[r->id] = std::move(r);
+    s->reqs[rid] = std::move(r);
   }
   s->cv.notify_all();
   return PF_OK;
@@ -228,7 +239,7 @@ pf_status pf_server_poll(pf_server *s, int64_t id, pf_request_info *info, double
     info->footprint = r.footprint;
     info->queue_ms = r.state == PF_REQ_QUEUED ? ms_between(r.t_submit, now)
                                               : ms_between(r.t_submit, r.t_start);
-    const bool done = r.state == PF_REQ_DONE || r.state == PF_REQ_FAILED;
+    const bool done = r.state >= PF_REQ_DONE;   // done, failed or cancelled
     info->path_ms = done ? ms_between(r.t_submit, r.t_end) : 0.0;
     info->step_ms_p50 = percentile(r.step_ms, 0.5);
     info->step_ms_p99 = percentile(r.step_ms, 0.99);
@@ -258,6 +269,35 @@ pf_status pf_server_stats(pf_server *s, size_t *peak_bytes, int *peak_running) {
   std::lock_guard<std::mutex> lk(s->mu);
   if (peak_bytes) *peak_bytes = s->peak_in_use;
   if (peak_running) *peak_running = s->peak_running;
+  return PF_OK;
+}
+
+pf_status pf_server_cancel(pf_server *s, int64_t id) {
+  if (!s) return PF_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return PF_EINVAL;
+    Request *r = it->second.get();
+    if (r->state == PF_REQ_QUEUED) {
+      s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r));
+      r->state = PF_REQ_CANCELLED;
+      r->t_start = r->t_end = Clock::now();
+    } else if (r->state == PF_REQ_RUNNING) {
+      r->cancel = true;
+    }
+  }
+  s->cv.notify_all();
+  return PF_OK;
+}
+
+pf_status pf_server_pause(pf_server *s, int paused) {
+  if (!s) return PF_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->paused = paused != 0;
+  }
+  s->cv.notify_all();
   return PF_OK;
 }
 

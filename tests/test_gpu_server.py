@@ -72,3 +72,21 @@ def test_native_server_results_alone_and_in_the_mix_agree(gpu):
         alone = server.run_path(server.Request(r.spec, r.scheme, r.precision, r.precond, r.tol))
         assert list(x["reactions"]) == alone.reactions
         assert list(x["stag_iters"]) == alone.stag_iters
+
+
+def test_native_server_cancels_a_running_request_between_steps(gpu):
+    sp = S.tensile(32, l=0.06, steps=400, u_max=6e-3)
+    srv = binding.NativeServer(1 << 36, 1)
+    rid = srv.submit(sp, scheme=binding.S1, tol=1e-6)
+    import time
+    for _ in range(600):                        # wait until it has run a few steps
+        if srv.poll(rid)["steps_done"] >= 3:
+            break
+        time.sleep(0.01)
+    srv.cancel(rid)
+    assert srv.drain(120.0)
+    x = srv.poll(rid)
+    srv.close()
+    assert x["state"] == binding.REQ_CANCELLED and x["status"] == binding.PF_OK
+    assert 3 <= x["steps_done"] < 400
+    assert len(x["reactions"]) == x["steps_done"]

@@ -73,3 +73,29 @@ def test_destroy_with_queued_requests_returns():
     for _ in range(5):
         srv.submit(sp)
     srv.close()          # queued requests are dropped, the running one finishes
+
+
+def test_pause_and_cancel_of_queued_requests():
+    sp = _spec()
+    srv = binding.NativeServer(1 << 40, 2)
+    try:
+        srv.pause()
+        ids = [srv.submit(sp) for _ in range(4)]
+        srv.cancel(ids[1])
+        srv.cancel(ids[3])
+        info = srv.poll(ids[0])
+        assert info["state"] == binding.REQ_QUEUED and info["admit_seq"] == -1
+        assert srv.poll(ids[1])["state"] == binding.REQ_CANCELLED
+        assert not srv.drain(0.2)               # paused with requests queued
+        srv.pause(False)
+        assert srv.drain(60.0)
+        seq = [srv.poll(i)["admit_seq"] for i in ids]
+        assert seq[0] == 0 and seq[2] == 1 and seq[1] == seq[3] == -1
+        assert srv.poll(ids[3])["state"] == binding.REQ_CANCELLED
+        assert srv.poll(ids[3])["path_ms"] >= 0.0
+        with pytest.raises(binding.PfError):
+            srv.cancel(999)
+        srv.cancel(ids[0])                      # finished: left as it is
+        assert srv.poll(ids[0])["state"] in (binding.REQ_DONE, binding.REQ_FAILED)
+    finally:
+        srv.close()
