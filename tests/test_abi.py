@@ -65,3 +65,39 @@ def test_create_rejects_bad_mesh_without_touching_the_gpu(L):
     mesh = binding.Mesh(0, 4, 1.0, 1.0, None, None, 0, 0, 1, 0)
     assert L.pf_create(ctypes.byref(mesh), 210.0, 0.3, 1e-3, 0.1, 0.0, ctypes.byref(out)) == binding.PF_EINVAL
     assert not out.value
+
+
+def test_create_rejects_bad_model_and_split(L):
+    out = ctypes.c_void_p()
+    flags = (ctypes.c_uint8 * 25)()
+    for model, split in ((5, 0), (0, 2), (0, -1)):
+        mesh = binding.Mesh(4, 4, 1.0, 1.0, None, ctypes.addressof(flags), 0, 0, 1, 0, model,
+                            0.0, split)
+        assert L.pf_create(ctypes.byref(mesh), 210.0, 0.3, 1e-3, 0.1, 0.0,
+                           ctypes.byref(out)) == binding.PF_EINVAL
+        assert not out.value
+
+
+def test_footprint_of_the_spectral_split(L):
+    # the spectral split adds per-point stress and tangent (9 doubles per point) and the
+    # nodal stencil of the tangent (36 values per node, FP64 and, in FP32-IR, FP32)
+    nx, ny = 30, 20
+    nn, nq = (nx + 1) * (ny + 1), 4 * nx * ny
+    for prec, extra in ((binding.FP64, 0), (binding.FP32_IR, 36 * nn * 4)):
+        vals = []
+        for split in (binding.SPLIT_VD, binding.SPLIT_SPECTRAL):
+            mesh = binding.Mesh(nx, ny, 1.0, 1.0, None, 1, 0, prec, 1, binding.PRECOND_GMG, 0,
+                                0.0, split)
+            vals.append(L.pf_footprint_bytes(ctypes.byref(mesh)))
+        assert vals[1] - vals[0] == 9 * nq * 8 + 36 * nn * 8 + extra
+
+
+def test_operator_calls_reject_an_unknown_split(L):
+    g = binding.grid(4, 4, 0.25, 0.25)
+    m = binding.material(210.0, 0.3, 2.7e-3, 0.03, 1e-9, 0)
+    m.split = 3
+    fake = ctypes.c_void_p(16)                  # never dereferenced: validation comes first
+    assert L.pf_op_qp_energy(ctypes.byref(g), ctypes.byref(m), fake, fake, None, fake,
+                             None) == binding.PF_EINVAL
+    assert L.pf_op_elas_tangent_qp(ctypes.byref(g), ctypes.byref(m), fake, fake, fake,
+                                   None) == binding.PF_EINVAL
