@@ -20,7 +20,8 @@
 // The VD tangent is fixed by one sign bit per point, so it is applied matrix-free.  The
 // spectral tangent depends on the whole strain: the u-solves assemble the per-point
 // tangents into the nodal stencil of the multigrid hierarchy (9 neighbours x 2 x 2 blocks)
-// and apply that, reading 36 values per node where the matrix-free VD operator reads 2.
+// and apply that: 36 stencil values per node on top of the operand and the product, where
+// the matrix-free VD operator reads only d and one sign byte per element besides them.
 #include <math.h>
 
 #include "pf_fused.cuh"
