@@ -121,3 +121,22 @@ def test_dirichlet_values_held():
     assert np.array_equal(st.u[cu], g.u_dirichlet_values(st.ubar)[cu])
     cd = g.d_constrained()
     assert np.array_equal(st.d[cd], g.d_dirichlet_values()[cd])
+
+
+def test_tensile_pass_ranking_of_sec_4_1():
+    # Sec. 4.1 ranks the maximum number of staggered iterations per load step in the
+    # tensile test as ST > S1 > S2 > S3.  Checker on a 24 x 24 notched square through the
+    # crack (TOL_ST 1e-8): 104, 67, 66, 59.  S1 and S2 differ by one pass here, so the
+    # check keeps the robust part: ST well above every fixed-stress scheme, S3 lowest.
+    sp = S.tensile(24, l=0.08, steps=6, u_max=8e-3)
+    g, m = _grid(sp), _mat(sp)
+    mx, tot = {}, {}
+    for scheme in (model.ST, model.S1, model.S2, model.S3):
+        res, _ = stg.load_path(g, m, sp.increments, scheme, stg.Options(tol_st=1e-8), 1)
+        assert all(r.converged for r in res)
+        mx[scheme] = max(r.stag_iters for r in res)
+        tot[scheme] = sum(r.stag_iters for r in res)
+    s_schemes = (model.S1, model.S2, model.S3)
+    assert mx[model.ST] > 1.3 * max(mx[s] for s in s_schemes)
+    assert mx[model.S3] < min(mx[model.S1], mx[model.S2])
+    assert tot[model.ST] > max(tot[s] for s in s_schemes)
