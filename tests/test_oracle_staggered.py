@@ -140,3 +140,18 @@ def test_tensile_pass_ranking_of_sec_4_1():
     assert mx[model.ST] > 1.3 * max(mx[s] for s in s_schemes)
     assert mx[model.S3] < min(mx[model.S1], mx[model.S2])
     assert tot[model.ST] > max(tot[s] for s in s_schemes)
+
+
+def test_converged_states_agree_across_schemes_before_the_crack():
+    # The schemes change only the iteration, not the equations: before the crack forms
+    # the converged states of S1/S2/S3 equal the ST state to the staggered tolerance.
+    sp = S.tensile(24, l=0.08, steps=6, u_max=8e-3)
+    g, m = _grid(sp), _mat(sp)
+    opts = stg.Options(tol_st=1e-11, tol_nr=1e-11)
+    ref, st_ref = stg.load_path(g, m, sp.increments[:3], model.ST, opts, 1)
+    for scheme in (model.S1, model.S2, model.S3):
+        res, st = stg.load_path(g, m, sp.increments[:3], scheme, opts, 1)
+        for a, b in zip(res, ref):
+            assert a.reaction == pytest.approx(b.reaction, rel=1e-9)
+        assert np.max(np.abs(st.d - st_ref.d)) < 1e-9
+        assert np.allclose(st.H, st_ref.H, rtol=1e-8, atol=1e-14)
