@@ -150,8 +150,11 @@ def test_exact_newton_corrections_match_checker(gpu):
 @pytest.mark.parametrize("precond", PRECONDS)
 @pytest.mark.parametrize("scheme", [0, 1, 3])
 def test_tensile_path_fp32_refined(gpu, scheme, precond):
+    # At the crack step the iteration passes an unstable equilibrium whose residual minimum
+    # (2-5e-7 in the checker on x86) is set by rounding; at a tolerance of 1e-7 either code
+    # may stop there on another machine.  1e-9 lies two orders below (reading R25).
     spec = S.tensile(SMALL["n"], l=SMALL["l"], steps=SMALL["steps"], u_max=SMALL["u_max"])
-    g, m, out = _run_both(spec, scheme, tol=1e-7, precision=binding.FP32_IR, tol_lin=1e-10,
+    g, m, out = _run_both(spec, scheme, tol=1e-9, precision=binding.FP32_IR, tol_lin=1e-12,
                           precond=precond)
     Fr = np.array([o[0].reaction for o in out])
     Fg = np.array([o[1]["reaction"] for o in out])
