@@ -184,22 +184,30 @@ def test_s3_prediction_holds_the_stress_in_tension():
     assert np.all((ratio > 3.5) & (ratio < 4.5)), ratio
 
 
-def _bar_closed_form(split, eyy, Gc, l, eta):
-    """Homogeneous plane-strain bar with free sides at axial strain eyy (AT2, monotone):
-    (d, sigma_yy) from sigma_xx = 0 and d = 2 Psi+ / (G_c/l + 2 Psi+)."""
+def _bar_closed_form(split, eyy, Gc, l, eta, plane=model.PLANE_STRAIN):
+    """Homogeneous bar with free sides at axial strain eyy (AT2, monotone): (d, sigma_yy)
+    from sigma_xx = 0 and d = 2 Psi+ / (G_c/l + 2 Psi+).  Plane strain: Lame constant
+    LAM, 3D bulk modulus; plane stress: lam* = E nu / (1 - nu^2), K2 = E / (2 (1 - nu))
+    (2D invariants)."""
+    E, nu = model.E_nu_from_lame(LAM, MU)
+    if plane == model.PLANE_STRAIN:
+        lam, K, c = LAM, LAM + 2 * MU / 3, 1.0 / 3.0
+    else:
+        lam, K, c = E * nu / (1 - nu ** 2), E / (2 * (1 - nu)), 0.5
+
     def state(d):
         gd = (1 - d) ** 2 + eta
         if split == model.SPECTRAL:
-            exx = -gd * LAM * eyy / (gd * LAM + 2 * MU)
+            exx = -gd * lam * eyy / (gd * lam + 2 * MU)
             tr = exx + eyy
-            psi = 0.5 * LAM * tr ** 2 + MU * eyy ** 2
-            syy = gd * (LAM * tr + 2 * MU * eyy)
+            psi = 0.5 * lam * tr ** 2 + MU * eyy ** 2
+            syy = gd * (lam * tr + 2 * MU * eyy)
         else:
-            exx = -LAM * eyy / (LAM + 2 * MU)
+            # sigma_xx = g [2 mu (e_xx - c tr) + K tr] = 0
+            exx = -(K - 2 * MU * c) * eyy / (2 * MU * (1 - c) + K)
             tr = exx + eyy
-            K = LAM + 2 * MU / 3
-            psi = MU * (exx ** 2 + eyy ** 2 - tr ** 2 / 3) + 0.5 * K * tr ** 2
-            syy = gd * (LAM * tr + 2 * MU * eyy)
+            psi = MU * (exx ** 2 + eyy ** 2 - c * tr ** 2) + 0.5 * K * tr ** 2
+            syy = gd * (2 * MU * (eyy - c * tr) + K * tr)
         return psi, syy
 
     f = lambda d: d * (Gc / l + 2 * state(d)[0]) - 2 * state(d)[0]
@@ -207,12 +215,14 @@ def _bar_closed_form(split, eyy, Gc, l, eta):
     return d, state(d)[1]
 
 
+@pytest.mark.parametrize("plane", [model.PLANE_STRAIN, model.PLANE_STRESS])
 @pytest.mark.parametrize("split", [model.VD, model.SPECTRAL])
 @pytest.mark.parametrize("scheme", [model.ST, model.S1, model.S3])
-def test_free_sided_bar_closed_form(split, scheme):
+def test_free_sided_bar_closed_form(split, scheme, plane):
     Gc, l, eta = 2.7e-3, 0.03, 1e-9
     sp = S.uniaxial_stress_bar(3, 4, Lx=0.5, Ly=1.0, Gc=Gc, l=l, eta=eta, steps=5,
                                u_max=1.1e-2)
+    sp.plane = plane
     g = q1.Grid(sp.nx, sp.ny, sp.Lx, sp.Ly, sp.node_flags, sp.elem_active)
     m = model.material_from_E_nu(sp.E, sp.nu, Gc, l, eta, sp.plane, split)
     st = stg.State(g)
@@ -220,7 +230,7 @@ def test_free_sided_bar_closed_form(split, scheme):
     for du in sp.increments:
         r = stg.load_step(g, m, st, du, scheme, opts, reaction_dir=1)
         assert r.converged
-        d_ex, syy = _bar_closed_form(split, st.ubar / sp.Ly, Gc, l, eta)
+        d_ex, syy = _bar_closed_form(split, st.ubar / sp.Ly, Gc, l, eta, plane)
         assert np.allclose(st.d, d_ex, rtol=1e-8, atol=1e-10)
         assert r.reaction == pytest.approx(syy * sp.Lx, rel=1e-7)
     # the path ends just before the peak of the homogeneous response (past it, under
