@@ -266,6 +266,9 @@ pf_status pf_server_stats(pf_server *s, size_t *peak_bytes, int *peak_running);
  * one stops after its current load step (its results so far stay readable).  PF_EINVAL
  * for an unknown id; a finished request is left as it is. */
 pf_status pf_server_cancel(pf_server *s, int64_t id);
+/* Forget a finished (done, failed or cancelled) request and free its results; later
+ * calls with `id` return PF_EINVAL.  PF_EBUSY while it is queued or running. */
+pf_status pf_server_release(pf_server *s, int64_t id);
 /* paused != 0: admit no further requests (running ones continue); 0: resume admission. */
 pf_status pf_server_pause(pf_server *s, int paused);
 /* Stop: requests still queued are not started; running ones finish their load path;

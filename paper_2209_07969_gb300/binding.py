@@ -118,6 +118,7 @@ _PROTOS = {
     "pf_server_stats": (S, [P, C.POINTER(C.c_size_t), C.POINTER(I)]),
     "pf_server_cancel": (S, [P, C.c_int64]),
     "pf_server_pause": (S, [P, I]),
+    "pf_server_release": (S, [P, C.c_int64]),
     "pf_server_destroy": (None, [P]),
     "pf_op_dof_mask": (S, [I, I, P, P, P, P]),
     "pf_op_elas_residual": (S, [C.POINTER(Grid), C.POINTER(Material), P, P, P, P, P]),
@@ -324,6 +325,8 @@ class NativeServer:
         return rid.value
 
     def poll(self, rid):
+        if rid not in self._steps:
+            check(PF_EINVAL, f"pf_server_poll: unknown request {rid}")
         n = self._steps[rid]
         info = RequestInfo()
         reactions = np.zeros(n)
@@ -350,6 +353,11 @@ class NativeServer:
 
     def cancel(self, rid):
         check(lib().pf_server_cancel(self.s, rid), "pf_server_cancel")
+
+    def release(self, rid):
+        """Free a finished request's record (its id becomes unknown)."""
+        check(lib().pf_server_release(self.s, rid), "pf_server_release")
+        self._steps.pop(rid, None)
 
     def pause(self, paused=True):
         check(lib().pf_server_pause(self.s, 1 if paused else 0), "pf_server_pause")

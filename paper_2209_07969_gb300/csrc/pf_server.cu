@@ -4,7 +4,8 @@
 // head's device footprint fits in the budget left by the running simulations, runs its
 // whole load path on its own pf_ctx (own CUDA stream), and returns the reserved bytes.
 // The head blocks the queue (first come, first served).  Per-request results (reaction and
-// staggered passes per step, device time per step) are kept until the server is destroyed.
+// staggered passes per step, device time per step) are kept until the request is released
+// or the server destroyed.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -288,6 +289,16 @@ pf_status pf_server_cancel(pf_server *s, int64_t id) {
     }
   }
   s->cv.notify_all();
+  return PF_OK;
+}
+
+pf_status pf_server_release(pf_server *s, int64_t id) {
+  if (!s) return PF_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return PF_EINVAL;
+  if (it->second->state < PF_REQ_DONE) return PF_EBUSY;
+  s->reqs.erase(it);
   return PF_OK;
 }
 

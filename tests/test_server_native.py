@@ -99,3 +99,25 @@ def test_pause_and_cancel_of_queued_requests():
         assert srv.poll(ids[0])["state"] in (binding.REQ_DONE, binding.REQ_FAILED)
     finally:
         srv.close()
+
+
+def test_release_of_finished_requests():
+    sp = _spec()
+    srv = binding.NativeServer(1 << 40, 1)
+    try:
+        srv.pause()
+        a, b = srv.submit(sp), srv.submit(sp)
+        with pytest.raises(binding.PfError) as e:
+            srv.release(a)                      # still queued
+        assert e.value.status == binding.PF_EBUSY
+        srv.cancel(b)
+        srv.release(b)                          # cancelled counts as finished
+        with pytest.raises(binding.PfError):
+            srv.poll(b)
+        srv.pause(False)
+        assert srv.drain(60.0)
+        srv.release(a)
+        with pytest.raises(binding.PfError):
+            srv.release(a)
+    finally:
+        srv.close()
