@@ -101,3 +101,55 @@ def test_at1_fixed_stress_equals_standard_without_softening(scheme):
         out.append(([r.reaction for r in res], [r.stag_iters for r in res], st.d))
     (Fa, ka, da), (Fb, kb, db) = out
     assert Fa == Fb and ka == kb and np.array_equal(da, db)
+
+
+@pytest.mark.parametrize("split", [model.VD, model.SPECTRAL])
+@pytest.mark.parametrize("scheme", [model.ST, model.S1])
+def test_at1_free_sided_bar_both_splits(split, scheme):
+    # Free sides: the lateral strain follows from sigma_xx = 0 and, for the spectral split,
+    # depends on d; the homogeneous state solves the scalar stationarity equation
+    # -2 (1-d) Psi+(d) + a + gamma <d - d_{n-1}>_- = 0 at every step (below the elastic
+    # limit Psi+ = a/2 the penalty holds d slightly below d_{n-1} = 0).  Past the limit the
+    # AT1 bar softens at once and the homogeneous state is unstable under displacement
+    # control: with the spectral split the checker localizes in the first damaging step
+    # (a band with d = 1, also a solution), with VD it stays homogeneous for a few steps.
+    # The path therefore stops below the limit for the spectral split and four steps past
+    # it for VD.
+    lam, mu, Gc, l, eta = 121.15, 80.77, 2.7e-3, 0.03, 1e-9
+    from scipy.optimize import brentq
+    u_max, steps = (1.8e-2, 12) if split == model.VD else (1.2e-2, 8)
+    sp = S.uniaxial_stress_bar(3, 4, Lx=0.5, Ly=1.0, lam=lam, mu=mu, Gc=Gc, l=l, eta=eta,
+                               steps=steps, u_max=u_max)
+    g = _grid(sp)
+    m = model.material_from_E_nu(sp.E, sp.nu, Gc, l, eta, sp.plane, split)
+    a, _, gamma = model.at1_constants(m, 0.01)
+
+    def psi_syy(d, eyy):
+        gd = (1 - d) ** 2 + eta
+        if split == model.SPECTRAL:
+            exx = -gd * lam * eyy / (gd * lam + 2 * mu)
+            tr = exx + eyy
+            return 0.5 * lam * tr ** 2 + mu * eyy ** 2, gd * (lam * tr + 2 * mu * eyy)
+        exx = -lam * eyy / (lam + 2 * mu)
+        tr = exx + eyy
+        K = lam + 2 * mu / 3
+        return (mu * (exx ** 2 + eyy ** 2 - tr ** 2 / 3) + 0.5 * K * tr ** 2,
+                gd * (lam * tr + 2 * mu * eyy))
+
+    opts = stg.Options(tol_st=1e-11, tol_nr=1e-11, max_stag=400, model=model.AT1, tol_ir=0.01)
+    st = stg.State(g)
+    d_prev = 0.0
+    for du in sp.increments:
+        r = stg.load_step(g, m, st, du, scheme, opts, reaction_dir=1)
+        assert r.converged
+        eyy = st.ubar / sp.Ly
+        f = lambda d: (-2 * (1 - d) * psi_syy(d, eyy)[0] + a
+                       + gamma * min(d - d_prev, 0.0))
+        d_ex = brentq(f, -0.5, 1 - 1e-12, xtol=1e-15, rtol=1e-15)
+        assert np.allclose(st.d, d_ex, rtol=1e-8, atol=1e-10)
+        assert r.reaction == pytest.approx(psi_syy(d_ex, eyy)[1] * sp.Lx, rel=1e-7)
+        d_prev = d_ex
+    if split == model.VD:
+        assert d_prev > 0.4                    # four damaging steps
+    else:
+        assert -1e-3 < d_prev < 0.0            # penalty branch just below the limit
