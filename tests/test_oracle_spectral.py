@@ -217,7 +217,7 @@ def _bar_closed_form(split, eyy, Gc, l, eta, plane=model.PLANE_STRAIN):
 
 @pytest.mark.parametrize("plane", [model.PLANE_STRAIN, model.PLANE_STRESS])
 @pytest.mark.parametrize("split", [model.VD, model.SPECTRAL])
-@pytest.mark.parametrize("scheme", [model.ST, model.S1, model.S3])
+@pytest.mark.parametrize("scheme", [model.ST, model.S1, model.S2, model.S3])
 def test_free_sided_bar_closed_form(split, scheme, plane):
     Gc, l, eta = 2.7e-3, 0.03, 1e-9
     sp = S.uniaxial_stress_bar(3, 4, Lx=0.5, Ly=1.0, Gc=Gc, l=l, eta=eta, steps=5,
