@@ -761,6 +761,7 @@ cudaError_t gmg_alloc(Gmg<T> &G, int nx, int ny, int B, const RedWs &ws) {
     L.ny = cy;
     L.nn = (size_t)(cx + 1) * (cy + 1);
     const size_t nb = (size_t)B * L.nn;
+    G.nl = l + 1;   // gmg_free releases a partly allocated hierarchy up to this level
     cudaError_t e;
     if ((e = cudaMalloc(&L.S, 9 * B * B * L.nn * sizeof(T))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&L.invd, nb * sizeof(T))) != cudaSuccess) return e;
@@ -800,7 +801,8 @@ size_t gmg_bytes(int nx, int ny, int B, size_t tsize) {
   size_t last_nn = 0;
   while (true) {
     const size_t nn = (size_t)(cx + 1) * (cy + 1);
-    total += 9 * B * B * nn * tsize + 5 * B * nn * tsize + nn + sizeof(double) + 4 * tsize;
+    // stencil, six B-vectors (invd, x, b, r, dv, y), mask, bound, coefficients
+    total += 9 * B * B * nn * tsize + 6 * B * nn * tsize + nn + sizeof(double) + 4 * tsize;
     last_nn = nn;
     ++l;
     if ((cx <= GMG_COARSE_MAX && cy <= GMG_COARSE_MAX) || l == GMG_MAX_LEVELS) break;

@@ -68,8 +68,15 @@ struct pf_server {
 
 namespace {
 
-// Run one request's load path on the worker's thread (no lock held).
-void run_request(pf_server *s, Request *r) {
+// Run one request's load path on the worker's thread (no lock held).  The final state is
+// returned, not published: the worker publishes it in the same critical section that
+// returns the request's footprint, because a client may release a finished request (and
+// free its record) as soon as it sees the final state.
+struct Outcome {
+  int state, status;
+};
+
+Outcome run_request(pf_server *s, Request *r) {
   cudaSetDevice(s->device);
   pf_ctx *ctx = nullptr;
   pf_status st = pf_create(&r->mesh, r->E, r->nu, r->Gc, r->l, r->k_res, &ctx);
@@ -98,10 +105,7 @@ void run_request(pf_server *s, Request *r) {
     }
   }
   if (ctx) pf_destroy(ctx);
-  std::lock_guard<std::mutex> lk(s->mu);
-  r->status = st;
-  r->state = st != PF_OK ? PF_REQ_FAILED : stopped ? PF_REQ_CANCELLED : PF_REQ_DONE;
-  r->t_end = Clock::now();
+  return {st != PF_OK ? PF_REQ_FAILED : stopped ? PF_REQ_CANCELLED : PF_REQ_DONE, (int)st};
 }
 
 void worker(pf_server *s) {
@@ -127,11 +131,15 @@ void worker(pf_server *s) {
         s->cv.wait(lk);
       }
     }
-    run_request(s, r);
+    const Outcome o = run_request(s, r);
     {
+      // r may be released by a client right after this block: nothing touches it later
       std::lock_guard<std::mutex> lk(s->mu);
       s->in_use -= r->footprint;
       s->running -= 1;
+      r->status = o.status;
+      r->state = o.state;
+      r->t_end = Clock::now();
     }
     s->cv.notify_all();
   }

@@ -90,3 +90,28 @@ def test_native_server_cancels_a_running_request_between_steps(gpu):
     assert x["state"] == binding.REQ_CANCELLED and x["status"] == binding.PF_OK
     assert 3 <= x["steps_done"] < 400
     assert len(x["reactions"]) == x["steps_done"]
+
+
+@pytest.mark.parametrize("n,precision,precond,split", [
+    (512, binding.FP32_IR, binding.PRECOND_GMG, binding.SPLIT_VD),
+    (512, binding.FP64, binding.PRECOND_GMG, binding.SPLIT_VD),
+    (1024, binding.FP32_IR, binding.PRECOND_GMG, binding.SPLIT_VD),
+    (512, binding.FP64, binding.PRECOND_JACOBI, binding.SPLIT_VD),
+    (256, binding.FP32_IR, binding.PRECOND_GMG, binding.SPLIT_SPECTRAL),
+])
+def test_footprint_bounds_the_device_allocation(gpu, n, precision, precond, split):
+    # The server admits requests by pf_footprint_bytes, so the formula must not undercount
+    # what pf_create takes from the device (nor overcount it grossly).  cudaMemGetInfo
+    # moves in 2 MiB pages; the slack covers that rounding.
+    import torch
+    spec = S.tensile(n, l=4.0 / n)
+    fp = binding.footprint_bytes(spec, precision, precond, split=split)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    sim = binding.Simulation(spec, precision=precision, precond=precond, split=split)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    sim.close()
+    used = free0 - free1
+    assert used <= fp + (8 << 20), (used, fp)
+    assert used >= 0.8 * fp - (8 << 20), (used, fp)

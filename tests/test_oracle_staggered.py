@@ -155,3 +155,63 @@ def test_converged_states_agree_across_schemes_before_the_crack():
             assert a.reaction == pytest.approx(b.reaction, rel=1e-9)
         assert np.max(np.abs(st.d - st_ref.d)) < 1e-9
         assert np.allclose(st.H, st_ref.H, rtol=1e-8, atol=1e-14)
+
+
+def _one_element(flags=None, Lx=1.0):
+    g = q1.Grid(1, 1, Lx, 1.0, flags)
+    # plane strain, mu = 1, lambda = 2 (K = lambda + 2 mu / 3), G_c = l = 1
+    m = model.Material(1.0, 2.0 + 2.0 / 3.0, 1.0, 1.0, 1e-9, 1.0 / 3.0)
+    return g, m
+
+
+def _uniaxial_u(g, eps):
+    # u_x = eps x, u_y = 0: eps_xx = eps everywhere, tension, Psi+ = (lambda/2 + mu) eps^2
+    x = np.tile(np.arange(g.nx + 1) * g.hx, g.ny + 1)
+    u = np.zeros(2 * g.nn)
+    u[0::2] = eps * x
+    return u
+
+
+def test_stag_residual_on_one_element_by_hand():
+    # Unit square, one element, nodes (0,0), (1,0), (0,1), (1,1).  eps = 1/2 gives
+    # Psi+ = 2 eps^2 = 1/2 at every Gauss point; with H_{n-1} = 0 the coefficient is
+    # G_c/l + 2H = 2.  The Q1 matrices of the unit square are the Kronecker products of
+    # the 1D linear element's mass m1 = [[2,1],[1,2]]/6 and stiffness k1 = [[1,-1],[-1,1]],
+    # so K_dd = 2 m1(x)m1 + k1(x)m1 + m1(x)k1 has the rows
+    #   [ 8/9, -1/18, -1/18, -5/18 ] and its permutations, diagonal 8/9,
+    # and the right-hand side int 2H N_i = 2 (1/2) (1/4) = 1/4.  For d = (0, .2, .4, .6):
+    # K d - b = (-0.45, -13/60, 1/60, 1/4), divided by 8/9:
+    # (-0.50625, -0.24375, 0.01875, 0.28125).
+    g, m = _one_element()
+    u = _uniaxial_u(g, 0.5)
+    d = np.array([0.0, 0.2, 0.4, 0.6])
+    H0 = np.zeros((1, 4))
+    assert stg.stag_residual(g, m, u, d, H0) == pytest.approx(0.50625, rel=1e-13)
+    # node 0 held (D_FIX0): the maximum over the free DOFs is node 3's
+    g0, _ = _one_element(np.array([q1.D_FIX0, 0, 0, 0], np.uint8))
+    assert stg.stag_residual(g0, m, u, d, H0) == pytest.approx(0.28125, rel=1e-13)
+    # a committed history above Psi+ wins the max: H = 1 gives coefficient 3, rhs 1/2,
+    # diagonal 3 (4/36) + 2/3 = 1, row 0 of K = [1, 3(2/36) - 1/6, 3(2/36) - 1/6, 3/36 - 1/3]
+    # = [1, 0, 0, -1/4]: R_0 = -0.15 - 0.5 = -0.65 over the diagonal 1
+    H1 = np.ones((1, 4))
+    assert stg.stag_residual(g, m, u, d, H1) == pytest.approx(0.65, rel=1e-13)
+    # a history below Psi+ is ignored
+    assert stg.stag_residual(g, m, u, d, 0.25 * H1) == pytest.approx(0.50625, rel=1e-13)
+
+
+def test_stag_residual_on_a_stretched_element():
+    # hx = 2, hy = 1: mass m1x (x) m1y with m1x = 2 m1, stiffness k1x (x) m1y + m1x (x) k1y
+    # with k1x = k1 / 2 (ordering: x fastest, so the y factor is the outer one).
+    g, m = _one_element(Lx=2.0)
+    eps = 0.3
+    u = _uniaxial_u(g, eps)
+    psi = 2.0 * eps ** 2
+    m1 = np.array([[2.0, 1.0], [1.0, 2.0]]) / 6.0
+    k1 = np.array([[1.0, -1.0], [-1.0, 1.0]])
+    M = np.kron(m1, 2.0 * m1)
+    G = np.kron(m1, 0.5 * k1) + np.kron(k1, 2.0 * m1)
+    K = (1.0 + 2.0 * psi) * M + G
+    b = 2.0 * psi * 2.0 / 4.0 * np.ones(4)
+    d = np.array([0.1, 0.7, 0.3, 0.05])
+    want = np.max(np.abs((K @ d - b) / np.diag(K)))
+    assert stg.stag_residual(g, m, u, d, np.zeros((1, 4))) == pytest.approx(want, rel=1e-13)

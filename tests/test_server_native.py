@@ -121,3 +121,26 @@ def test_release_of_finished_requests():
             srv.release(a)
     finally:
         srv.close()
+
+
+def test_release_right_after_completion_keeps_admission_accounting():
+    # A client that releases a request the moment it sees it finished must not race the
+    # worker that ran it: the final state is published together with the return of the
+    # request's footprint, so the budget stays exact and later requests are still admitted.
+    import time
+    sp = _spec()
+    fp = binding.footprint_bytes(sp)
+    srv = binding.NativeServer(fp, 2)           # one simulation at a time, two workers
+    try:
+        for _ in range(60):
+            rid = srv.submit(sp)
+            t0 = time.time()
+            while srv.poll(rid)["state"] < binding.REQ_DONE:
+                assert time.time() - t0 < 30.0
+            srv.release(rid)
+        last = srv.submit(sp)
+        assert srv.drain(30.0)
+        assert srv.poll(last)["admit_seq"] == 60
+        assert srv.stats()["peak_bytes"] == fp
+    finally:
+        srv.close()
