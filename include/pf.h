@@ -203,6 +203,43 @@ const char *pf_status_string(pf_status s);
 void pf_destroy(pf_ctx *ctx);
 
 /* ------------------------------------------------------------------------------------
+ * Batches.  Several simulations advanced together so that their Krylov solves share
+ * kernel launches.  Each attached context runs its load steps on its own host thread (or
+ * through pf_batch_load_step); whenever every attached context that is inside a load
+ * step waits for an FP32 multigrid solve (the inner solves of PF_FP32_IR with
+ * PF_PRECOND_GMG and the VD split; Sec. 3.1-3.5 are unchanged), those solves run as one
+ * captured CUDA graph in which each fused PCG stage, multigrid level and coarse cycle is
+ * one launch for all of them, on the batch's own stream, with a device-side loop that
+ * stops every simulation's iteration on its own convergence test.  A simulation's
+ * arithmetic does not depend on the others: its results are bit-identical alone and in
+ * any batch.  Other solves (FP64, Jacobi, spectral split, grids too small for the fused
+ * multigrid) run per context as without a batch.  The paper has no batching layer; this
+ * is the lock-step executor of the batched workloads.
+ * ------------------------------------------------------------------------------------ */
+typedef struct pf_batch pf_batch;
+/* A batch on the calling thread's CUDA device.  Errors: PF_EINVAL, PF_ENOMEM, PF_ECUDA. */
+pf_status pf_batch_create(pf_batch **out);
+/* Attach ctx (same device, not attached elsewhere: PF_EBUSY).  Allocates a few hundred
+ * bytes of device memory per multigrid hierarchy.  Not while ctx is in a load step. */
+pf_status pf_batch_attach(pf_batch *b, pf_ctx *ctx);
+/* Detach ctx; PF_EBUSY while ctx is inside a load step.  pf_destroy detaches too. */
+pf_status pf_batch_detach(pf_batch *b, pf_ctx *ctx);
+/* One load step of each of the n distinct attached contexts ctx[i] (increment d_ubar[i],
+ * scheme[i], tolerance tol[i]), run concurrently on n host threads; returns when all are
+ * done.  res[i] / status[i] (each n long or NULL) receive what pf_load_step returns for
+ * ctx[i].  Returns PF_OK, PF_ENOTCONV if some step did not converge, or the first hard
+ * error; PF_EINVAL for a context not attached to b or listed twice. */
+pf_status pf_batch_load_step(pf_batch *b, int n, pf_ctx *const *ctx, const double *d_ubar,
+                             const int *scheme, const double *tol, pf_step_result *res,
+                             pf_status *status);
+/* Kernel launches of the batched solves, solves and launch groups run, largest group. */
+pf_status pf_batch_stats(const pf_batch *b, int64_t *launches, int64_t *solves,
+                         int64_t *groups, int *max_group);
+/* Detach every context and free the batch.  No load step of an attached context may be
+ * running. */
+void pf_batch_destroy(pf_batch *b);
+
+/* ------------------------------------------------------------------------------------
  * Serving.  A continuous-batching request server on the calling thread's CUDA device:
  * `slots` host worker threads each run one simulation at a time (pf_create, one
  * pf_load_step per load increment, pf_destroy), so up to `slots` simulations are resident

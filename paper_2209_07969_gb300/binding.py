@@ -111,6 +111,13 @@ _PROTOS = {
     "pf_profile": (S, [P, P, I, I]),
     "pf_last_error": (C.c_char_p, [P]),
     "pf_destroy": (None, [P]),
+    "pf_batch_create": (S, [C.POINTER(P)]),
+    "pf_batch_attach": (S, [P, P]),
+    "pf_batch_detach": (S, [P, P]),
+    "pf_batch_load_step": (S, [P, I, P, P, P, P, P, P]),
+    "pf_batch_stats": (S, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                           C.POINTER(C.c_int64), C.POINTER(I)]),
+    "pf_batch_destroy": (None, [P]),
     "pf_server_create": (S, [C.c_size_t, I, C.POINTER(P)]),
     "pf_server_submit": (S, [P, C.POINTER(Request), C.POINTER(C.c_int64)]),
     "pf_server_poll": (S, [P, C.c_int64, C.POINTER(RequestInfo), P, P]),
@@ -288,6 +295,71 @@ class Simulation:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """Simulations advanced together with batched Krylov solves (pf_batch_*, include/pf.h).
+
+    ``step(increments, schemes, tols)`` runs one load step of every member on its own host
+    thread inside the library; their FP32 multigrid solves share kernel launches."""
+
+    def __init__(self, sims=()):
+        p = P()
+        check(lib().pf_batch_create(C.byref(p)), "pf_batch_create")
+        self.b = p
+        self.sims = []
+        for sim in sims:
+            self.attach(sim)
+
+    def attach(self, sim):
+        check(lib().pf_batch_attach(self.b, sim.ctx), "pf_batch_attach", sim.ctx)
+        self.sims.append(sim)
+
+    def detach(self, sim):
+        check(lib().pf_batch_detach(self.b, sim.ctx), "pf_batch_detach", sim.ctx)
+        self.sims.remove(sim)
+
+    def step(self, increments, schemes, tols, sims=None):
+        """One load step of each simulation (default: all members); returns the per-
+        simulation result dicts with their 'status'."""
+        sims = self.sims if sims is None else list(sims)
+        n = len(sims)
+        ctxs = (P * n)(*[s.ctx for s in sims])
+        du = np.ascontiguousarray(np.broadcast_to(increments, (n,)), dtype=np.float64)
+        sc = np.ascontiguousarray(np.broadcast_to(schemes, (n,)), dtype=np.int32)
+        tl = np.ascontiguousarray(np.broadcast_to(tols, (n,)), dtype=np.float64)
+        res = (StepResult * n)()
+        st = np.zeros(n, dtype=np.int32)
+        s = lib().pf_batch_load_step(self.b, n, ctxs, du.ctypes.data, sc.ctypes.data,
+                                     tl.ctypes.data, C.addressof(res), st.ctypes.data)
+        if s not in (PF_OK, PF_ENOTCONV):
+            bad = [i for i in range(n) if st[i] not in (PF_OK, PF_ENOTCONV)]
+            check(s, "pf_batch_load_step", sims[bad[0]].ctx if bad else None)
+        out = []
+        for i in range(n):
+            d = res[i].as_dict()
+            d["status"] = int(st[i])
+            out.append(d)
+        return out
+
+    def stats(self):
+        la, so, gr, mg = C.c_int64(), C.c_int64(), C.c_int64(), I()
+        check(lib().pf_batch_stats(self.b, C.byref(la), C.byref(so), C.byref(gr), C.byref(mg)),
+              "pf_batch_stats")
+        return {"launches": la.value, "solves": so.value, "groups": gr.value,
+                "max_group": mg.value}
+
+    def close(self):
+        if self.b:
+            lib().pf_batch_destroy(self.b)
+            self.b = None
+            self.sims = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class NativeServer:

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "pf_gmg.cuh"
+#include "pf_batch.cuh"
 #include "pf_spectral.cuh"
 
 namespace pf {
@@ -308,12 +309,18 @@ __device__ __forceinline__ void sten_row(int nx, int ny, size_t nn, const T *__r
 
 // y = A x  (mode 0) or y = b - A x (mode 1), rows of non-free DOFs zero.
 template <class T, int B>
-__global__ void k_sten_apply(int nx, int ny, const T *__restrict__ S,
-                             const uint8_t *__restrict__ fm, const T *__restrict__ x,
-                             const T *__restrict__ b, T *__restrict__ y, int mode) {
+struct StenApplyF {
+  int nx, ny;
+  const T *__restrict__ S;
+  const uint8_t *__restrict__ fm;
+  const T *__restrict__ x;
+  const T *__restrict__ b;
+  T *__restrict__ y;
+  int mode;
+  __device__ void operator()(unsigned bid, unsigned nblk) const {
   const size_t nn = (size_t)(nx + 1) * (ny + 1);
-  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
-       n += (size_t)gridDim.x * blockDim.x) {
+  for (size_t n = bid * (size_t)blockDim.x + threadIdx.x; n < nn;
+       n += (size_t)nblk * blockDim.x) {
     T acc[B];
     sten_row<T, B>(nx, ny, nn, S, x, n, acc);
     const uint8_t f = fm[n];
@@ -324,19 +331,29 @@ __global__ void k_sten_apply(int nx, int ny, const T *__restrict__ S,
     }
   }
 }
+};
+template <class T, int B>
+__global__ void k_sten_apply(StenApplyF<T, B> f) { f(blockIdx.x, gridDim.x); }
 
 
 // ---- fused smoothing kernels of the grid-wide stencil levels ------------------------------
 // Pre-smoothing from x = 0 in one pass: d0 = it D^-1 b is formed at the neighbours, so
 // x = d0 + c1 d0 + c2 D^-1 (b - A d0) needs no stored d0 or residual.
 template <class T, int B>
-__global__ void k_sten_pre(int nx, int ny, const T *__restrict__ S, const T *__restrict__ invd,
-                           const T *coef, const uint8_t *__restrict__ fm, const T *__restrict__ b,
-                           T *__restrict__ x) {
+struct StenPreF {
+  int nx, ny;
+  const T *__restrict__ S;
+  const T *__restrict__ invd;
+  const T *coef;
+  const uint8_t *__restrict__ fm;
+  const T *__restrict__ b;
+  T *__restrict__ x;
+  __device__ void operator()(unsigned bid, unsigned nblk) const {
+    const T *__restrict__ invd = this->invd, *__restrict__ b = this->b;
   const size_t nn = (size_t)(nx + 1) * (ny + 1);
   const T it = coef[0], c2 = coef[1], c1 = coef[2];
-  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
-       n += (size_t)gridDim.x * blockDim.x) {
+  for (size_t n = bid * (size_t)blockDim.x + threadIdx.x; n < nn;
+       n += (size_t)nblk * blockDim.x) {
     T acc[B];
     sten_row_by<T, B>(nx, ny, nn, S, n,
                       [=](size_t q) { return __ldg(invd + q) * __ldg(b + q) * it; }, acc);
@@ -351,6 +368,9 @@ __global__ void k_sten_pre(int nx, int ny, const T *__restrict__ S, const T *__r
     }
   }
 }
+};
+template <class T, int B>
+__global__ void k_sten_pre(StenPreF<T, B> f) { f(blockIdx.x, gridDim.x); }
 
 // Bilinear prolongation of the coarse correction at fine node (ix, iy), component c.
 template <class T, int B>
@@ -369,12 +389,23 @@ __device__ __forceinline__ T prolong_at(int ix, int iy, int nxc, int nyc, const 
 // Coarse-grid correction and first post-smoothing step in one pass: t = x_in + P x_c on the
 // free components is formed at the neighbours; r = b - A t, d = it D^-1 r, x_out = t + d.
 template <class T, int B>
-__global__ void k_sten_prolong_first(int nx, int ny, const T *__restrict__ S,
-                                     const T *__restrict__ invd, const T *coef,
-                                     const uint8_t *__restrict__ fm, int nxc, int nyc,
-                                     const T *__restrict__ xc, const T *__restrict__ b,
-                                     const T *__restrict__ xin, T *__restrict__ xout,
-                                     T *__restrict__ r, T *__restrict__ d) {
+struct StenProlongFirstF {
+  int nx, ny;
+  const T *__restrict__ S;
+  const T *__restrict__ invd;
+  const T *coef;
+  const uint8_t *__restrict__ fm;
+  int nxc, nyc;
+  const T *__restrict__ xc;
+  const T *__restrict__ b;
+  const T *__restrict__ xin;
+  T *__restrict__ xout;
+  T *__restrict__ r;
+  T *__restrict__ d;
+  __device__ void operator()(unsigned bid, unsigned nblk) const {
+    const T *__restrict__ xin = this->xin, *__restrict__ xc = this->xc;
+    const uint8_t *__restrict__ fm = this->fm;
+    const int nxc = this->nxc, nyc = this->nyc;
   const size_t nn = (size_t)(nx + 1) * (ny + 1);
   const int ld = nx + 1;
   const T it = coef[0];
@@ -386,8 +417,8 @@ __global__ void k_sten_prolong_first(int nx, int ny, const T *__restrict__ S,
       v += prolong_at<T, B>((int)(m % ld), (int)(m / ld), nxc, nyc, xc, c);
     return v;
   };
-  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
-       n += (size_t)gridDim.x * blockDim.x) {
+  for (size_t n = bid * (size_t)blockDim.x + threadIdx.x; n < nn;
+       n += (size_t)nblk * blockDim.x) {
     T acc[B];
     sten_row_by<T, B>(nx, ny, nn, S, n, t_at, acc);
     const uint8_t f = __ldg(fm + n);
@@ -402,16 +433,26 @@ __global__ void k_sten_prolong_first(int nx, int ny, const T *__restrict__ S,
     }
   }
 }
+};
+template <class T, int B>
+__global__ void k_sten_prolong_first(StenProlongFirstF<T, B> f) { f(blockIdx.x, gridDim.x); }
 
 // Second post-smoothing step: x += c1 d + c2 D^-1 (r - A d).
 template <class T, int B>
-__global__ void k_sten_post(int nx, int ny, const T *__restrict__ S, const T *__restrict__ invd,
-                            const T *coef, const uint8_t *__restrict__ fm, const T *__restrict__ d,
-                            const T *__restrict__ r, T *__restrict__ x) {
+struct StenPostF {
+  int nx, ny;
+  const T *__restrict__ S;
+  const T *__restrict__ invd;
+  const T *coef;
+  const uint8_t *__restrict__ fm;
+  const T *__restrict__ d;
+  const T *__restrict__ r;
+  T *__restrict__ x;
+  __device__ void operator()(unsigned bid, unsigned nblk) const {
   const size_t nn = (size_t)(nx + 1) * (ny + 1);
   const T c2 = coef[1], c1 = coef[2];
-  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
-       n += (size_t)gridDim.x * blockDim.x) {
+  for (size_t n = bid * (size_t)blockDim.x + threadIdx.x; n < nn;
+       n += (size_t)nblk * blockDim.x) {
     T acc[B];
     sten_row<T, B>(nx, ny, nn, S, d, n, acc);
     const uint8_t f = __ldg(fm + n);
@@ -423,6 +464,9 @@ __global__ void k_sten_post(int nx, int ny, const T *__restrict__ S, const T *__
     }
   }
 }
+};
+template <class T, int B>
+__global__ void k_sten_post(StenPostF<T, B> f) { f(blockIdx.x, gridDim.x); }
 
 // ---- coarse levels in one CTA --------------------------------------------------------------
 template <class T>
@@ -456,7 +500,7 @@ __device__ __forceinline__ void st_(T *p, T v) { *p = v; }
 //         r = b - A x;  b_coarse = P^T r
 //   up:   x += P x_coarse;  r = b - A x, d = it D^-1 r;  x = (x + d) + c1 d + c2 D^-1 (r - A d)
 template <class T, int B>
-__global__ void __launch_bounds__(COARSE_THREADS) k_coarse_cycle(CoarseArgs<T> a) {
+__device__ __forceinline__ void coarse_cycle_body(const CoarseArgs<T> &a) {
   const size_t t0 = threadIdx.x, nt = blockDim.x;
   const int last = a.nlev - 1;
   for (int l = 0; l < last; ++l) {
@@ -594,6 +638,18 @@ __global__ void __launch_bounds__(COARSE_THREADS) k_coarse_cycle(CoarseArgs<T> a
   }
 }
 
+template <class T, int B>
+__global__ void __launch_bounds__(COARSE_THREADS) k_coarse_cycle(CoarseArgs<T> a) {
+  coarse_cycle_body<T, B>(a);
+}
+
+// One simulation's coarse cycle in a batched launch: one CTA, arguments in device memory.
+template <class T, int B>
+struct CoarseF {
+  const CoarseArgs<T> *a;
+  __device__ void operator()(unsigned, unsigned) const { coarse_cycle_body<T, B>(*a); }
+};
+
 // Chebyshev on [lmax/10, lmax]: theta = 0.55 lmax, delta = 0.45 lmax, sigma = 11/9.
 // first step from x = 0: d = D^-1 b / theta; x = d; r = b
 template <class T>
@@ -650,11 +706,17 @@ __global__ void k_sub(size_t n, const T *__restrict__ b, const T *__restrict__ y
 
 // b_c = P^T r_f over free DOFs (out-of-grid fine neighbours: clamped index, weight 0).
 template <class T, int B>
-__global__ void k_restrict(int nxf, int nyf, const T *__restrict__ rf, const uint8_t *__restrict__ fmf,
-                           int nxc, int nyc, const uint8_t *__restrict__ fmc, T *__restrict__ bc) {
+struct RestrictF {
+  int nxf, nyf;
+  const T *__restrict__ rf;
+  const uint8_t *__restrict__ fmf;
+  int nxc, nyc;
+  const uint8_t *__restrict__ fmc;
+  T *__restrict__ bc;
+  __device__ void operator()(unsigned bid, unsigned nblk) const {
   const size_t nnc = (size_t)(nxc + 1) * (nyc + 1);
-  for (size_t I = blockIdx.x * (size_t)blockDim.x + threadIdx.x; I < nnc;
-       I += (size_t)gridDim.x * blockDim.x) {
+  for (size_t I = bid * (size_t)blockDim.x + threadIdx.x; I < nnc;
+       I += (size_t)nblk * blockDim.x) {
     const int Ix = (int)(I % (nxc + 1)), Iy = (int)(I / (nxc + 1));
     T acc[B];
 #pragma unroll
@@ -684,6 +746,9 @@ __global__ void k_restrict(int nxf, int nyf, const T *__restrict__ rf, const uin
     for (int c = 0; c < B; ++c) bc[B * I + c] = ((mc >> c) & 1) ? acc[c] : T(0);
   }
 }
+};
+template <class T, int B>
+__global__ void k_restrict(RestrictF<T, B> f) { f(blockIdx.x, gridDim.x); }
 
 // x_f += P x_c over free fine DOFs (always four parents, out-of-grid ones weighted 0).
 template <class T, int B>
@@ -823,6 +888,8 @@ void gmg_free(Gmg<T> &G) {
     L = GmgLevel<T>();
   }
   if (G.cinv) cudaFree(G.cinv);
+  if (G.dca) cudaFree(G.dca);
+  G.dca = nullptr;
   if (G.hS) cudaFreeHost(G.hS);
   delete[] G.hA;
   delete[] G.hInv;
@@ -929,9 +996,9 @@ void gmg_sten_apply(const Gmg<T> &G, int l, const T *x, const T *b, T *y, int mo
                     cudaStream_t st) {
   const GmgLevel<T> &L = G.lv[l];
   if (G.B == 2)
-    k_sten_apply<T, 2><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.fm, x, b, y, mode);
+    k_sten_apply<T, 2><<<nblk(L.nn), 256, 0, st>>>(StenApplyF<T, 2>{L.nx, L.ny, L.S, L.fm, x, b, y, mode});
   else
-    k_sten_apply<T, 1><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.fm, x, b, y, mode);
+    k_sten_apply<T, 1><<<nblk(L.nn), 256, 0, st>>>(StenApplyF<T, 1>{L.nx, L.ny, L.S, L.fm, x, b, y, mode});
 }
 template <class T>
 void gmg_cheb_first(const Gmg<T> &G, int l, const T *b, T *x, T *d, T *r, cudaStream_t st) {
@@ -960,9 +1027,9 @@ template <class T>
 void gmg_restrict(const Gmg<T> &G, int l, const T *rf, T *bc, cudaStream_t st) {
   const GmgLevel<T> &F = G.lv[l], &C = G.lv[l + 1];
   if (G.B == 2)
-    k_restrict<T, 2><<<nblk(C.nn), 256, 0, st>>>(F.nx, F.ny, rf, F.fm, C.nx, C.ny, C.fm, bc);
+    k_restrict<T, 2><<<nblk(C.nn), 256, 0, st>>>(RestrictF<T, 2>{F.nx, F.ny, rf, F.fm, C.nx, C.ny, C.fm, bc});
   else
-    k_restrict<T, 1><<<nblk(C.nn), 256, 0, st>>>(F.nx, F.ny, rf, F.fm, C.nx, C.ny, C.fm, bc);
+    k_restrict<T, 1><<<nblk(C.nn), 256, 0, st>>>(RestrictF<T, 1>{F.nx, F.ny, rf, F.fm, C.nx, C.ny, C.fm, bc});
 }
 template <class T>
 void gmg_prolong_add(const Gmg<T> &G, int l, const T *xc, T *xf, cudaStream_t st) {
@@ -976,31 +1043,31 @@ template <class T>
 void gmg_pre(const Gmg<T> &G, int l, const T *b, T *x, cudaStream_t st) {
   const GmgLevel<T> &L = G.lv[l];
   if (G.B == 2)
-    k_sten_pre<T, 2><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.coef, L.fm, b, x);
+    k_sten_pre<T, 2><<<nblk(L.nn), 256, 0, st>>>(StenPreF<T, 2>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm, b, x});
   else
-    k_sten_pre<T, 1><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.coef, L.fm, b, x);
+    k_sten_pre<T, 1><<<nblk(L.nn), 256, 0, st>>>(StenPreF<T, 1>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm, b, x});
 }
 template <class T>
 void gmg_prolong_first(const Gmg<T> &G, int l, const T *xin, T *xout, cudaStream_t st) {
   const GmgLevel<T> &L = G.lv[l], &C = G.lv[l + 1];
   if (G.B == 2)
-    k_sten_prolong_first<T, 2><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.coef, L.fm,
+    k_sten_prolong_first<T, 2><<<nblk(L.nn), 256, 0, st>>>(StenProlongFirstF<T, 2>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm,
                                                            C.nx, C.ny, C.x, L.b, xin, xout, L.r,
-                                                           L.dv);
+                                                           L.dv});
   else
-    k_sten_prolong_first<T, 1><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.coef, L.fm,
+    k_sten_prolong_first<T, 1><<<nblk(L.nn), 256, 0, st>>>(StenProlongFirstF<T, 1>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm,
                                                            C.nx, C.ny, C.x, L.b, xin, xout, L.r,
-                                                           L.dv);
+                                                           L.dv});
 }
 template <class T>
 void gmg_post(const Gmg<T> &G, int l, T *x, cudaStream_t st) {
   const GmgLevel<T> &L = G.lv[l];
   if (G.B == 2)
-    k_sten_post<T, 2><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.coef, L.fm, L.dv,
-                                                  L.r, x);
+    k_sten_post<T, 2><<<nblk(L.nn), 256, 0, st>>>(StenPostF<T, 2>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm, L.dv,
+                                                  L.r, x});
   else
-    k_sten_post<T, 1><<<nblk(L.nn), 256, 0, st>>>(L.nx, L.ny, L.S, L.invd, L.coef, L.fm, L.dv,
-                                                  L.r, x);
+    k_sten_post<T, 1><<<nblk(L.nn), 256, 0, st>>>(StenPostF<T, 1>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm, L.dv,
+                                                  L.r, x});
 }
 template <class T>
 void gmg_coarse_cycle(const Gmg<T> &G, int lc, const T *b0, T *x0, cudaStream_t st) {
@@ -1020,6 +1087,97 @@ void gmg_coarse_cycle(const Gmg<T> &G, int lc, const T *b0, T *x0, cudaStream_t 
     k_coarse_cycle<T, 1><<<1, COARSE_THREADS, 0, st>>>(a);
 }
 
+// ---- batched V-cycle (pf_batch.cuh) ----------------------------------------------------
+template <class T>
+static CoarseArgs<T> coarse_args(const Gmg<T> &G, int lc, const T *b0, T *x0) {
+  CoarseArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  a.nlev = G.nl - lc;
+  for (int l = lc; l < G.nl; ++l) {
+    const GmgLevel<T> &L = G.lv[l];
+    a.L[l - lc] = CoarseLevel<T>{L.nx, L.ny, L.S, L.invd, L.x, L.b, L.r, L.dv, L.y, L.fm, L.coef};
+  }
+  a.b0 = b0;
+  a.x0 = x0;
+  a.cinv = G.cinv;
+  a.ncoarse = G.ncoarse;
+  return a;
+}
+
+template <class T>
+cudaError_t gmg_batch_prepare(Gmg<T> &G) {
+  const int lc = G.lc > 1 ? G.lc : 1;
+  if (lc >= G.nl) return cudaErrorInvalidValue;
+  const CoarseArgs<T> a = coarse_args<T>(G, lc, G.lv[lc].b, G.lv[lc].x);
+  cudaError_t e = cudaSuccess;
+  if (!G.dca && (e = cudaMalloc(&G.dca, sizeof(CoarseArgs<T>))) != cudaSuccess) {
+    G.dca = nullptr;
+    return e;
+  }
+  return cudaMemcpy(G.dca, &a, sizeof(a), cudaMemcpyHostToDevice);
+}
+
+template <class T, int B>
+static int restrict0_batch_b(int n, Gmg<T> *const *G, const int *const *done, cudaStream_t st) {
+  Batcher<RestrictF<T, B>, 256> b;
+  for (int i = 0; i < n; ++i) {
+    const GmgLevel<T> &F = G[i]->lv[0], &C = G[i]->lv[1];
+    b.add(RestrictF<T, B>{F.nx, F.ny, F.r, F.fm, C.nx, C.ny, C.fm, C.b}, nblk(C.nn), done[i]);
+  }
+  return b.launch(st);
+}
+template <class T>
+int gmg_restrict0_batch(int n, Gmg<T> *const *G, const int *const *done, cudaStream_t st) {
+  return G[0]->B == 2 ? restrict0_batch_b<T, 2>(n, G, done, st)
+                      : restrict0_batch_b<T, 1>(n, G, done, st);
+}
+
+// The launch order of gmg_mid(G, 1) for every hierarchy: down through the grid levels each
+// hierarchy has (level l takes the hierarchies with l < lc), the coarse cycles, and up.
+template <class T, int B>
+static int mid_batch_b(int n, Gmg<T> *const *G, const int *const *done, cudaStream_t st) {
+  int launches = 0, lmax = 1;
+  for (int i = 0; i < n; ++i) lmax = G[i]->lc > lmax ? G[i]->lc : lmax;
+  for (int l = 1; l < lmax; ++l) {
+    Batcher<StenPreF<T, B>, 256> pre;
+    Batcher<StenApplyF<T, B>, 256> app;
+    Batcher<RestrictF<T, B>, 256> res;
+    for (int i = 0; i < n; ++i) {
+      if (l >= G[i]->lc) continue;
+      const GmgLevel<T> &L = G[i]->lv[l], &C = G[i]->lv[l + 1];
+      pre.add(StenPreF<T, B>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm, L.b, L.y}, nblk(L.nn), done[i]);
+      app.add(StenApplyF<T, B>{L.nx, L.ny, L.S, L.fm, L.y, L.b, L.r, 1}, nblk(L.nn), done[i]);
+      res.add(RestrictF<T, B>{L.nx, L.ny, L.r, L.fm, C.nx, C.ny, C.fm, C.b}, nblk(C.nn), done[i]);
+    }
+    launches += pre.launch(st) + app.launch(st) + res.launch(st);
+  }
+  {
+    Batcher<CoarseF<T, B>, COARSE_THREADS> cc;
+    for (int i = 0; i < n; ++i)
+      cc.add(CoarseF<T, B>{static_cast<const CoarseArgs<T> *>(G[i]->dca)}, 1, done[i]);
+    launches += cc.launch(st);
+  }
+  for (int l = lmax - 1; l >= 1; --l) {
+    Batcher<StenProlongFirstF<T, B>, 256> pf;
+    Batcher<StenPostF<T, B>, 256> post;
+    for (int i = 0; i < n; ++i) {
+      if (l >= G[i]->lc) continue;
+      const GmgLevel<T> &L = G[i]->lv[l], &C = G[i]->lv[l + 1];
+      pf.add(StenProlongFirstF<T, B>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm, C.nx, C.ny, C.x, L.b,
+                                     L.y, L.x, L.r, L.dv},
+             nblk(L.nn), done[i]);
+      post.add(StenPostF<T, B>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm, L.dv, L.r, L.x}, nblk(L.nn),
+               done[i]);
+    }
+    launches += pf.launch(st) + post.launch(st);
+  }
+  return launches;
+}
+template <class T>
+int gmg_mid_batch(int n, Gmg<T> *const *G, const int *const *done, cudaStream_t st) {
+  return G[0]->B == 2 ? mid_batch_b<T, 2>(n, G, done, st) : mid_batch_b<T, 1>(n, G, done, st);
+}
+
 #define GMG_INST(T)                                                                            \
   template cudaError_t gmg_alloc<T>(Gmg<T> &, int, int, int, const RedWs &);                   \
   template void gmg_free<T>(Gmg<T> &);                                                         \
@@ -1037,6 +1195,9 @@ void gmg_coarse_cycle(const Gmg<T> &G, int lc, const T *b0, T *x0, cudaStream_t 
   template void gmg_cheb_step<T>(const Gmg<T> &, int, const T *, T *, T *, T *, cudaStream_t);  \
   template void gmg_sub<T>(size_t, const T *, const T *, T *, cudaStream_t);                    \
   template void gmg_restrict<T>(const Gmg<T> &, int, const T *, T *, cudaStream_t);             \
+  template cudaError_t gmg_batch_prepare<T>(Gmg<T> &);                                         \
+  template int gmg_restrict0_batch<T>(int, Gmg<T> *const *, const int *const *, cudaStream_t); \
+  template int gmg_mid_batch<T>(int, Gmg<T> *const *, const int *const *, cudaStream_t);       \
   template void gmg_prolong_add<T>(const Gmg<T> &, int, const T *, T *, cudaStream_t);          \
   template void gmg_coarse_cycle<T>(const Gmg<T> &, int, const T *, T *, cudaStream_t);      \
   template void gmg_pre<T>(const Gmg<T> &, int, const T *, T *, cudaStream_t);                 \

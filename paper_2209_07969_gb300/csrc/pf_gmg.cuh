@@ -53,6 +53,7 @@ struct Gmg {
   T *hInv = nullptr;
   RedWs ws{};
   bool ready = false;
+  void *dca = nullptr;      // device copy of the coarse-cycle arguments (batched launches)
 };
 
 // Allocate the hierarchy for a fine grid (device memory owned by the Gmg object).
@@ -74,6 +75,19 @@ cudaError_t gmg_setup_damage(Gmg<T> &G, const GridD &g, const T *c, double kappa
 // Elasticity setup from per-point tangents Dq (6 x Q, FP64; spectral split), see sp_points.
 template <class T>
 cudaError_t gmg_setup_elas_qp(Gmg<T> &G, const GridD &g, const double *Dq, cudaStream_t st);
+
+// Batched V-cycle below level 0 for n hierarchies of one kind (same B, each with
+// lc >= 1): the restriction of level 0's residual (lv[0].r -> lv[1].b), and gmg_mid(G, 1)
+// of every hierarchy with one launch per kernel and level for all of them.  done[i]: stop
+// flag of hierarchy i's Krylov solve (its CTAs skip the launch once it is set).
+// gmg_batch_prepare writes the device copy of the coarse-cycle arguments; it allocates,
+// so it runs outside stream capture, once per hierarchy.  n <= PF_MAXB.
+template <class T>
+cudaError_t gmg_batch_prepare(Gmg<T> &G);
+template <class T>
+int gmg_restrict0_batch(int n, Gmg<T> *const *G, const int *const *done, cudaStream_t st);
+template <class T>
+int gmg_mid_batch(int n, Gmg<T> *const *G, const int *const *done, cudaStream_t st);
 
 // Launchers of the V-cycle building blocks (pf_gmg.cu).
 template <class T>

@@ -40,9 +40,9 @@ struct KrylovScal {
   double rr0;    // ||r||^2 after the initialisation
   double rtol2;  // stop when rr <= rtol2 rr0
   int maxit;     // stop after maxit iterations
+  int done;      // set when this solve has stopped (batched solves skip its work)
   int it;        // iterations done
   int breakdown;
-  int pad;
 };
 
 // Reduction workspace: per-CTA partials (up to 4 values each) and the arrival counter,
@@ -92,11 +92,13 @@ __device__ __forceinline__ void red_cta(double (&v)[NV], double (*sh)[32], bool 
 // order.  Returns true in thread 0 of that CTA, with tot[] holding the totals; the counter
 // is reset for the next launch.  Every CTA of the grid must call it.
 constexpr int RED_UNROLL = 8;
+// bid / nblk: the CTA's index among the nblk CTAs that take part (a batched launch runs
+// several such groups, one per simulation, each with its own workspace).
 template <int NV>
-__device__ bool red_grid(double (&v)[NV], const RedWs ws, double (&tot)[NV], bool is_max) {
+__device__ bool red_grid(double (&v)[NV], const RedWs ws, double (&tot)[NV], bool is_max,
+                         unsigned bid, unsigned nblk) {
   __shared__ double sh[NV][32];
   __shared__ int go;
-  const unsigned nblk = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
   const double none = is_max ? -INFINITY : 0.0;
   const size_t mb = (size_t)ws.max_blocks;
   red_cta<NV>(v, sh, is_max);
@@ -135,6 +137,11 @@ __device__ bool red_grid(double (&v)[NV], const RedWs ws, double (&tot)[NV], boo
 #pragma unroll
   for (int k = 0; k < NV; ++k) tot[k] = w[k];
   return true;
+}
+template <int NV>
+__device__ bool red_grid(double (&v)[NV], const RedWs ws, double (&tot)[NV], bool is_max) {
+  return red_grid<NV>(v, ws, tot, is_max, blockIdx.y * gridDim.x + blockIdx.x,
+                      gridDim.x * gridDim.y);
 }
 #endif
 

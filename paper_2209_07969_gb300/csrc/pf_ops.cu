@@ -16,8 +16,11 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <type_traits>
+
 #include "pf_internal.cuh"
 #include "pf_fused.cuh"
+#include "pf_batch.cuh"
 
 namespace pf {
 
@@ -290,15 +293,17 @@ constexpr int STRIP_WARPS = 4;  // warps per CTA
 // RESID: internal force of the nonlinear stress law instead of the tangent product; the
 // element's tension bits are computed and stored (by the lane and row that own the element).
 template <class T, int SR, class Op, bool RESID = false>
-__global__ void __launch_bounds__(32 * STRIP_WARPS)
-k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, uint8_t *__restrict__ tens,
-             Op op, RedWs ws) {
+__device__ __forceinline__ void elas_strip_body(unsigned bid, unsigned nblk, const GridD &g,
+                                                const ElemConst<T> &kc,
+                                                const T *__restrict__ d,
+                                                uint8_t *__restrict__ tens, Op op,
+                                                const RedWs &ws) {
   constexpr int NR = Op::NR > 0 ? Op::NR : 1;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int nx = g.nx, ny = g.ny, ld = nx + 1;
   const int nstrips = (nx + 1 + SW - 1) / SW, nchunks = (ny + 1 + SR - 1) / SR;
-  const int gw = blockIdx.x * STRIP_WARPS + (threadIdx.x >> 5);
+  const int gw = bid * STRIP_WARPS + (threadIdx.x >> 5);
   const int strip = gw % nstrips, chunk = gw / nstrips;
   op.begin();
   T acc[NR];
@@ -400,9 +405,30 @@ k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, uint8_t *__restr
     double v[NR], tot[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) v[k] = (double)acc[k];
-    if (grid_reduce<NR>(v, ws, tot)) op.fin(tot);
+    if (red_grid<NR>(v, ws, tot, false, bid, nblk)) op.fin(tot);
   }
 }
+
+template <class T, int SR, class Op, bool RESID = false>
+__global__ void __launch_bounds__(32 * STRIP_WARPS)
+k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, uint8_t *__restrict__ tens,
+             Op op, RedWs ws) {
+  elas_strip_body<T, SR, Op, RESID>(blockIdx.x, gridDim.x, g, kc, d, tens, op, ws);
+}
+
+// One simulation's share of a batched strip launch (pf_batch.cuh).
+template <class T, int SR, class Op>
+struct StripF {
+  GridD g;
+  ElemConst<T> kc;
+  const T *d;
+  const uint8_t *tens;
+  Op op;
+  RedWs ws;
+  __device__ void operator()(unsigned bid, unsigned nblk) const {
+    elas_strip_body<T, SR, Op, false>(bid, nblk, g, kc, d, const_cast<uint8_t *>(tens), op, ws);
+  }
+};
 
 // ------------------------------------------------------------------------------------
 // Evolution equation: K_dd diagonal / AT2 right-hand side (one tile of nodes per CTA,
@@ -472,8 +498,9 @@ k_damage(GridD g, ElemConst<T> kc, const C *__restrict__ c, T *__restrict__ y) {
 // apply, the operand formed by op.in() while the CTA stages its node patch and the product
 // handed to op.out() at each owned node.
 template <class T, class Op>
-__global__ void __launch_bounds__(TILE_THREADS, sizeof(T) == 4 ? 8 : 4)
-k_damage_op(GridD g, ElemConst<T> kc, const T *__restrict__ c, Op op, RedWs ws) {
+__device__ __forceinline__ void damage_op_body(unsigned bid, unsigned nblk, const GridD &g,
+                                               const ElemConst<T> &kc, const T *__restrict__ c,
+                                               Op op, const RedWs &ws) {
   constexpr int PX = TX + 2, PY = TY + 2, EX = TX + 1, EY = TY + 1, NE = EX * EY;
   constexpr int NR = Op::NR > 0 ? Op::NR : 1;
   __shared__ T sxv[PY * PX];
@@ -487,7 +514,7 @@ k_damage_op(GridD g, ElemConst<T> kc, const T *__restrict__ c, Op op, RedWs ws) 
   const T ihx = kc.ihx, ihy = kc.ihy, w = kc.w;
   const T kappa = kc.kappa;
   const T G0 = kc.G0, G1 = kc.G1;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int tile = (int)bid; tile < ntiles; tile += (int)nblk) {
     const int i0 = (tile % tbx) * TX, j0 = (tile / tbx) * TY;
     for (int t = threadIdx.x; t < PX * PY; t += TILE_THREADS) {
       const int li = t % PX, lj = t / PX;
@@ -555,9 +582,28 @@ k_damage_op(GridD g, ElemConst<T> kc, const T *__restrict__ c, Op op, RedWs ws) 
     double v[NR], tot[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) v[k] = (double)acc[k];
-    if (grid_reduce<NR>(v, ws, tot)) op.fin(tot);
+    if (red_grid<NR>(v, ws, tot, false, bid, nblk)) op.fin(tot);
   }
 }
+
+template <class T, class Op>
+__global__ void __launch_bounds__(TILE_THREADS, sizeof(T) == 4 ? 8 : 4)
+k_damage_op(GridD g, ElemConst<T> kc, const T *__restrict__ c, Op op, RedWs ws) {
+  damage_op_body<T, Op>(blockIdx.x, gridDim.x, g, kc, c, op, ws);
+}
+
+// One simulation's share of a batched K_dd launch (pf_batch.cuh).
+template <class T, class Op>
+struct DamageF {
+  GridD g;
+  ElemConst<T> kc;
+  const T *c;
+  Op op;
+  RedWs ws;
+  __device__ void operator()(unsigned bid, unsigned nblk) const {
+    damage_op_body<T, Op>(bid, nblk, g, kc, c, op, ws);
+  }
+};
 
 // ------------------------------------------------------------------------------------
 // Per-Gauss-point kernels (one thread per element, FP64).
@@ -812,6 +858,23 @@ static inline unsigned elem_blocks(size_t n) {
   return (unsigned)(b < 1 ? 1 : (b > 65535u * 8u ? 65535u * 8u : b));
 }
 
+// Node rows per warp of the strip kernel.  A warp also evaluates the element row below its
+// chunk: SR rows cost SR + 1 element rows.  FP32 launches are latency-bound at small sizes
+// (short strips, more warps); FP64 ones are bound by the FP64 pipe, so they take long
+// strips to waste little arithmetic.
+template <class T>
+static int strip_rows(size_t nn) {
+  if (sizeof(T) == 8 && nn >= (size_t)100000) return 8;
+  if (nn < (size_t)1500000) return 2;
+  if (nn < (size_t)6000000) return 4;
+  return 8;
+}
+static unsigned strip_blocks(const GridD &g, int sr) {
+  const unsigned strips = (unsigned)((g.nx + 1 + SW - 1) / SW);
+  const unsigned warps = strips * (unsigned)((g.ny + 1 + sr - 1) / sr);
+  return (warps + STRIP_WARPS - 1) / STRIP_WARPS;
+}
+
 template <class T, class Op, bool RESID = false>
 static void strip_launch(const GridD &g, const MatD &m, const T *d, const uint8_t *tens_c,
                          const Op &op, const RedWs &w, cudaStream_t st) {
@@ -823,14 +886,10 @@ static void strip_launch(const GridD &g, const MatD &m, const T *d, const uint8_
     return (warps + STRIP_WARPS - 1) / STRIP_WARPS;
   };
   const ElemConst<T> kc = elem_const<T>(g, m);
-  // A warp also evaluates the element row below its chunk: SR rows cost SR + 1 element rows.
-  // FP32 launches are latency-bound at small sizes (short strips, more warps); FP64 ones
-  // are bound by the FP64 pipe, so they take long strips to waste little arithmetic.
-  if (sizeof(T) == 8 && nn >= (size_t)100000)
-    k_elas_strip<T, 8, Op, RESID><<<blocks(8), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
-  else if (nn < (size_t)1500000)
+  const int sr = strip_rows<T>(nn);
+  if (sr == 2)
     k_elas_strip<T, 2, Op, RESID><<<blocks(2), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
-  else if (nn < (size_t)6000000)
+  else if (sr == 4)
     k_elas_strip<T, 4, Op, RESID><<<blocks(4), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
   else
     k_elas_strip<T, 8, Op, RESID><<<blocks(8), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
@@ -844,46 +903,78 @@ void elas_apply(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, 
   strip_launch<T>(g, m, d, tens, OpApply<T, 2>{x, y, sc, e}, w, st);
 }
 
+// The input/output policy of fused stage `stage` (pf_fused.cuh) on the buffers M, handed
+// to f.  B = 2: elasticity, B = 1: phase field.
+template <class T, int B, class F>
+static void stage_op(int stage, const MgBufs<T> &M, F &&f) {
+  T *rprev = M.r[0], *rcur = M.r[1], *pprev = M.p[0], *pcur = M.p[1];
+  switch (stage) {
+    case FS_DIR:
+      f(OpDir<T, B>{M.zb, pprev, pcur, M.q, M.sc});
+      break;
+    case FS_UPD:
+      f(OpUpd<T, B, false>{rprev, M.q, pcur, M.invd, M.coef, rcur, M.x, M.za, M.sc});
+      break;
+    case FS_UPD_INIT:
+      f(OpUpd<T, B, true>{M.b, nullptr, nullptr, M.invd, M.coef, rcur, M.x, M.za, M.sc});
+      break;
+    case FS_RESID:
+      f(OpResid<T, B>{M.za, rcur, M.lr});
+      break;
+    case FS_PROLONG:
+      f(OpProlong<T, B>{M.za, M.xc, rcur, M.invd, M.coef, M.fm, M.nxc, M.nyc, M.zb, M.lr, M.dv});
+      break;
+    case FS_FINISH:
+      f(OpFinish<T, B, false>{M.dv, M.lr, M.invd, M.coef, rcur, pcur, M.zb, rprev, pprev, M.sc});
+      break;
+    case FS_FINISH_FIRST:
+      f(OpFinish<T, B, true>{M.dv, M.lr, M.invd, M.coef, rcur, pcur, M.zb, rprev, pprev, M.sc});
+      break;
+  }
+}
+
 template <class T>
 void elas_mg_stage(int stage, const GridD &g, const MatD &m, const T *d, const uint8_t *tens,
                    const MgBufs<T> &B, const RedWs &ws, cudaStream_t st) {
-  T *rprev = B.r[0], *rcur = B.r[1], *pprev = B.p[0], *pcur = B.p[1];
-  switch (stage) {
-    case FS_DIR:
-      strip_launch<T>(g, m, d, tens, OpDir<T, 2>{B.zb, pprev, pcur, B.q, B.sc}, ws, st);
-      break;
-    case FS_UPD:
-      strip_launch<T>(g, m, d, tens,
-                      OpUpd<T, 2, false>{rprev, B.q, pcur, B.invd, B.coef, rcur, B.x, B.za, B.sc},
-                      ws, st);
-      break;
-    case FS_UPD_INIT:
-      strip_launch<T>(g, m, d, tens,
-                      OpUpd<T, 2, true>{B.b, nullptr, nullptr, B.invd, B.coef, rcur, B.x, B.za, B.sc},
-                      ws, st);
-      break;
-    case FS_RESID:
-      strip_launch<T>(g, m, d, tens, OpResid<T, 2>{B.za, rcur, B.lr}, ws, st);
-      break;
-    case FS_PROLONG:
-      strip_launch<T>(g, m, d, tens,
-                      OpProlong<T, 2>{B.za, B.xc, rcur, B.invd, B.coef, B.fm, B.nxc, B.nyc, B.zb,
-                                   B.lr, B.dv},
-                      ws, st);
-      break;
-    case FS_FINISH:
-      strip_launch<T>(g, m, d, tens,
-                      OpFinish<T, 2, false>{B.dv, B.lr, B.invd, B.coef, rcur, pcur, B.zb, rprev,
-                                         pprev, B.sc},
-                      ws, st);
-      break;
-    case FS_FINISH_FIRST:
-      strip_launch<T>(g, m, d, tens,
-                      OpFinish<T, 2, true>{B.dv, B.lr, B.invd, B.coef, rcur, pcur, B.zb, rprev,
-                                        pprev, B.sc},
-                      ws, st);
-      break;
-  }
+  stage_op<T, 2>(stage, B, [&](auto op) { strip_launch<T>(g, m, d, tens, op, ws, st); });
+}
+
+// Batched form: stage `stage` for n simulations in one launch per strip height (the strip
+// height follows the grid size exactly as in the single launch, so a simulation's blocks
+// and reductions are the same in both).
+template <class T>
+int elas_mg_stage_batch(int stage, int n, const ElasStageIn<T> *in, cudaStream_t st) {
+  int launches = 0;
+  stage_op<T, 2>(stage, in[0].B, [&](auto op0) {
+    using Op = decltype(op0);
+    constexpr int TH = 32 * STRIP_WARPS;
+    Batcher<StripF<T, 2, Op>, TH, 8> b2;
+    Batcher<StripF<T, 4, Op>, TH, 8> b4;
+    Batcher<StripF<T, 8, Op>, TH, 8> b8;
+    for (int i = 0; i < n; ++i) {
+      const ElasStageIn<T> &q = in[i];
+      const size_t nn = (size_t)(q.g.nx + 1) * (q.g.ny + 1);
+      const int sr = strip_rows<T>(nn);
+      const ElemConst<T> kc = elem_const<T>(q.g, q.m);
+      const int *done = &q.B.sc->done;
+      stage_op<T, 2>(stage, q.B, [&](auto op) {
+        if constexpr (std::is_same<decltype(op), Op>::value) {
+          if (sr == 2) {
+            if (b2.L.n == PF_MAXB) { launches += b2.launch(st); b2 = {}; }
+            b2.add(StripF<T, 2, Op>{q.g, kc, q.d, q.tens, op, q.ws}, strip_blocks(q.g, 2), done);
+          } else if (sr == 4) {
+            if (b4.L.n == PF_MAXB) { launches += b4.launch(st); b4 = {}; }
+            b4.add(StripF<T, 4, Op>{q.g, kc, q.d, q.tens, op, q.ws}, strip_blocks(q.g, 4), done);
+          } else {
+            if (b8.L.n == PF_MAXB) { launches += b8.launch(st); b8 = {}; }
+            b8.add(StripF<T, 8, Op>{q.g, kc, q.d, q.tens, op, q.ws}, strip_blocks(q.g, 8), done);
+          }
+        }
+      });
+    }
+    launches += b2.launch(st) + b4.launch(st) + b8.launch(st);
+  });
+  return launches;
 }
 
 template <class T>
@@ -913,48 +1004,34 @@ void damage_apply(const GridD &g, const T *c, double kappa, const T *x, T *y, cu
 template <class T>
 void damage_mg_stage(int stage, const GridD &g, const T *c, double kappa, const MgBufs<T> &B,
                      const RedWs &ws, cudaStream_t st) {
-  T *rprev = B.r[0], *rcur = B.r[1], *pprev = B.p[0], *pcur = B.p[1];
   const ElemConst<T> kc = elem_const<T>(g, MatD{}, kappa);
   const dim3 gt = tile_grid(g);
-  switch (stage) {
-    case FS_DIR:
-      k_damage_op<T, OpDir<T, 1>><<<gt, TILE_THREADS, 0, st>>>(
-          g, kc, c, OpDir<T, 1>{B.zb, pprev, pcur, B.q, B.sc}, ws);
-      break;
-    case FS_UPD:
-      k_damage_op<T, OpUpd<T, 1, false>><<<gt, TILE_THREADS, 0, st>>>(
-          g, kc, c, OpUpd<T, 1, false>{rprev, B.q, pcur, B.invd, B.coef, rcur, B.x, B.za, B.sc},
-          ws);
-      break;
-    case FS_UPD_INIT:
-      k_damage_op<T, OpUpd<T, 1, true>><<<gt, TILE_THREADS, 0, st>>>(
-          g, kc, c,
-          OpUpd<T, 1, true>{B.b, nullptr, nullptr, B.invd, B.coef, rcur, B.x, B.za, B.sc}, ws);
-      break;
-    case FS_RESID:
-      k_damage_op<T, OpResid<T, 1>><<<gt, TILE_THREADS, 0, st>>>(
-          g, kc, c, OpResid<T, 1>{B.za, rcur, B.lr}, ws);
-      break;
-    case FS_PROLONG:
-      k_damage_op<T, OpProlong<T, 1>><<<gt, TILE_THREADS, 0, st>>>(
-          g, kc, c,
-          OpProlong<T, 1>{B.za, B.xc, rcur, B.invd, B.coef, B.fm, B.nxc, B.nyc, B.zb, B.lr, B.dv},
-          ws);
-      break;
-    case FS_FINISH:
-      k_damage_op<T, OpFinish<T, 1, false>><<<gt, TILE_THREADS, 0, st>>>(
-          g, kc, c,
-          OpFinish<T, 1, false>{B.dv, B.lr, B.invd, B.coef, rcur, pcur, B.zb, rprev, pprev, B.sc},
-          ws);
-      break;
-    case FS_FINISH_FIRST:
-      k_damage_op<T, OpFinish<T, 1, true>><<<gt, TILE_THREADS, 0, st>>>(
-          g, kc, c,
-          OpFinish<T, 1, true>{B.dv, B.lr, B.invd, B.coef, rcur, pcur, B.zb, rprev, pprev, B.sc},
-          ws);
-      break;
-  }
+  stage_op<T, 1>(stage, B, [&](auto op) {
+    k_damage_op<T, decltype(op)><<<gt, TILE_THREADS, 0, st>>>(g, kc, c, op, ws);
+  });
 }
+
+template <class T>
+int damage_mg_stage_batch(int stage, int n, const DamageStageIn<T> *in, cudaStream_t st) {
+  int launches = 0;
+  stage_op<T, 1>(stage, in[0].B, [&](auto op0) {
+    using Op = decltype(op0);
+    Batcher<DamageF<T, Op>, TILE_THREADS, sizeof(T) == 4 ? 8 : 4> b;
+    for (int i = 0; i < n; ++i) {
+      const DamageStageIn<T> &q = in[i];
+      const ElemConst<T> kc = elem_const<T>(q.g, MatD{}, q.kappa);
+      stage_op<T, 1>(stage, q.B, [&](auto op) {
+        if constexpr (std::is_same<decltype(op), Op>::value) {
+          if (b.L.n == PF_MAXB) { launches += b.launch(st); b = {}; }
+          b.add(DamageF<T, Op>{q.g, kc, q.c, op, q.ws}, tile_count(q.g), &q.B.sc->done);
+        }
+      });
+    }
+    launches += b.launch(st);
+  });
+  return launches;
+}
+
 template <class T>
 void damage_diag(const GridD &g, const T *c, double kappa, T *diag, cudaStream_t st) {
   k_damage<T, T, DM_DIAG><<<tile_grid(g), TILE_THREADS, 0, st>>>(
@@ -1006,6 +1083,8 @@ template void elas_diag<float>(const GridD &, const MatD &, const float *, const
 template void elas_mg_stage<double>(int, const GridD &, const MatD &, const double *,
                                     const uint8_t *, const MgBufs<double> &, const RedWs &,
                                     cudaStream_t);
+template int elas_mg_stage_batch<float>(int, int, const ElasStageIn<float> *, cudaStream_t);
+template int damage_mg_stage_batch<float>(int, int, const DamageStageIn<float> *, cudaStream_t);
 template void elas_mg_stage<float>(int, const GridD &, const MatD &, const float *,
                                    const uint8_t *, const MgBufs<float> &, const RedWs &,
                                    cudaStream_t);

@@ -15,9 +15,15 @@
 #include <string.h>
 
 #include <chrono>
+#include <condition_variable>
+#include <map>
+#include <mutex>
 #include <new>
+#include <thread>
+#include <type_traits>
 #include <vector>
 
+#include "pf_batch.cuh"
 #include "pf_gmg.cuh"
 #include "pf_spectral.cuh"
 #include "pf_internal.cuh"
@@ -107,6 +113,51 @@ struct pf_ctx {
   double *dscal = nullptr;   // device scalars for norms / residual / reaction
   double *hbuf = nullptr;    // pinned host mirror
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  pf_batch *batch = nullptr;   // batch this context is attached to (pf_batch_attach)
+  bool batching = false;       // inside a load step whose FP32 multigrid solves are batched
+  cudaEvent_t evb = nullptr;   // marks the context's work before a batched solve
+};
+
+// ---- batched solves ----------------------------------------------------------------------
+// A batch (pf_batch_*) joins the FP32 multigrid Krylov solves of the contexts attached to
+// it: every context runs its load step on its own host thread, and when all of them wait
+// for such a solve the last to arrive launches them together: one captured CUDA graph per
+// set of participants, whose kernels run each fused stage, multigrid level and coarse
+// cycle of all participants in one launch (pf_batch.cuh), with a device-side loop that
+// stops each participant's iteration on its own test.  Each participant's arithmetic is
+// that of its own solve, so results are bit-identical alone and in any batch.
+struct BatchReq {
+  pf_ctx *ctx = nullptr;
+  int kind = 0;                 // 0: elasticity (B = 2), 1: phase field (B = 1)
+  Gmg<float> *G = nullptr;
+  ElasStageIn<float> e{};
+  DamageStageIn<float> dm{};
+  double rtol = 0.0;
+  int maxit = 0;
+  int iters = 0;
+  bool ok = false;
+  pf_status status = PF_OK;
+  bool finished = false;
+};
+
+struct BatchGraph {
+  cudaGraphExec_t exec = nullptr;
+  int init_launches = 0, body_launches = 0;
+};
+
+struct pf_batch {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  std::mutex mu;
+  std::condition_variable cv;
+  int active = 0;               // attached contexts inside a batched load step
+  bool leading = false;         // a thread is running a batch
+  std::vector<BatchReq *> pending;
+  std::map<std::vector<uintptr_t>, BatchGraph> graphs;   // by kind and participants
+  std::vector<pf_ctx *> members;
+  int64_t launches = 0;         // kernel launches of batched solves
+  int64_t solves = 0, groups = 0;
+  int max_group = 0;
 };
 
 namespace {
@@ -289,7 +340,8 @@ pf_status krylov_run(pf_ctx *ctx, int sidx, Init init, Body body, int every, dou
     KrylovScal *hk = host_scal(ctx);
     hk->rtol2 = rtol * rtol;
     hk->maxit = maxit;
-    CK(cudaMemcpyAsync(&ctx->sc->rtol2, &hk->rtol2, sizeof(double) + sizeof(int),
+    hk->done = 0;
+    CK(cudaMemcpyAsync(&ctx->sc->rtol2, &hk->rtol2, sizeof(double) + 2 * sizeof(int),
                        cudaMemcpyHostToDevice, st));
     CK(cudaGraphLaunch(W.exec, st));
     CK(cudaMemcpyAsync(hk, ctx->sc, sizeof(KrylovScal), cudaMemcpyDeviceToHost, st));
@@ -362,10 +414,8 @@ pf_status pcg(pf_ctx *ctx, int slot, Apply apply, Fine fine, Gmg<T> *G, size_t n
 // operator.  Needs a hierarchy with at least one grid level above the single-CTA coarse
 // cycle (G.lc >= 1).  Level-0 vectors of the hierarchy serve as the second residual and
 // direction buffers and as smoother scratch.
-template <class T, class Stage>
-pf_status pcg_mg_fused(pf_ctx *ctx, int sidx, Gmg<T> &G, Stage stage_fn, const T *b, T *x,
-                       T *r, T *z, T *p, T *q, double rtol, int maxit, int *iters, bool *ok) {
-  cudaStream_t st = ctx->st;
+template <class T>
+MgBufs<T> mg_bufs(pf_ctx *ctx, Gmg<T> &G, const T *b, T *x, T *r, T *z, T *p, T *q) {
   GmgLevel<T> &L0 = G.lv[0];
   MgBufs<T> B;
   B.b = b;
@@ -386,6 +436,15 @@ pf_status pcg_mg_fused(pf_ctx *ctx, int sidx, Gmg<T> &G, Stage stage_fn, const T
   B.nxc = G.lv[1].nx;
   B.nyc = G.lv[1].ny;
   B.sc = ctx->sc;
+  return B;
+}
+
+template <class T, class Stage>
+pf_status pcg_mg_fused(pf_ctx *ctx, int sidx, Gmg<T> &G, Stage stage_fn, const T *b, T *x,
+                       T *r, T *z, T *p, T *q, double rtol, int maxit, int *iters, bool *ok) {
+  cudaStream_t st = ctx->st;
+  GmgLevel<T> &L0 = G.lv[0];
+  const MgBufs<T> B = mg_bufs<T>(ctx, G, b, x, r, z, p, q);
   auto stage = [&](int s) { stage_fn(s, B); };
   // residual, restriction, coarse levels and post-smoothing of the V-cycle on r[1]
   auto vcycle_rest = [&](bool first) -> int {
@@ -410,9 +469,219 @@ pf_status pcg_mg_fused(pf_ctx *ctx, int sidx, Gmg<T> &G, Stage stage_fn, const T
   return krylov_run(ctx, sidx, init, body, every, rtol, maxit, iters, ok);
 }
 
+// Capture the batched solve of group g (one kind, at most PF_MAXB participants): the
+// initialisation, then a conditional WHILE node whose body is one iteration of every
+// participant and the batched loop condition.  Kernel order per participant is that of
+// pcg_mg_fused.
+cudaError_t build_batch_graph(pf_batch *b, const std::vector<BatchReq *> &g, BatchGraph &W) {
+  const int n = (int)g.size();
+  const int kind = g[0]->kind;
+  cudaStream_t st = b->st;
+  ElasStageIn<float> ein[PF_MAXB];
+  DamageStageIn<float> din[PF_MAXB];
+  Gmg<float> *G[PF_MAXB];
+  const int *done[PF_MAXB];
+  KrylovScal *sc[PF_MAXB];
+  for (int i = 0; i < n; ++i) {
+    ein[i] = g[i]->e;
+    din[i] = g[i]->dm;
+    G[i] = g[i]->G;
+    sc[i] = g[i]->ctx->sc;
+    done[i] = &sc[i]->done;
+  }
+  auto stage = [&](int s) {
+    return kind == 0 ? elas_mg_stage_batch<float>(s, n, ein, st)
+                     : damage_mg_stage_batch<float>(s, n, din, st);
+  };
+  auto vrest = [&](bool first) {
+    int nl = stage(FS_RESID);
+    nl += gmg_restrict0_batch<float>(n, G, done, st);
+    nl += gmg_mid_batch<float>(n, G, done, st);
+    nl += stage(FS_PROLONG);
+    nl += stage(first ? FS_FINISH_FIRST : FS_FINISH);
+    return nl;
+  };
+  cudaGraph_t gi = nullptr, gr = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  W.init_launches = stage(FS_UPD_INIT) + vrest(true);
+  if ((e = cudaStreamEndCapture(st, &gi)) != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  cudaGraphNode_t ni, nc;
+  cudaGraphNodeParams cp = {};
+  if ((e = cudaGraphCreate(&gr, 0)) != cudaSuccess) goto done;
+  if ((e = cudaGraphConditionalHandleCreate(&h, gr, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+    goto done;
+  if ((e = cudaGraphAddChildGraphNode(&ni, gr, nullptr, 0, gi)) != cudaSuccess) goto done;
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if ((e = cudaGraphAddNode(&nc, gr, &ni, nullptr, 1, &cp)) != cudaSuccess) goto done;
+  {
+    cudaGraph_t bg = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(st, bg, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) goto done;
+    W.body_launches = stage(FS_DIR) + stage(FS_UPD) + vrest(false) + 1;
+    krylov_while_batch(h, n, sc, st);
+    if ((e = cudaStreamEndCapture(st, &bg)) != cudaSuccess) goto done;
+  }
+  e = cudaGraphInstantiate(&W.exec, gr, 0);
+  if (e != cudaSuccess) W.exec = nullptr;
+done:
+  if (gi) cudaGraphDestroy(gi);
+  if (gr) cudaGraphDestroy(gr);
+  return e;
+}
+
+// Run one group on the batch stream after each participant's earlier work, and hand each
+// participant the result its own solve would give (krylov_run's device-loop branch).
+void run_group(pf_batch *b, const std::vector<BatchReq *> &g) {
+  cudaStream_t st = b->st;
+  std::vector<uintptr_t> key;
+  key.push_back((uintptr_t)g[0]->kind);
+  for (BatchReq *r : g) {
+    key.push_back((uintptr_t)r->ctx);
+    if (r->kind == 1) {   // the captured kernels carry the gradient coefficient
+      uint64_t kb;
+      memcpy(&kb, &r->dm.kappa, sizeof(kb));
+      key.push_back((uintptr_t)kb);
+    }
+  }
+  BatchGraph &W = b->graphs[key];
+  cudaError_t e = cudaSuccess;
+  if (!W.exec) e = build_batch_graph(b, g, W);
+  if (e != cudaSuccess || !W.exec) {
+    cudaGetLastError();
+    for (BatchReq *r : g)
+      r->status = set_err(r->ctx, PF_ECUDA, "batched solve graph: %s", cudaGetErrorString(e));
+    b->graphs.erase(key);
+    return;
+  }
+  for (BatchReq *r : g) {
+    KrylovScal *hk = host_scal(r->ctx);
+    hk->rtol2 = r->rtol * r->rtol;
+    hk->maxit = r->maxit;
+    hk->done = 0;
+    cudaStreamWaitEvent(st, r->ctx->evb, 0);
+    cudaMemcpyAsync(&r->ctx->sc->rtol2, &hk->rtol2, sizeof(double) + 2 * sizeof(int),
+                    cudaMemcpyHostToDevice, st);
+  }
+  cudaGraphLaunch(W.exec, st);
+  for (BatchReq *r : g)
+    cudaMemcpyAsync(host_scal(r->ctx), r->ctx->sc, sizeof(KrylovScal), cudaMemcpyDeviceToHost, st);
+  e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  int most = 0;
+  for (BatchReq *r : g) {
+    if (e != cudaSuccess) {
+      r->status = set_err(r->ctx, PF_ECUDA, "batched solve: %s", cudaGetErrorString(e));
+      continue;
+    }
+    const KrylovScal *hk = host_scal(r->ctx);
+    most = hk->it > most ? hk->it : most;
+    if (!(hk->rr0 > 0.0)) {
+      r->iters = 0;
+      r->ok = true;
+    } else {
+      r->iters = hk->it;
+      r->ok = hk->rr <= hk->rtol2 * hk->rr0;
+    }
+  }
+  std::lock_guard<std::mutex> lk(b->mu);
+  b->launches += W.init_launches + (int64_t)most * W.body_launches;
+  b->solves += (int64_t)g.size();
+  b->groups += 1;
+  b->max_group = (int)g.size() > b->max_group ? (int)g.size() : b->max_group;
+}
+
+void run_batch(pf_batch *b, const std::vector<BatchReq *> &reqs) {
+  cudaSetDevice(b->device);
+  for (int kind = 0; kind < 2; ++kind) {
+    std::vector<BatchReq *> g;
+    for (BatchReq *r : reqs) {
+      if (r->kind != kind) continue;
+      g.push_back(r);
+      if ((int)g.size() == PF_MAXB) {
+        run_group(b, g);
+        g.clear();
+      }
+    }
+    if (!g.empty()) run_group(b, g);
+  }
+}
+
+// Submit one solve and wait for it.  When every context of the batch that is inside a
+// load step waits for a solve, the thread that sees it runs them all.
+pf_status batch_solve(pf_ctx *ctx, BatchReq &req, int *iters, bool *ok) {
+  pf_batch *b = ctx->batch;
+  CK(cudaEventRecord(ctx->evb, ctx->st));
+  std::unique_lock<std::mutex> lk(b->mu);
+  b->pending.push_back(&req);
+  while (!req.finished) {
+    if (!b->leading && (int)b->pending.size() >= b->active) {
+      b->leading = true;
+      std::vector<BatchReq *> reqs;
+      reqs.swap(b->pending);
+      lk.unlock();
+      run_batch(b, reqs);
+      lk.lock();
+      for (BatchReq *r : reqs) r->finished = true;
+      b->leading = false;
+      b->cv.notify_all();
+      continue;
+    }
+    b->cv.wait(lk);
+  }
+  lk.unlock();
+  *iters = req.iters;
+  *ok = req.ok;
+  return req.status;
+}
+
+bool batch_eligible(const pf_ctx *c) {
+  return c->precision == PF_FP32_IR && c->precond == PF_PRECOND_GMG &&
+         c->m.split == PF_SPLIT_VD && c->opt.device_loop && c->gu32.lc >= 1 && c->gd32.lc >= 1;
+}
+
+// A load step of an attached context whose FP32 multigrid solves go through its batch.
+struct BatchScope {
+  pf_ctx *ctx;
+  bool on = false;
+  explicit BatchScope(pf_ctx *c) : ctx(c) {
+    if (!c->batch || !batch_eligible(c)) return;
+    std::lock_guard<std::mutex> lk(c->batch->mu);
+    c->batch->active++;
+    c->batching = on = true;
+  }
+  ~BatchScope() {
+    if (!on) return;
+    {
+      std::lock_guard<std::mutex> lk(ctx->batch->mu);
+      ctx->batch->active--;
+      ctx->batching = false;
+    }
+    ctx->batch->cv.notify_all();
+  }
+};
+
 template <class T>
 pf_status pcg_mg_elas(pf_ctx *ctx, Gmg<T> &G, const T *d, const T *b, T *x, T *r, T *z, T *p,
                       T *q, double rtol, int maxit, int *iters, bool *ok) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (ctx->batching) {
+      BatchReq req;
+      req.ctx = ctx;
+      req.kind = 0;
+      req.G = &G;
+      req.e = ElasStageIn<float>{ctx->g, ctx->m, d, ctx->tens,
+                                 mg_bufs<float>(ctx, G, b, x, r, z, p, q), ctx->ws};
+      req.rtol = rtol;
+      req.maxit = maxit;
+      return batch_solve(ctx, req, iters, ok);
+    }
+  }
   auto stage = [ctx, d](int s, const MgBufs<T> &B) {
     elas_mg_stage<T>(s, ctx->g, ctx->m, d, ctx->tens, B, ctx->ws, ctx->st);
   };
@@ -422,6 +691,19 @@ pf_status pcg_mg_elas(pf_ctx *ctx, Gmg<T> &G, const T *d, const T *b, T *x, T *r
 template <class T>
 pf_status pcg_mg_damage(pf_ctx *ctx, Gmg<T> &G, const T *c, double kappa, const T *b, T *x,
                         T *r, T *z, T *p, T *q, double rtol, int maxit, int *iters, bool *ok) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (ctx->batching) {
+      BatchReq req;
+      req.ctx = ctx;
+      req.kind = 1;
+      req.G = &G;
+      req.dm = DamageStageIn<float>{ctx->g, c, kappa, mg_bufs<float>(ctx, G, b, x, r, z, p, q),
+                                    ctx->ws};
+      req.rtol = rtol;
+      req.maxit = maxit;
+      return batch_solve(ctx, req, iters, ok);
+    }
+  }
   auto stage = [ctx, c, kappa](int s, const MgBufs<T> &B) {
     damage_mg_stage<T>(s, ctx->g, c, kappa, B, ctx->ws, ctx->st);
   };
@@ -1008,6 +1290,7 @@ void free_all(pf_ctx *c) {
   for (WhileGraph &w : c->wgraphs)
     if (w.exec) cudaGraphExecDestroy(w.exec);
   if (c->hbuf) cudaFreeHost(c->hbuf);
+  if (c->evb) cudaEventDestroy(c->evb);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -1250,6 +1533,7 @@ pf_status pf_load_step(pf_ctx *ctx, double d_ubar, int scheme, double tol,
   if (scheme < PF_ST || scheme > PF_S3 || !(tol > 0) || !isfinite(d_ubar))
     return set_err(ctx, PF_EINVAL, "invalid scheme/tol/d_ubar");
   CK(cudaSetDevice(ctx->device));
+  BatchScope batch_scope(ctx);
   PhaseTimer tm_all(&ctx->prof[PF_PROF_TOTAL]);
   pf_step_result r;
   memset(&r, 0, sizeof(r));
@@ -1390,10 +1674,136 @@ const char *pf_last_error(const pf_ctx *ctx) { return ctx ? ctx->err : "null con
 
 void pf_destroy(pf_ctx *ctx) {
   if (!ctx) return;
+  if (ctx->batch) pf_batch_detach(ctx->batch, ctx);
   cudaSetDevice(ctx->device);
   if (ctx->st) cudaStreamSynchronize(ctx->st);
   free_all(ctx);
   delete ctx;
+}
+
+// ---- batches (pf_batch_*) ------------------------------------------------------------------
+pf_status pf_batch_create(pf_batch **out) {
+  if (!out) return PF_EINVAL;
+  *out = nullptr;
+  pf_batch *b = new (std::nothrow) pf_batch();
+  if (!b) return PF_ENOMEM;
+  cudaGetDevice(&b->device);
+  if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return PF_ECUDA;
+  }
+  *out = b;
+  return PF_OK;
+}
+
+pf_status pf_batch_attach(pf_batch *b, pf_ctx *ctx) {
+  if (!b || !ctx) return PF_EINVAL;
+  if (ctx->batch)
+    return ctx->batch == b ? PF_OK : set_err(ctx, PF_EBUSY, "context is attached to another batch");
+  if (ctx->device != b->device)
+    return set_err(ctx, PF_EINVAL, "batch and context are on different devices");
+  CK(cudaSetDevice(ctx->device));
+  if (ctx->precision == PF_FP32_IR && ctx->precond == PF_PRECOND_GMG) {
+    if ((ctx->gu32.lc >= 1 && gmg_batch_prepare<float>(ctx->gu32) != cudaSuccess) ||
+        (ctx->gd32.lc >= 1 && gmg_batch_prepare<float>(ctx->gd32) != cudaSuccess))
+      return set_err(ctx, PF_ENOMEM, "batch: coarse-cycle arguments");
+  }
+  if (!ctx->evb && cudaEventCreateWithFlags(&ctx->evb, cudaEventDisableTiming) != cudaSuccess)
+    return set_err(ctx, PF_ECUDA, "batch: event");
+  std::lock_guard<std::mutex> lk(b->mu);
+  b->members.push_back(ctx);
+  ctx->batch = b;
+  return PF_OK;
+}
+
+pf_status pf_batch_detach(pf_batch *b, pf_ctx *ctx) {
+  if (!b || !ctx || ctx->batch != b) return PF_EINVAL;
+  std::unique_lock<std::mutex> lk(b->mu);
+  if (ctx->batching) return set_err(ctx, PF_EBUSY, "batch: context is inside a load step");
+  b->cv.wait(lk, [b]() { return !b->leading; });   // graphs are in use while a batch runs
+  for (auto it = b->graphs.begin(); it != b->graphs.end();) {
+    bool has = false;
+    for (size_t k = 1; k < it->first.size(); ++k) has = has || it->first[k] == (uintptr_t)ctx;
+    if (has) {
+      if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+      it = b->graphs.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  for (size_t k = 0; k < b->members.size(); ++k)
+    if (b->members[k] == ctx) {
+      b->members.erase(b->members.begin() + (long)k);
+      break;
+    }
+  ctx->batch = nullptr;
+  return PF_OK;
+}
+
+pf_status pf_batch_load_step(pf_batch *b, int n, pf_ctx *const *ctx, const double *d_ubar,
+                             const int *scheme, const double *tol, pf_step_result *res,
+                             pf_status *status) {
+  if (!b || n < 1 || !ctx || !d_ubar || !scheme || !tol) return PF_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!ctx[i] || ctx[i]->batch != b) return PF_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctx[j] == ctx[i]) return PF_EINVAL;
+  }
+  std::vector<pf_status> st(n, PF_OK);
+  std::vector<pf_step_result> rs(n);
+  auto one = [&](int i) { st[i] = pf_load_step(ctx[i], d_ubar[i], scheme[i], tol[i], &rs[i]); };
+  std::vector<std::thread> th;
+  try {
+    for (int i = 1; i < n; ++i) th.emplace_back(one, i);
+  } catch (...) {
+    for (std::thread &t : th) t.join();
+    return PF_ENOMEM;
+  }
+  one(0);
+  for (std::thread &t : th) t.join();
+  pf_status worst = PF_OK;
+  for (int i = 0; i < n; ++i) {
+    if (res) res[i] = rs[i];
+    if (status) status[i] = st[i];
+    if (st[i] != PF_OK && (worst == PF_OK || worst == PF_ENOTCONV)) worst = st[i];
+  }
+  return worst;
+}
+
+pf_status pf_batch_stats(const pf_batch *b, int64_t *launches, int64_t *solves, int64_t *groups,
+                         int *max_group) {
+  if (!b) return PF_EINVAL;
+  std::lock_guard<std::mutex> lk(const_cast<pf_batch *>(b)->mu);
+  if (launches) *launches = b->launches;
+  if (solves) *solves = b->solves;
+  if (groups) *groups = b->groups;
+  if (max_group) *max_group = b->max_group;
+  return PF_OK;
+}
+
+void pf_batch_destroy(pf_batch *b) {
+  if (!b) return;
+  while (true) {
+    pf_ctx *c = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(b->mu);
+      if (b->members.empty()) break;
+      c = b->members.back();
+    }
+    if (pf_batch_detach(b, c) != PF_OK) {   // still running: drop it from the list anyway
+      std::lock_guard<std::mutex> lk(b->mu);
+      b->members.pop_back();
+      c->batch = nullptr;
+    }
+  }
+  for (auto &kv : b->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  if (b->st) {
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->st);
+    cudaStreamDestroy(b->st);
+  }
+  delete b;
 }
 
 }  // extern "C"

@@ -5,6 +5,7 @@
 
 #include "pf_internal.cuh"
 #include "pf_vec.cuh"
+#include "pf_batch.cuh"
 
 namespace pf {
 
@@ -162,6 +163,29 @@ __global__ void k_krylov_while(cudaGraphConditionalHandle h, KrylovScal *sc) {
   sc->it = it;
   const bool more = sc->rr > sc->rtol2 * sc->rr0 && !sc->breakdown && it < sc->maxit;
   cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// Batched form: each simulation that has not stopped counts its iteration and stops on the
+// single solve's test (so it runs exactly the iterations it runs alone); the loop goes on
+// while any simulation has not stopped.
+struct ScalSet {
+  int n;
+  KrylovScal *sc[PF_MAXB];
+};
+__global__ void k_krylov_while_batch(cudaGraphConditionalHandle h, ScalSet s) {
+  bool any = false;
+  for (int i = 0; i < s.n; ++i) {
+    KrylovScal *k = s.sc[i];
+    if (k->done) continue;
+    const int it = k->it + 1;
+    k->it = it;
+    const bool more = k->rr > k->rtol2 * k->rr0 && !k->breakdown && it < k->maxit;
+    if (more)
+      any = true;
+    else
+      k->done = 1;
+  }
+  cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
 // ---- helpers ---------------------------------------------------------------------------
@@ -356,6 +380,13 @@ void fill(size_t n, double v, double *y, cudaStream_t st) {
 }
 void krylov_while(cudaGraphConditionalHandle h, KrylovScal *sc, cudaStream_t st) {
   k_krylov_while<<<1, 1, 0, st>>>(h, sc);
+}
+void krylov_while_batch(cudaGraphConditionalHandle h, int n, KrylovScal *const *sc,
+                        cudaStream_t st) {
+  ScalSet s;
+  s.n = n < PF_MAXB ? n : PF_MAXB;
+  for (int i = 0; i < s.n; ++i) s.sc[i] = sc[i];
+  k_krylov_while_batch<<<1, 1, 0, st>>>(h, s);
 }
 void masked_comb(size_t n, int ncomp, const uint8_t *dofm, double s, const double *a, double t,
                  const double *b, double *out, cudaStream_t st) {

@@ -101,3 +101,13 @@ def test_operator_calls_reject_an_unknown_split(L):
                              None) == binding.PF_EINVAL
     assert L.pf_op_elas_tangent_qp(ctypes.byref(g), ctypes.byref(m), fake, fake, fake,
                                    None) == binding.PF_EINVAL
+
+
+def test_batch_entry_points_reject_bad_arguments(L):
+    # no device work: argument checks come first
+    assert L.pf_batch_create(None) == binding.PF_EINVAL
+    assert L.pf_batch_attach(None, None) == binding.PF_EINVAL
+    assert L.pf_batch_detach(None, None) == binding.PF_EINVAL
+    assert L.pf_batch_load_step(None, 1, None, None, None, None, None, None) == binding.PF_EINVAL
+    assert L.pf_batch_stats(None, None, None, None, None) == binding.PF_EINVAL
+    L.pf_batch_destroy(None)
