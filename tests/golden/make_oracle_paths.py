@@ -11,7 +11,7 @@ passes at the finer grid), so they are stored rather than recomputed by the test
     python tests/golden/make_oracle_paths.py merge             # join the parts
 
 Cases:
-  tensile64   64 x 64, l = 0.03 mm, 20 steps to 6e-3 mm, ST, TOL_ST 1e-7 (the plain
+  tensile64   64 x 64, l = 0.03 mm, 20 steps to 6e-3 mm, ST, TOL_ST 1e-9 (the plain
               standard-scheme benchmark in FP64), phase field at every step.
   tensile128  128 x 128, l = 0.03 mm (l/h = 3.84, the l/h of the 512 x 512 workload with
               l = 0.0075 mm), 100 steps to 6e-3 mm, ST/S1/S2/S3, TOL_ST 1e-5, phase field
@@ -32,7 +32,7 @@ from oracle import model, q1, staggered as stg  # noqa: E402
 from paper_2209_07969_gb300 import specimens as S  # noqa: E402
 
 CASES = {
-    "tensile64": dict(n=64, l=0.03, steps=20, schemes=(0,), tol=1e-7,
+    "tensile64": dict(n=64, l=0.03, steps=20, schemes=(0,), tol=1e-9,
                       keep=tuple(range(1, 21))),
     "tensile128": dict(n=128, l=0.03, steps=100, schemes=(0, 1, 2, 3), tol=1e-5,
                        keep=(40, 60, 80, 100)),

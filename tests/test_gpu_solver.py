@@ -148,7 +148,7 @@ def test_exact_newton_corrections_match_checker(gpu):
 
 
 @pytest.mark.parametrize("precond", PRECONDS)
-@pytest.mark.parametrize("scheme", [0, 1, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
 def test_tensile_path_fp32_refined(gpu, scheme, precond):
     # At the crack step the iteration passes an unstable equilibrium whose residual minimum
     # (2-5e-7 in the checker on x86) is set by rounding; at a tolerance of 1e-7 either code
