@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--executor", default="batched", choices=["batched", "streams"],
                    help="batched: pf_batch (shared launches); streams: one stream per simulation")
     p.add_argument("--max-stag", type=int, default=20000)
+    p.add_argument("--no-tune", action="store_true", help="skip pf_autotune")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end whole path")
     p.add_argument("--no-fp64", action="store_true",
                    help="skip the FP64-form comparison on the 128 x 128 path")
@@ -289,7 +290,7 @@ class Runner:
     """B simulations of one specimen and the executor that advances them."""
 
     def __init__(self, spec, B, executor, split, max_stag, host_loop=False, scheme=1,
-                 precision=None):
+                 precision=None, tune=False):
         from paper_2209_07969_gb300 import binding
         self.binding = binding
         self.spec, self.B, self.scheme = spec, B, scheme
@@ -298,6 +299,8 @@ class Runner:
                                         split=split) for _ in range(B)]
         for s in self.sims:
             s.set_options(max_stag=max_stag, device_loop=0 if host_loop else 1)
+        # launch shapes timed on this grid (pf_autotune) before the first load step
+        self.tuning = [s.autotune() for s in self.sims] if tune else None
         self.batch = binding.Batch(self.sims) if executor == "batched" else None
         self.init = [s.get_state() for s in self.sims]
         self.results = [[] for _ in range(B)]
@@ -402,7 +405,7 @@ def run_ours(args):
     split = binding.SPLIT_SPECTRAL if args.split == "spectral" else binding.SPLIT_VD
     B = args.batch
     R = Runner(spec, B, args.executor, split, args.max_stag, args.host_loop,
-               binding.SCHEMES[args.scheme])
+               binding.SCHEMES[args.scheme], tune=not args.no_tune and split == binding.SPLIT_VD)
     bounds = chunks(args.steps)
     K = len(bounds) - 1
     nn = (spec.nx + 1) * (spec.ny + 1)
@@ -482,6 +485,7 @@ def run_ours(args):
                                       "load paths"
                                       + ("; spectral energy split" if split else ""),
                           "batch": B, "executor": args.executor,
+                          "autotune": (R.tuning[0] if R.tuning else None),
                           "load_steps_per_bench_step": bounds[1] - bounds[0],
                           "l2": "working set per simulation ~0.2 GB; every load step reads "
                                 "the operator data anew"},

@@ -153,7 +153,9 @@ void pf_default_options(pf_options *opt);
 pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double l,
                     double k_res, pf_ctx **out);
 /* Device bytes pf_create allocates for this mesh (0 for an invalid mesh); a scheduler
- * admits simulations by this footprint. */
+ * admits simulations by this footprint.  Exact: pf_create takes every array of the
+ * context from one allocation of this size (each array 256-byte aligned); the driver's
+ * page rounding (up to 2 MiB) and pf_batch_attach's few hundred bytes come on top. */
 size_t pf_footprint_bytes(const pf_mesh *mesh);
 pf_status pf_set_options(pf_ctx *ctx, const pf_options *opt);
 pf_status pf_get_options(const pf_ctx *ctx, pf_options *opt);
@@ -201,6 +203,30 @@ pf_status pf_profile(pf_ctx *ctx, double *ms, int n, int reset);
 const char *pf_last_error(const pf_ctx *ctx);
 const char *pf_status_string(pf_status s);
 void pf_destroy(pf_ctx *ctx);
+
+/* ------------------------------------------------------------------------------------
+ * Autotuning.  Launch shapes of the FP32 multigrid solve timed on the context's own grid
+ * (CUDA events on its stream, 3 untimed and 10 timed launches each) and fixed for its
+ * later load steps: the node rows per warp of the strip kernel that applies the FP32
+ * elasticity tangent (2, 4 or 8) and the largest level, in nodes, that the single-CTA
+ * coarse cycle takes (300, 1100 or 4300; larger levels run as grid-wide kernels).  Both
+ * change only how the work is split into launches and CTAs, not the method; reductions
+ * are grouped differently, so results can change in the last bits.  The paper has no
+ * counterpart (it names no hardware mapping).
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+  int strip_rows;          /* chosen rows per warp; 0 = grid-size rule (not tuned) */
+  int coarse_nodes;        /* chosen single-CTA coarse-cycle limit; 0 = built-in 1100 */
+  double apply_us[3];      /* FP32 tangent apply, strip rows 2, 4, 8 (0: not timed) */
+  double vcycle_us[3];     /* V-cycle below the fine level, coarse limits 300, 1100, 4300 */
+} pf_tuning;
+/* Time the candidates and keep the fastest.  Only before the first load step of ctx and
+ * while ctx is not attached to a batch (PF_EBUSY otherwise); PF_EINVAL unless ctx uses
+ * PF_FP32_IR with PF_PRECOND_GMG and the VD split.  out (may be NULL) receives the choice
+ * and the timings. */
+pf_status pf_autotune(pf_ctx *ctx, pf_tuning *out);
+/* The current choice (zeros where pf_autotune has not run). */
+pf_status pf_get_tuning(const pf_ctx *ctx, pf_tuning *out);
 
 /* ------------------------------------------------------------------------------------
  * Batches.  Several simulations advanced together so that their Krylov solves share

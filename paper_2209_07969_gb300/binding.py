@@ -56,6 +56,15 @@ class StepResult(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Tuning(C.Structure):
+    _fields_ = [("strip_rows", C.c_int), ("coarse_nodes", C.c_int),
+                ("apply_us", C.c_double * 3), ("vcycle_us", C.c_double * 3)]
+
+    def as_dict(self):
+        return {"strip_rows": self.strip_rows, "coarse_nodes": self.coarse_nodes,
+                "apply_us": list(self.apply_us), "vcycle_us": list(self.vcycle_us)}
+
+
 class Request(C.Structure):
     _fields_ = [("mesh", Mesh), ("E", C.c_double), ("nu", C.c_double), ("Gc", C.c_double),
                 ("l", C.c_double), ("k_res", C.c_double), ("increments", C.c_void_p),
@@ -111,6 +120,8 @@ _PROTOS = {
     "pf_profile": (S, [P, P, I, I]),
     "pf_last_error": (C.c_char_p, [P]),
     "pf_destroy": (None, [P]),
+    "pf_autotune": (S, [P, C.POINTER(Tuning)]),
+    "pf_get_tuning": (S, [P, C.POINTER(Tuning)]),
     "pf_batch_create": (S, [C.POINTER(P)]),
     "pf_batch_attach": (S, [P, P]),
     "pf_batch_detach": (S, [P, P]),
@@ -275,6 +286,18 @@ class Simulation:
         ms = np.zeros(8)
         check(lib().pf_profile(self.ctx, ms.ctypes.data, 8, int(reset)), "pf_profile", self.ctx)
         return dict(zip(self.PHASES, ms[:7].tolist()))
+
+    def autotune(self):
+        """Time the launch-shape candidates on this grid and keep the fastest
+        (pf_autotune); returns the choice and the timings."""
+        t = Tuning()
+        check(lib().pf_autotune(self.ctx, C.byref(t)), "pf_autotune", self.ctx)
+        return t.as_dict()
+
+    def tuning(self):
+        t = Tuning()
+        check(lib().pf_get_tuning(self.ctx, C.byref(t)), "pf_get_tuning", self.ctx)
+        return t.as_dict()
 
     def launches(self):
         return int(lib().pf_launch_count(self.ctx))

@@ -63,6 +63,7 @@ struct ElasStageIn {
   const uint8_t *tens;
   MgBufs<T> B;
   RedWs ws;
+  int sr;     // strip rows per warp (0: the grid-size rule)
 };
 template <class T>
 struct DamageStageIn {

@@ -776,38 +776,87 @@ __global__ void k_prolong_add(int nxf, int nyf, const uint8_t *__restrict__ fmf,
   }
 }
 
-// FP64 host Cholesky inverse of an SPD matrix (in place); non-positive pivots are
-// lifted to a small fraction of the largest diagonal entry.
-void host_spd_inverse(double *A, int n) {
-  double dmax = 0.0;
-  for (int i = 0; i < n; ++i) dmax = fmax(dmax, A[(size_t)i * n + i]);
-  const double floor_p = (dmax > 0 ? dmax : 1.0) * 1e-14;
-  std::vector<double> L((size_t)n * n, 0.0);
-  for (int j = 0; j < n; ++j) {
-    double s = A[(size_t)j * n + j];
-    for (int k = 0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
-    if (!(s > floor_p)) s = floor_p;
-    const double ljj = sqrt(s);
-    L[(size_t)j * n + j] = ljj;
-    for (int i = j + 1; i < n; ++i) {
-      double t = A[(size_t)i * n + j];
-      for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
-      L[(size_t)i * n + j] = t / ljj;
+// Dense inverse of the coarsest level in one CTA, in FP64: assemble the level's stencil
+// as a dense matrix (rows of non-free DOFs: identity), symmetrise it (the Galerkin product
+// is symmetric up to rounding), invert it in place by Gauss-Jordan elimination without
+// pivoting (the matrix is SPD; a pivot below 1e-14 of the largest diagonal entry is lifted
+// to that value), and write the inverse in T with the rows and columns of non-free DOFs
+// zeroed, so the coarse correction vanishes there.  A: n x n FP64 work array; n <= 256.
+constexpr int COARSE_INV_MAX = 256;
+template <class T, int B>
+__global__ void __launch_bounds__(1024) k_coarse_inverse(int nx, int ny, const T *__restrict__ S,
+                                                         const uint8_t *__restrict__ fm, int n,
+                                                         double *__restrict__ A,
+                                                         T *__restrict__ cinv) {
+  __shared__ double colk[COARSE_INV_MAX], rowk[COARSE_INV_MAX], red[32];
+  __shared__ double pinv_s, floor_s;
+  const int t = threadIdx.x, nt = blockDim.x;
+  const size_t nn = (size_t)(nx + 1) * (ny + 1), n2 = (size_t)n * n;
+  auto is_free = [&](int row) { return (__ldg(fm + row / B) >> (row % B)) & 1; };
+  for (size_t q = t; q < n2; q += nt) A[q] = 0.0;
+  __syncthreads();
+  for (int row = t; row < n; row += nt) {
+    const size_t node = (size_t)(row / B);
+    const int r = row % B;
+    if (!is_free(row)) {
+      A[(size_t)row * n + row] = 1.0;
+      continue;
+    }
+    const int i = (int)(node % (nx + 1)), j = (int)(node / (nx + 1));
+    for (int k = 0; k < 9; ++k) {
+      const int ii = i + k % 3 - 1, jj = j + k / 3 - 1;
+      if (ii < 0 || ii > nx || jj < 0 || jj > ny) continue;
+      const size_t m = (size_t)jj * (nx + 1) + ii;
+      for (int c = 0; c < B; ++c)
+        if ((__ldg(fm + m) >> c) & 1)
+          A[(size_t)row * n + (B * m + c)] = (double)S[sten_idx<B>(k, r, c, node, nn)];
     }
   }
-  // inverse via solves with unit vectors
-  std::vector<double> y(n);
-  for (int c = 0; c < n; ++c) {
-    for (int i = 0; i < n; ++i) {
-      double t = (i == c) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) t -= L[(size_t)i * n + k] * y[k];
-      y[i] = t / L[(size_t)i * n + i];
+  __syncthreads();
+  for (size_t q = t; q < n2; q += nt) {
+    const size_t i = q / n, j = q % n;
+    if (i < j) {
+      const double v = 0.5 * (A[i * n + j] + A[j * n + i]);
+      A[i * n + j] = A[j * n + i] = v;
     }
-    for (int i = n - 1; i >= 0; --i) {
-      double t = y[i];
-      for (int k = i + 1; k < n; ++k) t -= L[(size_t)k * n + i] * A[(size_t)k * n + c];
-      A[(size_t)i * n + c] = t / L[(size_t)i * n + i];
+  }
+  __syncthreads();
+  double dm = 0.0;
+  for (int i = t; i < n; i += nt) dm = fmax(dm, A[(size_t)i * n + i]);
+  dm = red_warp(dm, true);
+  if ((t & 31) == 0) red[t >> 5] = dm;
+  __syncthreads();
+  if (t == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (nt + 31) / 32; ++w) m = fmax(m, red[w]);
+    floor_s = (m > 0.0 ? m : 1.0) * 1e-14;
+  }
+  for (int k = 0; k < n; ++k) {
+    __syncthreads();
+    for (int i = t; i < n; i += nt) colk[i] = A[(size_t)i * n + k];
+    if (t == 0) {
+      double p = A[(size_t)k * n + k];
+      if (!(p > floor_s)) p = floor_s;
+      pinv_s = 1.0 / p;
     }
+    __syncthreads();
+    const double pinv = pinv_s;
+    for (int j = t; j < n; j += nt) {
+      const double v = (j == k ? 1.0 : A[(size_t)k * n + j]) * pinv;
+      rowk[j] = v;
+      A[(size_t)k * n + j] = v;
+    }
+    __syncthreads();
+    for (size_t q = t; q < n2; q += nt) {
+      const int i = (int)(q / n), j = (int)(q % n);
+      if (i == k) continue;
+      A[q] = (j == k ? 0.0 : A[q]) - colk[i] * rowk[j];
+    }
+  }
+  __syncthreads();
+  for (size_t q = t; q < n2; q += nt) {
+    const int i = (int)(q / n), j = (int)(q % n);
+    cinv[q] = (is_free(i) && is_free(j)) ? (T)A[q] : T(0);
   }
 }
 
@@ -815,7 +864,7 @@ void host_spd_inverse(double *A, int n) {
 
 // ---- host side ------------------------------------------------------------------------------
 template <class T>
-cudaError_t gmg_alloc(Gmg<T> &G, int nx, int ny, int B, const RedWs &ws) {
+cudaError_t gmg_alloc(Gmg<T> &G, int nx, int ny, int B, const RedWs &ws, Arena &A) {
   G.B = B;
   G.ws = ws;
   int l = 0;
@@ -826,18 +875,17 @@ cudaError_t gmg_alloc(Gmg<T> &G, int nx, int ny, int B, const RedWs &ws) {
     L.ny = cy;
     L.nn = (size_t)(cx + 1) * (cy + 1);
     const size_t nb = (size_t)B * L.nn;
-    G.nl = l + 1;   // gmg_free releases a partly allocated hierarchy up to this level
-    cudaError_t e;
-    if ((e = cudaMalloc(&L.S, 9 * B * B * L.nn * sizeof(T))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&L.invd, nb * sizeof(T))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&L.x, nb * sizeof(T))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&L.b, nb * sizeof(T))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&L.r, nb * sizeof(T))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&L.dv, nb * sizeof(T))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&L.y, nb * sizeof(T))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&L.fm, L.nn)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&L.lmax, sizeof(double))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&L.coef, 4 * sizeof(T))) != cudaSuccess) return e;
+    G.nl = l + 1;
+    if (!A.take(&L.S, 9 * B * B * L.nn)) return cudaErrorMemoryAllocation;
+    if (!A.take(&L.invd, nb)) return cudaErrorMemoryAllocation;
+    if (!A.take(&L.x, nb)) return cudaErrorMemoryAllocation;
+    if (!A.take(&L.b, nb)) return cudaErrorMemoryAllocation;
+    if (!A.take(&L.r, nb)) return cudaErrorMemoryAllocation;
+    if (!A.take(&L.dv, nb)) return cudaErrorMemoryAllocation;
+    if (!A.take(&L.y, nb)) return cudaErrorMemoryAllocation;
+    if (!A.take(&L.fm, L.nn)) return cudaErrorMemoryAllocation;
+    if (!A.take(&L.lmax, 1)) return cudaErrorMemoryAllocation;
+    if (!A.take(&L.coef, 4)) return cudaErrorMemoryAllocation;
     ++l;
     if ((cx <= GMG_COARSE_MAX && cy <= GMG_COARSE_MAX) || l == GMG_MAX_LEVELS) break;
     cx = (cx + 1) / 2;
@@ -852,51 +900,21 @@ cudaError_t gmg_alloc(Gmg<T> &G, int nx, int ny, int B, const RedWs &ws) {
     }
   const GmgLevel<T> &C = G.lv[l - 1];
   G.ncoarse = (int)(B * C.nn);
-  cudaError_t e = cudaMalloc(&G.cinv, (size_t)G.ncoarse * G.ncoarse * sizeof(T));
-  if (e != cudaSuccess) return e;
-  if ((e = cudaMallocHost(&G.hS, 9 * B * B * C.nn * sizeof(T) + C.nn)) != cudaSuccess) return e;
-  G.hA = new double[(size_t)G.ncoarse * G.ncoarse];
-  G.hInv = new T[(size_t)G.ncoarse * G.ncoarse];
+  if (G.ncoarse > COARSE_INV_MAX) return cudaErrorInvalidValue;
+  const size_t n2 = (size_t)G.ncoarse * G.ncoarse;
+  if (!A.take(&G.cinv, n2) || !A.take(&G.cwork, n2)) return cudaErrorMemoryAllocation;
   return cudaSuccess;
 }
 
-size_t gmg_bytes(int nx, int ny, int B, size_t tsize) {
-  size_t total = 0;
-  int cx = nx, cy = ny, l = 0;
-  size_t last_nn = 0;
-  while (true) {
-    const size_t nn = (size_t)(cx + 1) * (cy + 1);
-    // stencil, six B-vectors (invd, x, b, r, dv, y), mask, bound, coefficients
-    total += 9 * B * B * nn * tsize + 6 * B * nn * tsize + nn + sizeof(double) + 4 * tsize;
-    last_nn = nn;
-    ++l;
-    if ((cx <= GMG_COARSE_MAX && cy <= GMG_COARSE_MAX) || l == GMG_MAX_LEVELS) break;
-    cx = (cx + 1) / 2;
-    cy = (cy + 1) / 2;
-  }
-  const size_t nc = B * last_nn;
-  return total + nc * nc * tsize;
-}
-
+// The hierarchy's arrays belong to the owner's arena; only the batched coarse-cycle
+// arguments are allocated separately.
 template <class T>
 void gmg_free(Gmg<T> &G) {
-  for (int l = 0; l < G.nl; ++l) {
-    GmgLevel<T> &L = G.lv[l];
-    void *p[] = {L.S, L.invd, L.x, L.b, L.r, L.dv, L.y, L.fm, L.lmax, L.coef};
-    for (void *q : p)
-      if (q) cudaFree(q);
-    L = GmgLevel<T>();
-  }
-  if (G.cinv) cudaFree(G.cinv);
+  for (int l = 0; l < G.nl; ++l) G.lv[l] = GmgLevel<T>();
   if (G.dca) cudaFree(G.dca);
   G.dca = nullptr;
-  if (G.hS) cudaFreeHost(G.hS);
-  delete[] G.hA;
-  delete[] G.hInv;
   G.cinv = nullptr;
-  G.hS = nullptr;
-  G.hA = nullptr;
-  G.hInv = nullptr;
+  G.cwork = nullptr;
   G.nl = 0;
 }
 
@@ -918,54 +936,10 @@ static cudaError_t gmg_setup_common(Gmg<T> &G, const GridD &g, cudaStream_t st) 
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // coarsest dense inverse on the host
-  GmgLevel<T> &C = G.lv[G.nl - 1];
-  const size_t sb = 9 * B * B * C.nn * sizeof(T);
-  if ((e = cudaMemcpyAsync(G.hS, C.S, sb, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
-  uint8_t *hfm = (uint8_t *)((char *)G.hS + sb);
-  if ((e = cudaMemcpyAsync(hfm, C.fm, C.nn, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
-  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-  const int n = G.ncoarse, nx = C.nx, ny = C.ny;
-  double *A = G.hA;
-  memset(A, 0, sizeof(double) * (size_t)n * n);
-  for (size_t node = 0; node < C.nn; ++node) {
-    const int i = (int)(node % (nx + 1)), j = (int)(node / (nx + 1));
-    for (int r = 0; r < B; ++r) {
-      const int row = (int)(B * node + r);
-      if (!((hfm[node] >> r) & 1)) {
-        A[(size_t)row * n + row] = 1.0;
-        continue;
-      }
-      for (int k = 0; k < 9; ++k) {
-        const int ii = i + k % 3 - 1, jj = j + k / 3 - 1;
-        if (ii < 0 || ii > nx || jj < 0 || jj > ny) continue;
-        const size_t m = (size_t)jj * (nx + 1) + ii;
-        for (int c = 0; c < B; ++c) {
-          if (!((hfm[m] >> c) & 1)) continue;
-          A[(size_t)row * n + (B * m + c)] = (double)G.hS[((size_t)(k * B * B + r * B + c)) * C.nn + node];
-        }
-      }
-    }
-  }
-  // symmetrise (the Galerkin product is symmetric up to rounding)
-  for (int i = 0; i < n; ++i)
-    for (int j = i + 1; j < n; ++j) {
-      const double v = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
-      A[(size_t)i * n + j] = A[(size_t)j * n + i] = v;
-    }
-  host_spd_inverse(A, n);
-  for (size_t q = 0; q < (size_t)n * n; ++q) G.hInv[q] = (T)A[q];
-  // zero rows/cols of non-free coarse DOFs so the coarse correction vanishes there
-  for (size_t node = 0; node < C.nn; ++node)
-    for (int r = 0; r < B; ++r)
-      if (!((hfm[node] >> r) & 1)) {
-        const int row = (int)(B * node + r);
-        for (int c = 0; c < n; ++c) G.hInv[(size_t)row * n + c] = G.hInv[(size_t)c * n + row] = T(0);
-      }
-  if ((e = cudaMemcpyAsync(G.cinv, G.hInv, sizeof(T) * (size_t)n * n, cudaMemcpyHostToDevice, st)) !=
-      cudaSuccess)
-    return e;
-  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  // coarsest dense inverse on the device
+  const GmgLevel<T> &C = G.lv[G.nl - 1];
+  k_coarse_inverse<T, B><<<1, 1024, 0, st>>>(C.nx, C.ny, C.S, C.fm, G.ncoarse, G.cwork, G.cinv);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   G.ready = true;
   return cudaSuccess;
 }
@@ -1087,6 +1061,17 @@ void gmg_coarse_cycle(const Gmg<T> &G, int lc, const T *b0, T *x0, cudaStream_t 
     k_coarse_cycle<T, 1><<<1, COARSE_THREADS, 0, st>>>(a);
 }
 
+template <class T>
+int gmg_set_coarse_nodes(Gmg<T> &G, int nodes) {
+  G.lc = G.nl - 1;
+  for (int k = 0; k < G.nl; ++k)
+    if (G.lv[k].nn <= (size_t)nodes) {
+      G.lc = k;
+      break;
+    }
+  return G.lc;
+}
+
 // ---- batched V-cycle (pf_batch.cuh) ----------------------------------------------------
 template <class T>
 static CoarseArgs<T> coarse_args(const Gmg<T> &G, int lc, const T *b0, T *x0) {
@@ -1179,7 +1164,7 @@ int gmg_mid_batch(int n, Gmg<T> *const *G, const int *const *done, cudaStream_t 
 }
 
 #define GMG_INST(T)                                                                            \
-  template cudaError_t gmg_alloc<T>(Gmg<T> &, int, int, int, const RedWs &);                   \
+  template cudaError_t gmg_alloc<T>(Gmg<T> &, int, int, int, const RedWs &, Arena &);          \
   template void gmg_free<T>(Gmg<T> &);                                                         \
   template cudaError_t gmg_setup_elas<T>(Gmg<T> &, const GridD &, const MatD &, const T *,     \
                                          const uint8_t *, cudaStream_t);                       \
@@ -1196,6 +1181,7 @@ int gmg_mid_batch(int n, Gmg<T> *const *G, const int *const *done, cudaStream_t 
   template void gmg_sub<T>(size_t, const T *, const T *, T *, cudaStream_t);                    \
   template void gmg_restrict<T>(const Gmg<T> &, int, const T *, T *, cudaStream_t);             \
   template cudaError_t gmg_batch_prepare<T>(Gmg<T> &);                                         \
+  template int gmg_set_coarse_nodes<T>(Gmg<T> &, int);                                         \
   template int gmg_restrict0_batch<T>(int, Gmg<T> *const *, const int *const *, cudaStream_t); \
   template int gmg_mid_batch<T>(int, Gmg<T> *const *, const int *const *, cudaStream_t);       \
   template void gmg_prolong_add<T>(const Gmg<T> &, int, const T *, T *, cudaStream_t);          \

@@ -8,8 +8,8 @@
 // operator is assembled as a stencil only to form A_1 and the smoother bound; the fine
 // level itself is applied matrix-free.  Smoother: Chebyshev on D^-1 A over
 // [lmax/10, lmax], lmax the Gershgorin bound of D^-1 A (device scalar).  Coarsest level:
-// dense inverse, factorised on the host in FP64 at setup.  The V-cycle is a fixed,
-// symmetric linear operator, so it preconditions CG.
+// dense inverse, computed on the device in FP64 at setup (k_coarse_inverse).  The
+// V-cycle is a fixed, symmetric linear operator, so it preconditions CG.
 #pragma once
 #include "pf_internal.cuh"
 
@@ -48,21 +48,17 @@ struct Gmg {
   GmgLevel<T> lv[GMG_MAX_LEVELS];
   int ncoarse = 0;          // DOFs of the coarsest level
   T *cinv = nullptr;        // ncoarse^2 dense inverse
-  double *hA = nullptr;     // host scratch for the coarse factorisation
-  T *hS = nullptr;          // host copy of the coarsest stencil
-  T *hInv = nullptr;
+  double *cwork = nullptr;  // ncoarse^2 FP64 work array of its factorisation (device)
   RedWs ws{};
   bool ready = false;
   void *dca = nullptr;      // device copy of the coarse-cycle arguments (batched launches)
 };
 
-// Allocate the hierarchy for a fine grid (device memory owned by the Gmg object).
+// Lay out the hierarchy for a fine grid in arena A (counting only when A has no base).
 template <class T>
-cudaError_t gmg_alloc(Gmg<T> &G, int nx, int ny, int B, const RedWs &ws);
+cudaError_t gmg_alloc(Gmg<T> &G, int nx, int ny, int B, const RedWs &ws, Arena &A);
 template <class T>
 void gmg_free(Gmg<T> &G);
-// Device bytes gmg_alloc takes for an nx x ny grid with B components of tsize bytes.
-size_t gmg_bytes(int nx, int ny, int B, size_t tsize);
 
 // Setup from the fine operator.  Elasticity: fine tangent with d (type T) and tension
 // bits; damage: per-Gauss-point coefficient c (type T), kappa.  dofm: fine mask.
@@ -88,6 +84,11 @@ template <class T>
 int gmg_restrict0_batch(int n, Gmg<T> *const *G, const int *const *done, cudaStream_t st);
 template <class T>
 int gmg_mid_batch(int n, Gmg<T> *const *G, const int *const *done, cudaStream_t st);
+
+// First level handled by the single-CTA coarse cycle: the first with at most `nodes`
+// nodes (GMG_CTA_NODES at allocation).  Returns the new lc.
+template <class T>
+int gmg_set_coarse_nodes(Gmg<T> &G, int nodes);
 
 // Launchers of the V-cycle building blocks (pf_gmg.cu).
 template <class T>

@@ -54,6 +54,27 @@ struct RedWs {
 };
 inline size_t red_counters(int) { return 2; }
 
+// Bump allocator over one device slab: a context takes all of its arrays from a single
+// allocation, so its device footprint is exactly the slab.  With no base it only counts
+// (the dry run that sizes the slab and answers pf_footprint_bytes).  Every array starts
+// on a 256-byte boundary.
+struct Arena {
+  char *base = nullptr;
+  size_t used = 0, cap = 0;
+  template <class T>
+  bool take(T **p, size_t n) {
+    const size_t b = ((n ? n : 1) * sizeof(T) + 255) & ~(size_t)255;
+    if (base) {
+      if (used + b > cap) return false;
+      *p = reinterpret_cast<T *>(base + used);
+    } else {
+      *p = nullptr;
+    }
+    used += b;
+    return true;
+  }
+};
+
 #ifdef __CUDACC__
 __device__ __forceinline__ double red_warp(double v, bool is_max) {
 #pragma unroll
@@ -156,7 +177,7 @@ inline unsigned tile_blocks_y(int ny) { return (unsigned)((ny + 1 + TY - 1) / TY
 template <class T>
 void elas_apply(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, const T *x,
                 T *y, cudaStream_t st, KrylovScal *sc = nullptr, const RedWs *ws = nullptr,
-                int epi = 0);
+                int epi = 0, int sr = 0);
 template <class T>
 void elas_diag(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, T *diag,
                cudaStream_t st);
@@ -212,7 +233,8 @@ enum { FS_DIR, FS_UPD, FS_UPD_INIT, FS_RESID, FS_PROLONG, FS_FINISH, FS_FINISH_F
 // (tile kernel).
 template <class T>
 void elas_mg_stage(int stage, const GridD &g, const MatD &m, const T *d, const uint8_t *tens,
-                   const MgBufs<T> &b, const RedWs &ws, cudaStream_t st);
+                   const MgBufs<T> &b, const RedWs &ws, cudaStream_t st, int sr = 0);
+// sr: node rows per warp of the strip kernel (2, 4, 8), 0 for the grid-size rule.
 template <class T>
 void damage_mg_stage(int stage, const GridD &g, const T *c, double kappa, const MgBufs<T> &b,
                      const RedWs &ws, cudaStream_t st);

@@ -863,7 +863,8 @@ static inline unsigned elem_blocks(size_t n) {
 // (short strips, more warps); FP64 ones are bound by the FP64 pipe, so they take long
 // strips to waste little arithmetic.
 template <class T>
-static int strip_rows(size_t nn) {
+static int strip_rows(size_t nn, int sr = 0) {
+  if (sr == 2 || sr == 4 || sr == 8) return sr;   // chosen by pf_autotune
   if (sizeof(T) == 8 && nn >= (size_t)100000) return 8;
   if (nn < (size_t)1500000) return 2;
   if (nn < (size_t)6000000) return 4;
@@ -877,7 +878,7 @@ static unsigned strip_blocks(const GridD &g, int sr) {
 
 template <class T, class Op, bool RESID = false>
 static void strip_launch(const GridD &g, const MatD &m, const T *d, const uint8_t *tens_c,
-                         const Op &op, const RedWs &w, cudaStream_t st) {
+                         const Op &op, const RedWs &w, cudaStream_t st, int sr_req = 0) {
   uint8_t *tens = const_cast<uint8_t *>(tens_c);  // written only by the RESID form
   const size_t nn = (size_t)(g.nx + 1) * (g.ny + 1);
   const unsigned strips = (unsigned)((g.nx + 1 + SW - 1) / SW);
@@ -886,7 +887,7 @@ static void strip_launch(const GridD &g, const MatD &m, const T *d, const uint8_
     return (warps + STRIP_WARPS - 1) / STRIP_WARPS;
   };
   const ElemConst<T> kc = elem_const<T>(g, m);
-  const int sr = strip_rows<T>(nn);
+  const int sr = strip_rows<T>(nn, sr_req);
   if (sr == 2)
     k_elas_strip<T, 2, Op, RESID><<<blocks(2), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
   else if (sr == 4)
@@ -897,10 +898,10 @@ static void strip_launch(const GridD &g, const MatD &m, const T *d, const uint8_
 
 template <class T>
 void elas_apply(const GridD &g, const MatD &m, const T *d, const uint8_t *tens, const T *x,
-                T *y, cudaStream_t st, KrylovScal *sc, const RedWs *ws, int epi) {
+                T *y, cudaStream_t st, KrylovScal *sc, const RedWs *ws, int epi, int sr) {
   const RedWs w = ws ? *ws : RedWs{nullptr, nullptr, 0};
   const int e = ws ? epi : EPI_NONE;
-  strip_launch<T>(g, m, d, tens, OpApply<T, 2>{x, y, sc, e}, w, st);
+  strip_launch<T>(g, m, d, tens, OpApply<T, 2>{x, y, sc, e}, w, st, sr);
 }
 
 // The input/output policy of fused stage `stage` (pf_fused.cuh) on the buffers M, handed
@@ -935,8 +936,8 @@ static void stage_op(int stage, const MgBufs<T> &M, F &&f) {
 
 template <class T>
 void elas_mg_stage(int stage, const GridD &g, const MatD &m, const T *d, const uint8_t *tens,
-                   const MgBufs<T> &B, const RedWs &ws, cudaStream_t st) {
-  stage_op<T, 2>(stage, B, [&](auto op) { strip_launch<T>(g, m, d, tens, op, ws, st); });
+                   const MgBufs<T> &B, const RedWs &ws, cudaStream_t st, int sr) {
+  stage_op<T, 2>(stage, B, [&](auto op) { strip_launch<T>(g, m, d, tens, op, ws, st, sr); });
 }
 
 // Batched form: stage `stage` for n simulations in one launch per strip height (the strip
@@ -954,7 +955,7 @@ int elas_mg_stage_batch(int stage, int n, const ElasStageIn<T> *in, cudaStream_t
     for (int i = 0; i < n; ++i) {
       const ElasStageIn<T> &q = in[i];
       const size_t nn = (size_t)(q.g.nx + 1) * (q.g.ny + 1);
-      const int sr = strip_rows<T>(nn);
+      const int sr = strip_rows<T>(nn, q.sr);
       const ElemConst<T> kc = elem_const<T>(q.g, q.m);
       const int *done = &q.B.sc->done;
       stage_op<T, 2>(stage, q.B, [&](auto op) {
@@ -1072,22 +1073,22 @@ void dof_mask(int nx, int ny, const uint8_t *flags, const uint8_t *active, uint8
 
 template void elas_apply<double>(const GridD &, const MatD &, const double *, const uint8_t *,
                                  const double *, double *, cudaStream_t, KrylovScal *,
-                                 const RedWs *, int);
+                                 const RedWs *, int, int);
 template void elas_apply<float>(const GridD &, const MatD &, const float *, const uint8_t *,
                                 const float *, float *, cudaStream_t, KrylovScal *,
-                                const RedWs *, int);
+                                const RedWs *, int, int);
 template void elas_diag<double>(const GridD &, const MatD &, const double *, const uint8_t *,
                                 double *, cudaStream_t);
 template void elas_diag<float>(const GridD &, const MatD &, const float *, const uint8_t *,
                                float *, cudaStream_t);
 template void elas_mg_stage<double>(int, const GridD &, const MatD &, const double *,
                                     const uint8_t *, const MgBufs<double> &, const RedWs &,
-                                    cudaStream_t);
+                                    cudaStream_t, int);
 template int elas_mg_stage_batch<float>(int, int, const ElasStageIn<float> *, cudaStream_t);
 template int damage_mg_stage_batch<float>(int, int, const DamageStageIn<float> *, cudaStream_t);
 template void elas_mg_stage<float>(int, const GridD &, const MatD &, const float *,
                                    const uint8_t *, const MgBufs<float> &, const RedWs &,
-                                   cudaStream_t);
+                                   cudaStream_t, int);
 template void damage_mg_stage<double>(int, const GridD &, const double *, double,
                                       const MgBufs<double> &, const RedWs &, cudaStream_t);
 template void damage_mg_stage<float>(int, const GridD &, const float *, double,

@@ -17,6 +17,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -113,6 +114,8 @@ struct pf_ctx {
   double *dscal = nullptr;   // device scalars for norms / residual / reaction
   double *hbuf = nullptr;    // pinned host mirror
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  char *slab = nullptr;         // the one device allocation all arrays are carved from
+  pf_tuning tune{};             // launch shapes chosen by pf_autotune (0: built-in rules)
   pf_batch *batch = nullptr;   // batch this context is attached to (pf_batch_attach)
   bool batching = false;       // inside a load step whose FP32 multigrid solves are batched
   cudaEvent_t evb = nullptr;   // marks the context's work before a batched solve
@@ -676,14 +679,16 @@ pf_status pcg_mg_elas(pf_ctx *ctx, Gmg<T> &G, const T *d, const T *b, T *x, T *r
       req.kind = 0;
       req.G = &G;
       req.e = ElasStageIn<float>{ctx->g, ctx->m, d, ctx->tens,
-                                 mg_bufs<float>(ctx, G, b, x, r, z, p, q), ctx->ws};
+                                 mg_bufs<float>(ctx, G, b, x, r, z, p, q), ctx->ws,
+                                 ctx->tune.strip_rows};
       req.rtol = rtol;
       req.maxit = maxit;
       return batch_solve(ctx, req, iters, ok);
     }
   }
   auto stage = [ctx, d](int s, const MgBufs<T> &B) {
-    elas_mg_stage<T>(s, ctx->g, ctx->m, d, ctx->tens, B, ctx->ws, ctx->st);
+    elas_mg_stage<T>(s, ctx->g, ctx->m, d, ctx->tens, B, ctx->ws, ctx->st,
+                     sizeof(T) == 4 ? ctx->tune.strip_rows : 0);
   };
   return pcg_mg_fused<T>(ctx, SL_FUSED, G, stage, b, x, r, z, p, q, rtol, maxit, iters, ok);
 }
@@ -913,10 +918,12 @@ pf_status newton_correction(pf_ctx *ctx, double tol, int *lin, int *refines, boo
     return mg_solve(ctx, ctx->mg_u, mg, setup, solve, lin, ok);
   }
   auto Af32 = [ctx, st](const float *xx, float *yy, int epi) {
-    elas_apply<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, xx, yy, st, ctx->sc, &ctx->ws, epi);
+    elas_apply<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, xx, yy, st, ctx->sc, &ctx->ws, epi,
+                      ctx->tune.strip_rows);
   };
   auto Ff32 = [ctx, st](const float *xx, float *yy) {
-    elas_apply<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, xx, yy, st);
+    elas_apply<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, xx, yy, st, nullptr, nullptr, 0,
+                      ctx->tune.strip_rows);
   };
   if (!mg) {
     elas_diag<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, ctx->fz, st);
@@ -1264,23 +1271,58 @@ pf_status stag_residual(pf_ctx *ctx, double *out) {
   return PF_OK;
 }
 
-template <class T>
-pf_status dalloc(pf_ctx *ctx, T **p, size_t n) {
-  cudaError_t e = cudaMalloc((void **)p, (n ? n : 1) * sizeof(T));
-  if (e != cudaSuccess)
-    return set_err(ctx, PF_ENOMEM, "cudaMalloc of %zu bytes: %s", n * sizeof(T),
-                   cudaGetErrorString(e));
-  return PF_OK;
+// Every device array of a context, in one fixed order, taken from arena A (a dry run when
+// A has no base: it sizes the context's single slab and answers pf_footprint_bytes, so
+// the two cannot disagree).  Only mesh fields and ctx's pointer slots are used.
+bool layout(pf_ctx *ctx, const pf_mesh *mesh, Arena &A) {
+  const size_t nn = (size_t)(mesh->nx + 1) * (mesh->ny + 1), ne = (size_t)mesh->nx * mesh->ny;
+  const size_t nq = 4 * ne;
+  const bool f32 = mesh->precision == PF_FP32_IR;
+#define AL(p, n)                     \
+  do {                               \
+    if (!A.take(&ctx->p, (n))) return false; \
+  } while (0)
+  AL(u, 2 * nn); AL(d, nn); AL(H, nq); AL(d_prev, nn); AL(F, 2 * nn);
+  AL(Hk, nq); AL(cq, nq); AL(Hhalf, nq); AL(act, nq);
+  AL(bd, nn); AL(Kd, nn); AL(dd, nn); AL(csolve, nq);
+  if (mesh->model == PF_AT1_PENALTY) AL(bhalf, nq);
+  if (mesh->split == PF_SPLIT_SPECTRAL) {
+    AL(sp_Sq, 3 * nq); AL(sp_Dq, 6 * nq); AL(sp_S64, 36 * nn);
+    if (f32) AL(sp_S32, 36 * nn);
+  }
+  AL(flags, nn); AL(dofm, nn); AL(tens, ne);
+  if (mesh->elem_active) AL(active, ne);
+  AL(kb, 2 * nn); AL(kx, 2 * nn); AL(kr, 2 * nn); AL(kz, 2 * nn); AL(kp, 2 * nn);
+  AL(kq, 2 * nn); AL(kinv, 2 * nn); AL(kres, 2 * nn);
+  if (f32) {
+    AL(fb, 2 * nn); AL(fx, 2 * nn); AL(fr, 2 * nn); AL(fz, 2 * nn); AL(fp, 2 * nn);
+    AL(fq, 2 * nn); AL(finv, 2 * nn); AL(fd, nn); AL(fc, nq);
+  }
+  AL(sc, 1); AL(dscal, 8);
+  {
+    const size_t tiles = (size_t)tile_blocks_x(mesh->nx) * tile_blocks_y(mesh->ny);
+    ctx->ws.max_blocks = (int)(tiles > 4096 ? tiles : 4096);
+  }
+  AL(ws.partials, 4 * (size_t)ctx->ws.max_blocks);
+  AL(ws.counter, red_counters(ctx->ws.max_blocks));
+#undef AL
+  if (mesh->precond == PF_PRECOND_GMG) {
+    cudaError_t e1, e2;
+    if (!f32) {
+      e1 = gmg_alloc<double>(ctx->gu, mesh->nx, mesh->ny, 2, ctx->ws, A);
+      e2 = gmg_alloc<double>(ctx->gd, mesh->nx, mesh->ny, 1, ctx->ws, A);
+    } else {
+      e1 = gmg_alloc<float>(ctx->gu32, mesh->nx, mesh->ny, 2, ctx->ws, A);
+      e2 = gmg_alloc<float>(ctx->gd32, mesh->nx, mesh->ny, 1, ctx->ws, A);
+    }
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return false;
+  }
+  return true;
 }
 
 void free_all(pf_ctx *c) {
-  void *ptrs[] = {c->u,  c->d,  c->H,  c->d_prev, c->F,  c->Hk, c->cq, c->Hhalf, c->act,
-                  c->bd, c->Kd, c->dd, c->flags,  c->active, c->dofm, c->tens, c->kb, c->kx,
-                  c->kr, c->kz, c->kp, c->kq, c->kinv, c->kres, c->fb, c->fx, c->fr, c->fz,
-                  c->fp, c->fq, c->finv, c->fd, c->fc, c->sc, c->ws.partials, c->ws.counter,
-                  c->dscal, c->csolve, c->bhalf, c->sp_Sq, c->sp_Dq, c->sp_S64, c->sp_S32};
-  for (void *p : ptrs)
-    if (p) cudaFree(p);
+  if (c->slab) cudaFree(c->slab);
+  c->slab = nullptr;
   gmg_free<double>(c->gu);
   gmg_free<double>(c->gd);
   gmg_free<float>(c->gu32);
@@ -1399,45 +1441,19 @@ pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double 
     return fail(PF_ECUDA);
   ctx->own_stream = true;
   const size_t nn = ctx->nn, ne = ctx->ne, nq = ctx->nq;
-#define AL(p, n)                                   \
-  do {                                             \
-    if ((s = dalloc(ctx, &ctx->p, (n))) != PF_OK) \
-      return fail(s);                              \
-  } while (0)
-  AL(u, 2 * nn); AL(d, nn); AL(H, nq); AL(d_prev, nn); AL(F, 2 * nn);
-  AL(Hk, nq); AL(cq, nq); AL(Hhalf, nq); AL(act, nq);
-  AL(bd, nn); AL(Kd, nn); AL(dd, nn); AL(csolve, nq);
-  if (ctx->model == PF_AT1_PENALTY) AL(bhalf, nq);
-  if (mesh->split == PF_SPLIT_SPECTRAL) {
-    AL(sp_Sq, 3 * nq); AL(sp_Dq, 6 * nq); AL(sp_S64, 36 * nn);
-    if (ctx->precision == PF_FP32_IR) AL(sp_S32, 36 * nn);
-  }
-  AL(flags, nn); AL(dofm, nn); AL(tens, ne);
-  if (mesh->elem_active) AL(active, ne);
-  AL(kb, 2 * nn); AL(kx, 2 * nn); AL(kr, 2 * nn); AL(kz, 2 * nn); AL(kp, 2 * nn);
-  AL(kq, 2 * nn); AL(kinv, 2 * nn); AL(kres, 2 * nn);
-  if (ctx->precision == PF_FP32_IR) {
-    AL(fb, 2 * nn); AL(fx, 2 * nn); AL(fr, 2 * nn); AL(fz, 2 * nn); AL(fp, 2 * nn);
-    AL(fq, 2 * nn); AL(finv, 2 * nn); AL(fd, nn); AL(fc, nq);
-  }
-  AL(sc, 1); AL(dscal, 8);
   {
-    const size_t tiles = (size_t)tile_blocks_x(mesh->nx) * tile_blocks_y(mesh->ny);
-    ctx->ws.max_blocks = (int)(tiles > 4096 ? tiles : 4096);
-  }
-  AL(ws.partials, 4 * ctx->ws.max_blocks);
-  AL(ws.counter, red_counters(ctx->ws.max_blocks));
-#undef AL
-  if (ctx->precond == PF_PRECOND_GMG) {
-    cudaError_t e1, e2;
-    if (ctx->precision == PF_FP64) {
-      e1 = gmg_alloc<double>(ctx->gu, mesh->nx, mesh->ny, 2, ctx->ws);
-      e2 = gmg_alloc<double>(ctx->gd, mesh->nx, mesh->ny, 1, ctx->ws);
-    } else {
-      e1 = gmg_alloc<float>(ctx->gu32, mesh->nx, mesh->ny, 2, ctx->ws);
-      e2 = gmg_alloc<float>(ctx->gd32, mesh->nx, mesh->ny, 1, ctx->ws);
+    Arena dry;
+    if (!layout(ctx, mesh, dry)) return fail(set_err(ctx, PF_EINVAL, "layout"));
+    cudaError_t e = cudaMalloc((void **)&ctx->slab, dry.used);
+    if (e != cudaSuccess) {
+      ctx->slab = nullptr;
+      cudaGetLastError();
+      return fail(PF_ENOMEM);
     }
-    if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(PF_ENOMEM);
+    Arena real;
+    real.base = ctx->slab;
+    real.cap = dry.used;
+    if (!layout(ctx, mesh, real)) return fail(PF_ENOMEM);
   }
   if (cudaMallocHost((void **)&ctx->hbuf, 256) != cudaSuccess) return fail(PF_ENOMEM);
   if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess)
@@ -1490,25 +1506,11 @@ pf_status pf_create(const pf_mesh *mesh, double E, double nu, double Gc, double 
 
 size_t pf_footprint_bytes(const pf_mesh *mesh) {
   if (!mesh || mesh->nx < 1 || mesh->ny < 1) return 0;
-  const size_t nn = (size_t)(mesh->nx + 1) * (mesh->ny + 1), ne = (size_t)mesh->nx * mesh->ny;
-  const size_t nq = 4 * ne, D = sizeof(double), F = sizeof(float);
-  size_t b = (2 * nn + nn + nq + nn + 2 * nn) * D     // u, d, H, d_prev, F
-             + 4 * nq * D + nq                          // Hk, cq, Hhalf, csolve, act
-             + 3 * nn * D                               // bd, Kd, dd
-             + 2 * nn + ne * (mesh->elem_active ? 2 : 1)  // flags, dofm, tens, active
-             + 8 * 2 * nn * D;                          // Krylov work (FP64)
-  if (mesh->precision == PF_FP32_IR) b += 7 * 2 * nn * F + nn * F + nq * F;
-  if (mesh->model == PF_AT1_PENALTY) b += nq * D;          // bhalf
-  if (mesh->split == PF_SPLIT_SPECTRAL)                     // point data, stencils
-    b += 9 * nq * D + 36 * nn * D + (mesh->precision == PF_FP32_IR ? 36 * nn * F : 0);
-  const size_t tiles = (size_t)tile_blocks_x(mesh->nx) * tile_blocks_y(mesh->ny);
-  const size_t mb = tiles > 4096 ? tiles : 4096;
-  b += 4 * mb * D + red_counters((int)mb) * sizeof(unsigned) + sizeof(KrylovScal) + 8 * D;
-  if (mesh->precond == PF_PRECOND_GMG) {
-    const size_t ts = mesh->precision == PF_FP64 ? D : F;
-    b += gmg_bytes(mesh->nx, mesh->ny, 2, ts) + gmg_bytes(mesh->nx, mesh->ny, 1, ts);
-  }
-  return b;
+  std::unique_ptr<pf_ctx> tmp(new (std::nothrow) pf_ctx());
+  if (!tmp) return 0;
+  Arena dry;
+  if (!layout(tmp.get(), mesh, dry)) return 0;
+  return dry.used;
 }
 
 pf_status pf_set_options(pf_ctx *ctx, const pf_options *o) {
@@ -1679,6 +1681,73 @@ void pf_destroy(pf_ctx *ctx) {
   if (ctx->st) cudaStreamSynchronize(ctx->st);
   free_all(ctx);
   delete ctx;
+}
+
+// ---- autotuning -----------------------------------------------------------------------------
+pf_status pf_get_tuning(const pf_ctx *ctx, pf_tuning *out) {
+  if (!ctx || !out) return PF_EINVAL;
+  *out = ctx->tune;
+  return PF_OK;
+}
+
+pf_status pf_autotune(pf_ctx *ctx, pf_tuning *out) {
+  if (!ctx) return PF_EINVAL;
+  if (ctx->precision != PF_FP32_IR || ctx->precond != PF_PRECOND_GMG ||
+      ctx->m.split != PF_SPLIT_VD)
+    return set_err(ctx, PF_EINVAL, "autotune: needs FP32_IR, GMG and the VD split");
+  if (ctx->step != 0 || ctx->batch)
+    return set_err(ctx, PF_EBUSY, "autotune: only before the first load step, unattached");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->st;
+  pf_tuning t{};
+  // operands: the initial phase field and tension bits, a smooth vector
+  convert<double, float>(ctx->nn, ctx->d, ctx->fd, st);
+  fill_ramp_f32(2 * ctx->nn, ctx->fx, st);
+  auto time_it = [&](auto launch) -> double {
+    for (int k = 0; k < 3; ++k) launch();
+    cudaEventRecord(ctx->ev0, st);
+    for (int k = 0; k < 10; ++k) launch();
+    cudaEventRecord(ctx->ev1, st);
+    cudaEventSynchronize(ctx->ev1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    return 100.0 * ms;   // microseconds per launch
+  };
+  const int srs[3] = {2, 4, 8};
+  double best = INFINITY;
+  for (int k = 0; k < 3; ++k) {
+    t.apply_us[k] = time_it([&]() {
+      elas_apply<float>(ctx->g, ctx->m, ctx->fd, ctx->tens, ctx->fx, ctx->fq, st, nullptr,
+                        nullptr, 0, srs[k]);
+    });
+    if (t.apply_us[k] < best) {
+      best = t.apply_us[k];
+      t.strip_rows = srs[k];
+    }
+  }
+  Gmg<float> &G = ctx->gu32;
+  cudaError_t e = gmg_setup_elas<float>(G, ctx->g, ctx->m, ctx->fd, ctx->tens, st);
+  if (e != cudaSuccess) return set_err(ctx, PF_ECUDA, "autotune setup: %s", cudaGetErrorString(e));
+  CK(cudaMemsetAsync(G.lv[1].b, 0, (size_t)G.B * G.lv[1].nn * sizeof(float), st));
+  const int limits[3] = {300, 1100, 4300};
+  best = INFINITY;
+  t.coarse_nodes = GMG_CTA_NODES;
+  for (int k = 0; k < 3; ++k) {
+    if (gmg_set_coarse_nodes<float>(G, limits[k]) < 1) continue;   // fused path needs lc >= 1
+    t.vcycle_us[k] = time_it([&]() { gmg_mid<float>(G, 1, st); });
+    if (t.vcycle_us[k] < best) {
+      best = t.vcycle_us[k];
+      t.coarse_nodes = limits[k];
+    }
+  }
+  gmg_set_coarse_nodes<float>(G, t.coarse_nodes);
+  gmg_set_coarse_nodes<float>(ctx->gd32, t.coarse_nodes);
+  ctx->mg_u.stale = true;   // the first solve rebuilds for its own operator
+  CKS(check_launch(ctx));
+  CK(cudaStreamSynchronize(st));
+  ctx->tune = t;
+  if (out) *out = t;
+  return PF_OK;
 }
 
 // ---- batches (pf_batch_*) ------------------------------------------------------------------

@@ -381,6 +381,14 @@ void fill(size_t n, double v, double *y, cudaStream_t st) {
 void krylov_while(cudaGraphConditionalHandle h, KrylovScal *sc, cudaStream_t st) {
   k_krylov_while<<<1, 1, 0, st>>>(h, sc);
 }
+__global__ void k_fill_ramp_f32(size_t n, float *__restrict__ x) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    x[i] = 1e-3f * (float)((unsigned)(i * 2654435761u) % 1000u);
+}
+void fill_ramp_f32(size_t n, float *x, cudaStream_t st) {
+  k_fill_ramp_f32<<<vblocks(n, 1 << 16), VEC_THREADS, 0, st>>>(n, x);
+}
 void krylov_while_batch(cudaGraphConditionalHandle h, int n, KrylovScal *const *sc,
                         cudaStream_t st) {
   ScalSet s;

@@ -32,6 +32,8 @@ void convert(size_t n, const A *a, B *b, cudaStream_t st);
 // b = (float)(s a) and x += s (double)e: the FP32 side of iterative refinement works on a
 // right-hand side scaled to unit size (s a power of two, so the scaling is exact).
 void scale_to_f32(size_t n, double s, const double *a, float *b, cudaStream_t st);
+// x[i]: a fixed pattern in [0, 1e-3) (operand of launch-shape timings)
+void fill_ramp_f32(size_t n, float *x, cudaStream_t st);
 void add_scaled_f32(size_t n, double s, const float *e, double *x, cudaStream_t st);
 template <class T>
 void coef(size_t n, double gcl, const double *H, T *c, cudaStream_t st);

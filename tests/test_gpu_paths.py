@@ -13,7 +13,8 @@ The checker paths are written by tests/golden/make_oracle_paths.py (FP64 checker
   step of the first jump is not a unique result: at TOL_ST 1e-5 the iteration may stop on
   the un-cracked plateau for one or two more steps (reading R25), and which step it
   leaves it on is decided by rounding.  Compared: every step converged; reactions before
-  the first jump of either code within 1e-6 (FP64) / 1e-4 (mixed) of the peak; the jump
+  the step preceding the first jump of either code within 1e-6 (FP64) / 1e-4 (mixed) of
+  the peak; the jump
   within two steps; the peak reaction within 1e-4; the phase field (RMS over the domain,
   mirror-aware) within 1e-3 at steps 40, 60, 80 and 100; the broken state at step 100.
 """
@@ -79,6 +80,7 @@ def test_config0_full_path_fp64(gpu):
 @pytest.mark.parametrize("scheme", [0, 1, 2, 3])
 def test_tensile128_same_l_over_h_path(gpu, scheme, precision):
     z = np.load(os.path.join(GOLD, "oracle_tensile128.npz"))
+    assert f"s{scheme}_reaction" in z, "checker path not written (make_oracle_paths.py)"
     spec = S.tensile(128, l=0.03, steps=100, u_max=6e-3)
     g = _grid(spec)
     Fr, dref, keep = z[f"s{scheme}_reaction"], z[f"s{scheme}_d"], list(z["keep"])
@@ -97,7 +99,9 @@ def test_tensile128_same_l_over_h_path(gpu, scheme, precision):
     jr, jg = _first_jump(Fr), _first_jump(Fg)
     assert jr < 90 and abs(jr - jg) <= 2
     tol = 1e-6 if precision == binding.FP64 else 1e-4
-    before = min(jr, jg)
+    # the step before the jump stops near the unstable equilibrium (reading R25): at
+    # TOL_ST 1e-5 its stopping point is not unique, so the comparison ends one step earlier
+    before = min(jr, jg) - 1
     assert np.max(np.abs(Fg[:before] - Fr[:before])) <= tol * peak
     assert abs(Fg.max() - peak) <= 1e-4 * peak
     for i, step in enumerate(keep):
