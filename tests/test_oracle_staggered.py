@@ -215,3 +215,25 @@ def test_stag_residual_on_a_stretched_element():
     d = np.array([0.1, 0.7, 0.3, 0.05])
     want = np.max(np.abs((K @ d - b) / np.diag(K)))
     assert stg.stag_residual(g, m, u, d, np.zeros((1, 4))) == pytest.approx(want, rel=1e-13)
+
+
+def test_unlimited_augmented_tangent_stalls_on_the_tensile_benchmark():
+    # Reading R16.  The literal augmented d-tangent of Sec. 3.4, G_c/l + 2H + K~ with no
+    # lower limit, is indefinite where the softening test holds past the homogeneous peak.
+    # On the 64 x 64 benchmark S3 with it converges through load step 10, but at step 11
+    # the staggered residual stalls near 0.14, while from the same state the limited
+    # coefficient (>= G_c/l) converges in fewer than 30 passes.
+    spec = S.tensile(64)
+    g = _grid(spec)
+    m = model.material_from_E_nu(spec.E, spec.nu, spec.Gc, spec.l, spec.eta, spec.plane)
+    st = stg.State(g)
+    for du in spec.increments[:10]:
+        r = stg.load_step(g, m, st, du, model.S3, stg.Options(tol_st=1e-7, kt_floor=False),
+                          spec.reaction_dir)
+        assert r.converged
+    lit = stg.load_step(g, m, st.copy(), spec.increments[10], model.S3,
+                        stg.Options(tol_st=1e-7, max_stag=30, kt_floor=False), spec.reaction_dir)
+    assert not lit.converged and lit.stag_residual > 0.05
+    lim = stg.load_step(g, m, st.copy(), spec.increments[10], model.S3,
+                        stg.Options(tol_st=1e-7, max_stag=30, kt_floor=True), spec.reaction_dir)
+    assert lim.converged
