@@ -584,7 +584,8 @@ def run_serve(args):
     grids = tuple(int(g) for g in args.grids.split(","))
     mix = S.served_batch(args.requests, seed=0, rate_per_s=args.rate, grids=grids)
     reqs = [server.Request(sp, scheme=sch, precision=binding.FP32_IR,
-                           precond=binding.PRECOND_GMG, tol=1e-5) for _, sp, sch in mix]
+                           precond=binding.PRECOND_GMG, tol=1e-5,
+                           options={"max_stag": args.max_stag}) for _, sp, sch in mix]
     free, _ = torch.cuda.mem_get_info()
     srv = server.Server(hbm_budget=int(0.8 * free), slots=args.slots, device=0)
     t0 = time.perf_counter()
