@@ -27,6 +27,7 @@ struct BatchLaunch {
 #ifdef __CUDACC__
 template <class F, int THREADS, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) k_batch(const __grid_constant__ BatchLaunch<F> b) {
+  pdl_enter();
   const unsigned blk = blockIdx.x;
   int s = 0;
   while (s + 1 < b.n && blk >= b.start[s + 1]) ++s;
@@ -48,7 +49,7 @@ struct Batcher {
   }
   int launch(cudaStream_t st) {
     if (L.n == 0) return 0;
-    k_batch<F, THREADS, MINB><<<L.start[L.n], THREADS, 0, st>>>(L);
+    launch_pdl(k_batch<F, THREADS, MINB>, dim3(L.start[L.n]), dim3(THREADS), st, L);
     return 1;
   }
 };

@@ -318,22 +318,25 @@ struct StenApplyF {
   T *__restrict__ y;
   int mode;
   __device__ void operator()(unsigned bid, unsigned nblk) const {
-  const size_t nn = (size_t)(nx + 1) * (ny + 1);
-  for (size_t n = bid * (size_t)blockDim.x + threadIdx.x; n < nn;
-       n += (size_t)nblk * blockDim.x) {
-    T acc[B];
-    sten_row<T, B>(nx, ny, nn, S, x, n, acc);
-    const uint8_t f = fm[n];
+    const size_t nn = (size_t)(nx + 1) * (ny + 1);
+    for (size_t n = bid * (size_t)blockDim.x + threadIdx.x; n < nn;
+         n += (size_t)nblk * blockDim.x) {
+      T acc[B];
+      sten_row<T, B>(nx, ny, nn, S, x, n, acc);
+      const uint8_t f = fm[n];
 #pragma unroll
-    for (int r = 0; r < B; ++r) {
-      T v = mode ? b[B * n + r] - acc[r] : acc[r];
-      y[B * n + r] = ((f >> r) & 1) ? v : T(0);
+      for (int r = 0; r < B; ++r) {
+        T v = mode ? b[B * n + r] - acc[r] : acc[r];
+        y[B * n + r] = ((f >> r) & 1) ? v : T(0);
+      }
     }
   }
-}
 };
 template <class T, int B>
-__global__ void k_sten_apply(StenApplyF<T, B> f) { f(blockIdx.x, gridDim.x); }
+__global__ void k_sten_apply(StenApplyF<T, B> f) {
+  pdl_enter();
+  f(blockIdx.x, gridDim.x);
+}
 
 
 // ---- fused smoothing kernels of the grid-wide stencil levels ------------------------------
@@ -350,27 +353,30 @@ struct StenPreF {
   T *__restrict__ x;
   __device__ void operator()(unsigned bid, unsigned nblk) const {
     const T *__restrict__ invd = this->invd, *__restrict__ b = this->b;
-  const size_t nn = (size_t)(nx + 1) * (ny + 1);
-  const T it = coef[0], c2 = coef[1], c1 = coef[2];
-  for (size_t n = bid * (size_t)blockDim.x + threadIdx.x; n < nn;
-       n += (size_t)nblk * blockDim.x) {
-    T acc[B];
-    sten_row_by<T, B>(nx, ny, nn, S, n,
-                      [=](size_t q) { return __ldg(invd + q) * __ldg(b + q) * it; }, acc);
-    const uint8_t f = __ldg(fm + n);
+    const size_t nn = (size_t)(nx + 1) * (ny + 1);
+    const T it = coef[0], c2 = coef[1], c1 = coef[2];
+    for (size_t n = bid * (size_t)blockDim.x + threadIdx.x; n < nn;
+         n += (size_t)nblk * blockDim.x) {
+      T acc[B];
+      sten_row_by<T, B>(nx, ny, nn, S, n,
+                        [=](size_t q) { return __ldg(invd + q) * __ldg(b + q) * it; }, acc);
+      const uint8_t f = __ldg(fm + n);
 #pragma unroll
-    for (int c = 0; c < B; ++c) {
-      const size_t i = B * n + c;
-      const T iv = __ldg(invd + i), bi = __ldg(b + i);
-      const T d0 = iv * bi * it;
-      const T d1 = c1 * d0 + c2 * iv * (bi - acc[c]);
-      x[i] = ((f >> c) & 1) ? d0 + d1 : T(0);
+      for (int c = 0; c < B; ++c) {
+        const size_t i = B * n + c;
+        const T iv = __ldg(invd + i), bi = __ldg(b + i);
+        const T d0 = iv * bi * it;
+        const T d1 = c1 * d0 + c2 * iv * (bi - acc[c]);
+        x[i] = ((f >> c) & 1) ? d0 + d1 : T(0);
+      }
     }
   }
-}
 };
 template <class T, int B>
-__global__ void k_sten_pre(StenPreF<T, B> f) { f(blockIdx.x, gridDim.x); }
+__global__ void k_sten_pre(StenPreF<T, B> f) {
+  pdl_enter();
+  f(blockIdx.x, gridDim.x);
+}
 
 // Bilinear prolongation of the coarse correction at fine node (ix, iy), component c.
 template <class T, int B>
@@ -406,36 +412,39 @@ struct StenProlongFirstF {
     const T *__restrict__ xin = this->xin, *__restrict__ xc = this->xc;
     const uint8_t *__restrict__ fm = this->fm;
     const int nxc = this->nxc, nyc = this->nyc;
-  const size_t nn = (size_t)(nx + 1) * (ny + 1);
-  const int ld = nx + 1;
-  const T it = coef[0];
-  auto t_at = [=](size_t q) {
-    const size_t m = q / B;
-    const int c = (int)(q - m * B);
-    T v = __ldg(xin + q);
-    if ((__ldg(fm + m) >> c) & 1)
-      v += prolong_at<T, B>((int)(m % ld), (int)(m / ld), nxc, nyc, xc, c);
-    return v;
-  };
-  for (size_t n = bid * (size_t)blockDim.x + threadIdx.x; n < nn;
-       n += (size_t)nblk * blockDim.x) {
-    T acc[B];
-    sten_row_by<T, B>(nx, ny, nn, S, n, t_at, acc);
-    const uint8_t f = __ldg(fm + n);
+    const size_t nn = (size_t)(nx + 1) * (ny + 1);
+    const int ld = nx + 1;
+    const T it = coef[0];
+    auto t_at = [=](size_t q) {
+      const size_t m = q / B;
+      const int c = (int)(q - m * B);
+      T v = __ldg(xin + q);
+      if ((__ldg(fm + m) >> c) & 1)
+        v += prolong_at<T, B>((int)(m % ld), (int)(m / ld), nxc, nyc, xc, c);
+      return v;
+    };
+    for (size_t n = bid * (size_t)blockDim.x + threadIdx.x; n < nn;
+         n += (size_t)nblk * blockDim.x) {
+      T acc[B];
+      sten_row_by<T, B>(nx, ny, nn, S, n, t_at, acc);
+      const uint8_t f = __ldg(fm + n);
 #pragma unroll
-    for (int c = 0; c < B; ++c) {
-      const size_t i = B * n + c;
-      const T ri = ((f >> c) & 1) ? __ldg(b + i) - acc[c] : T(0);
-      const T di = __ldg(invd + i) * ri * it;
-      r[i] = ri;
-      d[i] = di;
-      xout[i] = t_at(i) + di;
+      for (int c = 0; c < B; ++c) {
+        const size_t i = B * n + c;
+        const T ri = ((f >> c) & 1) ? __ldg(b + i) - acc[c] : T(0);
+        const T di = __ldg(invd + i) * ri * it;
+        r[i] = ri;
+        d[i] = di;
+        xout[i] = t_at(i) + di;
+      }
     }
   }
-}
 };
 template <class T, int B>
-__global__ void k_sten_prolong_first(StenProlongFirstF<T, B> f) { f(blockIdx.x, gridDim.x); }
+__global__ void k_sten_prolong_first(StenProlongFirstF<T, B> f) {
+  pdl_enter();
+  f(blockIdx.x, gridDim.x);
+}
 
 // Second post-smoothing step: x += c1 d + c2 D^-1 (r - A d).
 template <class T, int B>
@@ -449,24 +458,27 @@ struct StenPostF {
   const T *__restrict__ r;
   T *__restrict__ x;
   __device__ void operator()(unsigned bid, unsigned nblk) const {
-  const size_t nn = (size_t)(nx + 1) * (ny + 1);
-  const T c2 = coef[1], c1 = coef[2];
-  for (size_t n = bid * (size_t)blockDim.x + threadIdx.x; n < nn;
-       n += (size_t)nblk * blockDim.x) {
-    T acc[B];
-    sten_row<T, B>(nx, ny, nn, S, d, n, acc);
-    const uint8_t f = __ldg(fm + n);
+    const size_t nn = (size_t)(nx + 1) * (ny + 1);
+    const T c2 = coef[1], c1 = coef[2];
+    for (size_t n = bid * (size_t)blockDim.x + threadIdx.x; n < nn;
+         n += (size_t)nblk * blockDim.x) {
+      T acc[B];
+      sten_row<T, B>(nx, ny, nn, S, d, n, acc);
+      const uint8_t f = __ldg(fm + n);
 #pragma unroll
-    for (int c = 0; c < B; ++c) {
-      const size_t i = B * n + c;
-      const T ri = __ldg(r + i) - (((f >> c) & 1) ? acc[c] : T(0));
-      x[i] = x[i] + (c1 * __ldg(d + i) + c2 * __ldg(invd + i) * ri);
+      for (int c = 0; c < B; ++c) {
+        const size_t i = B * n + c;
+        const T ri = __ldg(r + i) - (((f >> c) & 1) ? acc[c] : T(0));
+        x[i] = x[i] + (c1 * __ldg(d + i) + c2 * __ldg(invd + i) * ri);
+      }
     }
   }
-}
 };
 template <class T, int B>
-__global__ void k_sten_post(StenPostF<T, B> f) { f(blockIdx.x, gridDim.x); }
+__global__ void k_sten_post(StenPostF<T, B> f) {
+  pdl_enter();
+  f(blockIdx.x, gridDim.x);
+}
 
 // ---- coarse levels in one CTA --------------------------------------------------------------
 template <class T>
@@ -640,6 +652,7 @@ __device__ __forceinline__ void coarse_cycle_body(const CoarseArgs<T> &a) {
 
 template <class T, int B>
 __global__ void __launch_bounds__(COARSE_THREADS) k_coarse_cycle(CoarseArgs<T> a) {
+  pdl_enter();
   coarse_cycle_body<T, B>(a);
 }
 
@@ -714,41 +727,44 @@ struct RestrictF {
   const uint8_t *__restrict__ fmc;
   T *__restrict__ bc;
   __device__ void operator()(unsigned bid, unsigned nblk) const {
-  const size_t nnc = (size_t)(nxc + 1) * (nyc + 1);
-  for (size_t I = bid * (size_t)blockDim.x + threadIdx.x; I < nnc;
-       I += (size_t)nblk * blockDim.x) {
-    const int Ix = (int)(I % (nxc + 1)), Iy = (int)(I / (nxc + 1));
-    T acc[B];
+    const size_t nnc = (size_t)(nxc + 1) * (nyc + 1);
+    for (size_t I = bid * (size_t)blockDim.x + threadIdx.x; I < nnc;
+         I += (size_t)nblk * blockDim.x) {
+      const int Ix = (int)(I % (nxc + 1)), Iy = (int)(I / (nxc + 1));
+      T acc[B];
 #pragma unroll
-    for (int c = 0; c < B; ++c) acc[c] = T(0);
+      for (int c = 0; c < B; ++c) acc[c] = T(0);
 #pragma unroll
-    for (int b = -1; b <= 1; ++b) {
-      const int iy = 2 * Iy + b;
-      const bool vy = iy >= 0 && iy <= nyf;
-      const int iyc = iy < 0 ? 0 : (iy > nyf ? nyf : iy);
+      for (int b = -1; b <= 1; ++b) {
+        const int iy = 2 * Iy + b;
+        const bool vy = iy >= 0 && iy <= nyf;
+        const int iyc = iy < 0 ? 0 : (iy > nyf ? nyf : iy);
 #pragma unroll
-      for (int a = -1; a <= 1; ++a) {
-        const int ix = 2 * Ix + a;
-        const bool v = vy && ix >= 0 && ix <= nxf;
-        const int ixc = ix < 0 ? 0 : (ix > nxf ? nxf : ix);
-        const T wi = v ? (a == 0 ? T(1) : T(0.5)) * (b == 0 ? T(1) : T(0.5)) : T(0);
-        const size_t fi = (size_t)iyc * (nxf + 1) + ixc;
-        const uint8_t m = __ldg(fmf + fi);
+        for (int a = -1; a <= 1; ++a) {
+          const int ix = 2 * Ix + a;
+          const bool v = vy && ix >= 0 && ix <= nxf;
+          const int ixc = ix < 0 ? 0 : (ix > nxf ? nxf : ix);
+          const T wi = v ? (a == 0 ? T(1) : T(0.5)) * (b == 0 ? T(1) : T(0.5)) : T(0);
+          const size_t fi = (size_t)iyc * (nxf + 1) + ixc;
+          const uint8_t m = __ldg(fmf + fi);
 #pragma unroll
-        for (int c = 0; c < B; ++c) {
-          const T rv = __ldg(rf + B * fi + c);
-          acc[c] += ((m >> c) & 1) ? wi * rv : T(0);
+          for (int c = 0; c < B; ++c) {
+            const T rv = __ldg(rf + B * fi + c);
+            acc[c] += ((m >> c) & 1) ? wi * rv : T(0);
+          }
         }
       }
-    }
-    const uint8_t mc = fmc[I];
+      const uint8_t mc = fmc[I];
 #pragma unroll
-    for (int c = 0; c < B; ++c) bc[B * I + c] = ((mc >> c) & 1) ? acc[c] : T(0);
+      for (int c = 0; c < B; ++c) bc[B * I + c] = ((mc >> c) & 1) ? acc[c] : T(0);
+    }
   }
-}
 };
 template <class T, int B>
-__global__ void k_restrict(RestrictF<T, B> f) { f(blockIdx.x, gridDim.x); }
+__global__ void k_restrict(RestrictF<T, B> f) {
+  pdl_enter();
+  f(blockIdx.x, gridDim.x);
+}
 
 // x_f += P x_c over free fine DOFs (always four parents, out-of-grid ones weighted 0).
 template <class T, int B>
@@ -970,9 +986,11 @@ void gmg_sten_apply(const Gmg<T> &G, int l, const T *x, const T *b, T *y, int mo
                     cudaStream_t st) {
   const GmgLevel<T> &L = G.lv[l];
   if (G.B == 2)
-    k_sten_apply<T, 2><<<nblk(L.nn), 256, 0, st>>>(StenApplyF<T, 2>{L.nx, L.ny, L.S, L.fm, x, b, y, mode});
+    launch_pdl(k_sten_apply<T, 2>, dim3(nblk(L.nn)), dim3(256), st,
+               StenApplyF<T, 2>{L.nx, L.ny, L.S, L.fm, x, b, y, mode});
   else
-    k_sten_apply<T, 1><<<nblk(L.nn), 256, 0, st>>>(StenApplyF<T, 1>{L.nx, L.ny, L.S, L.fm, x, b, y, mode});
+    launch_pdl(k_sten_apply<T, 1>, dim3(nblk(L.nn)), dim3(256), st,
+               StenApplyF<T, 1>{L.nx, L.ny, L.S, L.fm, x, b, y, mode});
 }
 template <class T>
 void gmg_cheb_first(const Gmg<T> &G, int l, const T *b, T *x, T *d, T *r, cudaStream_t st) {
@@ -1001,9 +1019,11 @@ template <class T>
 void gmg_restrict(const Gmg<T> &G, int l, const T *rf, T *bc, cudaStream_t st) {
   const GmgLevel<T> &F = G.lv[l], &C = G.lv[l + 1];
   if (G.B == 2)
-    k_restrict<T, 2><<<nblk(C.nn), 256, 0, st>>>(RestrictF<T, 2>{F.nx, F.ny, rf, F.fm, C.nx, C.ny, C.fm, bc});
+    launch_pdl(k_restrict<T, 2>, dim3(nblk(C.nn)), dim3(256), st,
+               RestrictF<T, 2>{F.nx, F.ny, rf, F.fm, C.nx, C.ny, C.fm, bc});
   else
-    k_restrict<T, 1><<<nblk(C.nn), 256, 0, st>>>(RestrictF<T, 1>{F.nx, F.ny, rf, F.fm, C.nx, C.ny, C.fm, bc});
+    launch_pdl(k_restrict<T, 1>, dim3(nblk(C.nn)), dim3(256), st,
+               RestrictF<T, 1>{F.nx, F.ny, rf, F.fm, C.nx, C.ny, C.fm, bc});
 }
 template <class T>
 void gmg_prolong_add(const Gmg<T> &G, int l, const T *xc, T *xf, cudaStream_t st) {
@@ -1017,19 +1037,23 @@ template <class T>
 void gmg_pre(const Gmg<T> &G, int l, const T *b, T *x, cudaStream_t st) {
   const GmgLevel<T> &L = G.lv[l];
   if (G.B == 2)
-    k_sten_pre<T, 2><<<nblk(L.nn), 256, 0, st>>>(StenPreF<T, 2>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm, b, x});
+    launch_pdl(k_sten_pre<T, 2>, dim3(nblk(L.nn)), dim3(256), st,
+               StenPreF<T, 2>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm, b, x});
   else
-    k_sten_pre<T, 1><<<nblk(L.nn), 256, 0, st>>>(StenPreF<T, 1>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm, b, x});
+    launch_pdl(k_sten_pre<T, 1>, dim3(nblk(L.nn)), dim3(256), st,
+               StenPreF<T, 1>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm, b, x});
 }
 template <class T>
 void gmg_prolong_first(const Gmg<T> &G, int l, const T *xin, T *xout, cudaStream_t st) {
   const GmgLevel<T> &L = G.lv[l], &C = G.lv[l + 1];
   if (G.B == 2)
-    k_sten_prolong_first<T, 2><<<nblk(L.nn), 256, 0, st>>>(StenProlongFirstF<T, 2>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm,
+    launch_pdl(k_sten_prolong_first<T, 2>, dim3(nblk(L.nn)), dim3(256), st,
+               StenProlongFirstF<T, 2>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm,
                                                            C.nx, C.ny, C.x, L.b, xin, xout, L.r,
                                                            L.dv});
   else
-    k_sten_prolong_first<T, 1><<<nblk(L.nn), 256, 0, st>>>(StenProlongFirstF<T, 1>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm,
+    launch_pdl(k_sten_prolong_first<T, 1>, dim3(nblk(L.nn)), dim3(256), st,
+               StenProlongFirstF<T, 1>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm,
                                                            C.nx, C.ny, C.x, L.b, xin, xout, L.r,
                                                            L.dv});
 }
@@ -1037,10 +1061,12 @@ template <class T>
 void gmg_post(const Gmg<T> &G, int l, T *x, cudaStream_t st) {
   const GmgLevel<T> &L = G.lv[l];
   if (G.B == 2)
-    k_sten_post<T, 2><<<nblk(L.nn), 256, 0, st>>>(StenPostF<T, 2>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm, L.dv,
+    launch_pdl(k_sten_post<T, 2>, dim3(nblk(L.nn)), dim3(256), st,
+               StenPostF<T, 2>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm, L.dv,
                                                   L.r, x});
   else
-    k_sten_post<T, 1><<<nblk(L.nn), 256, 0, st>>>(StenPostF<T, 1>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm, L.dv,
+    launch_pdl(k_sten_post<T, 1>, dim3(nblk(L.nn)), dim3(256), st,
+               StenPostF<T, 1>{L.nx, L.ny, L.S, L.invd, L.coef, L.fm, L.dv,
                                                   L.r, x});
 }
 template <class T>
@@ -1056,9 +1082,9 @@ void gmg_coarse_cycle(const Gmg<T> &G, int lc, const T *b0, T *x0, cudaStream_t 
   a.cinv = G.cinv;
   a.ncoarse = G.ncoarse;
   if (G.B == 2)
-    k_coarse_cycle<T, 2><<<1, COARSE_THREADS, 0, st>>>(a);
+    launch_pdl(k_coarse_cycle<T, 2>, dim3(1), dim3(COARSE_THREADS), st, a);
   else
-    k_coarse_cycle<T, 1><<<1, COARSE_THREADS, 0, st>>>(a);
+    launch_pdl(k_coarse_cycle<T, 1>, dim3(1), dim3(COARSE_THREADS), st, a);
 }
 
 template <class T>

@@ -75,7 +75,40 @@ struct Arena {
   }
 };
 
+// Programmatic dependent launch.  The kernels of the Krylov iteration are launched with
+// programmatic stream serialization (launch_pdl) and open with pdl_enter(): the kernel's
+// CTAs are dispatched while its predecessor finishes, wait there until the predecessor
+// has completed and its writes are visible, then allow the next kernel to be dispatched
+// in turn.  The gap between the short dependent launches of one iteration shrinks to the
+// wait.  Without a programmatic launch both instructions return at once.  PF_PDL=0 in the
+// environment launches everything plainly.
+bool pdl_enabled();
 #ifdef __CUDACC__
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+template <class... KArgs, class... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  if (cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...) != cudaSuccess &&
+      cfg.numAttrs) {
+    cudaGetLastError();   // refused as a programmatic launch: launch it plainly
+    cfg.numAttrs = 0;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+  }
+}
+
 __device__ __forceinline__ double red_warp(double v, bool is_max) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

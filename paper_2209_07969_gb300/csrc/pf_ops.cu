@@ -413,6 +413,7 @@ template <class T, int SR, class Op, bool RESID = false>
 __global__ void __launch_bounds__(32 * STRIP_WARPS)
 k_elas_strip(GridD g, ElemConst<T> kc, const T *__restrict__ d, uint8_t *__restrict__ tens,
              Op op, RedWs ws) {
+  pdl_enter();
   elas_strip_body<T, SR, Op, RESID>(blockIdx.x, gridDim.x, g, kc, d, tens, op, ws);
 }
 
@@ -589,6 +590,7 @@ __device__ __forceinline__ void damage_op_body(unsigned bid, unsigned nblk, cons
 template <class T, class Op>
 __global__ void __launch_bounds__(TILE_THREADS, sizeof(T) == 4 ? 8 : 4)
 k_damage_op(GridD g, ElemConst<T> kc, const T *__restrict__ c, Op op, RedWs ws) {
+  pdl_enter();
   damage_op_body<T, Op>(blockIdx.x, gridDim.x, g, kc, c, op, ws);
 }
 
@@ -889,11 +891,14 @@ static void strip_launch(const GridD &g, const MatD &m, const T *d, const uint8_
   const ElemConst<T> kc = elem_const<T>(g, m);
   const int sr = strip_rows<T>(nn, sr_req);
   if (sr == 2)
-    k_elas_strip<T, 2, Op, RESID><<<blocks(2), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
+    launch_pdl(k_elas_strip<T, 2, Op, RESID>, dim3(blocks(2)), dim3(32 * STRIP_WARPS), st, g, kc, d,
+               tens, op, w);
   else if (sr == 4)
-    k_elas_strip<T, 4, Op, RESID><<<blocks(4), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
+    launch_pdl(k_elas_strip<T, 4, Op, RESID>, dim3(blocks(4)), dim3(32 * STRIP_WARPS), st, g, kc, d,
+               tens, op, w);
   else
-    k_elas_strip<T, 8, Op, RESID><<<blocks(8), 32 * STRIP_WARPS, 0, st>>>(g, kc, d, tens, op, w);
+    launch_pdl(k_elas_strip<T, 8, Op, RESID>, dim3(blocks(8)), dim3(32 * STRIP_WARPS), st, g, kc, d,
+               tens, op, w);
 }
 
 template <class T>
@@ -998,8 +1003,8 @@ void damage_apply(const GridD &g, const T *c, double kappa, const T *x, T *y, cu
                   KrylovScal *sc, const RedWs *ws, int epi) {
   const RedWs w = ws ? *ws : RedWs{nullptr, nullptr, 0};
   const int e = ws ? epi : EPI_NONE;
-  k_damage_op<T, OpApply<T, 1>><<<tile_grid(g), TILE_THREADS, 0, st>>>(
-      g, elem_const<T>(g, MatD{}, kappa), c, OpApply<T, 1>{x, y, sc, e}, w);
+  launch_pdl(k_damage_op<T, OpApply<T, 1>>, tile_grid(g), dim3(TILE_THREADS), st, g,
+             elem_const<T>(g, MatD{}, kappa), c, OpApply<T, 1>{x, y, sc, e}, w);
 }
 
 template <class T>
@@ -1008,7 +1013,7 @@ void damage_mg_stage(int stage, const GridD &g, const T *c, double kappa, const 
   const ElemConst<T> kc = elem_const<T>(g, MatD{}, kappa);
   const dim3 gt = tile_grid(g);
   stage_op<T, 1>(stage, B, [&](auto op) {
-    k_damage_op<T, decltype(op)><<<gt, TILE_THREADS, 0, st>>>(g, kc, c, op, ws);
+    launch_pdl(k_damage_op<T, decltype(op)>, gt, dim3(TILE_THREADS), st, g, kc, c, op, ws);
   });
 }
 

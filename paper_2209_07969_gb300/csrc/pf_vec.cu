@@ -2,6 +2,7 @@
 // Dot products accumulate in FP64 whatever the vector type; the last CTA of each
 // reduction updates the solver scalars on the device (no host round trip per step).
 #include <math.h>
+#include <stdlib.h>
 
 #include "pf_internal.cuh"
 #include "pf_vec.cuh"
@@ -158,7 +159,16 @@ __global__ void k_pcg_rz(size_t n, const T *__restrict__ r, const T *__restrict_
 // End of one pass of a device-side Krylov loop (a conditional WHILE node of a CUDA graph):
 // count the iteration and keep looping while ||r||^2 > rtol2 ||r0||^2, without breakdown,
 // for fewer than maxit iterations.  A NaN residual ends the loop (the comparison fails).
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char *e = getenv("PF_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 __global__ void k_krylov_while(cudaGraphConditionalHandle h, KrylovScal *sc) {
+  pdl_enter();
   const int it = sc->it + 1;
   sc->it = it;
   const bool more = sc->rr > sc->rtol2 * sc->rr0 && !sc->breakdown && it < sc->maxit;
@@ -173,6 +183,7 @@ struct ScalSet {
   KrylovScal *sc[PF_MAXB];
 };
 __global__ void k_krylov_while_batch(cudaGraphConditionalHandle h, ScalSet s) {
+  pdl_enter();
   bool any = false;
   for (int i = 0; i < s.n; ++i) {
     KrylovScal *k = s.sc[i];
@@ -379,7 +390,7 @@ void fill(size_t n, double v, double *y, cudaStream_t st) {
   k_fill<<<vblocks(n, 1 << 16), VEC_THREADS, 0, st>>>(n, v, y);
 }
 void krylov_while(cudaGraphConditionalHandle h, KrylovScal *sc, cudaStream_t st) {
-  k_krylov_while<<<1, 1, 0, st>>>(h, sc);
+  launch_pdl(k_krylov_while, dim3(1), dim3(1), st, h, sc);
 }
 __global__ void k_fill_ramp_f32(size_t n, float *__restrict__ x) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
@@ -394,7 +405,7 @@ void krylov_while_batch(cudaGraphConditionalHandle h, int n, KrylovScal *const *
   ScalSet s;
   s.n = n < PF_MAXB ? n : PF_MAXB;
   for (int i = 0; i < s.n; ++i) s.sc[i] = sc[i];
-  k_krylov_while_batch<<<1, 1, 0, st>>>(h, s);
+  launch_pdl(k_krylov_while_batch, dim3(1), dim3(1), st, h, s);
 }
 void masked_comb(size_t n, int ncomp, const uint8_t *dofm, double s, const double *a, double t,
                  const double *b, double *out, cudaStream_t st) {
