@@ -86,6 +86,13 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def workload_name(args, l):
+    """The workload as both arms name it in `config`."""
+    return (f"tensile notched square {args.grid}x{args.grid} Q1, l={l:g} mm, 100 load steps to "
+            f"6e-3 mm, TOL_ST 1e-5 (up to {args.max_stag} passes per step), scheme "
+            f"{args.scheme}; whole load paths")
+
+
 def workload(grid):
     from paper_2209_07969_gb300 import specimens as S
     return S.tensile(grid, l=0.0075 if grid == 512 else 0.0075 * 512 / grid,
@@ -197,9 +204,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"tensile notched square {args.grid}x{args.grid}, l=0.0075 mm, "
-                                   "100 load steps to 6e-3 mm, whole load paths (checker sample: "
-                                   "one phase-field solve of load step 1 per step)"},
+            "config": {"workload": workload_name(args, workload(args.grid).l),
+                       "form": "FP64 CPU checker (sparse LU), sampled"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "each step one exact phase-field solve (assembly + "
                                        "SuperLU) of load step 1, the least work of one "
@@ -478,12 +484,9 @@ def run_ours(args):
                "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * T / K,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f32+f64", "data": "synthetic",
-               "config": {"workload": f"tensile notched square {args.grid}x{args.grid} Q1, "
-                                      f"l={spec.l:g} mm, 100 load steps to 6e-3 mm, TOL_ST 1e-5 "
-                                      f"(up to {args.max_stag} passes per step), scheme "
-                                      f"{args.scheme}, FP32 CG + FP64 refinement, GMG; whole "
-                                      "load paths"
+               "config": {"workload": workload_name(args, spec.l)
                                       + ("; spectral energy split" if split else ""),
+                          "form": "FP32 CG + FP64 refinement, geometric multigrid",
                           "batch": B, "executor": args.executor,
                           "autotune": (R.tuning[0] if R.tuning else None),
                           "load_steps_per_bench_step": bounds[1] - bounds[0],
