@@ -282,7 +282,11 @@ def kernel_roofline(spec, sims, peak_gbs, reps=30):
     ach = bytes_ / t / 1e9
     return {"kernel": "k_elas_strip<float,2> (matrix-free Q1 elasticity tangent, FP32)",
             "bound": "hbm", "achieved": ach, "peak": peak_gbs, "unit": "GB/s",
-            "frac": ach / peak_gbs, "traffic": profiled_traffic(), "algorithmic_bytes": bytes_,
+            "frac": ach / peak_gbs, "traffic": profiled_traffic(),
+            "traffic_source": "carried over from the committed ncu capture "
+                              "(profiles/k_elas_strip_f32_512_traffic.md); null when the "
+                              "operator source differs from the captured one",
+            "algorithmic_bytes": bytes_,
             "launch_us": t * 1e6, "l2": "flushed before each launch"}
 
 
