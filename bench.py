@@ -225,9 +225,12 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the roofline kernel from the committed ncu summary, or
-    None when the operator source changed since the counters were taken."""
+def profiled_traffic(grid=512):
+    """DRAM bytes per launch of the roofline kernel from the committed ncu summary (taken
+    on the 512 x 512 grid), or None for another grid or when the operator source changed
+    since the counters were taken."""
+    if grid != 512:
+        return None
     import hashlib
     prof = os.path.join(ROOT, "profiles", "k_elas_strip_f32_512_traffic.md")
     src = os.path.join(ROOT, "paper_2209_07969_gb300", "csrc", "pf_ops.cu")
@@ -282,7 +285,7 @@ def kernel_roofline(spec, sims, peak_gbs, reps=30):
     ach = bytes_ / t / 1e9
     return {"kernel": "k_elas_strip<float,2> (matrix-free Q1 elasticity tangent, FP32)",
             "bound": "hbm", "achieved": ach, "peak": peak_gbs, "unit": "GB/s",
-            "frac": ach / peak_gbs, "traffic": profiled_traffic(),
+            "frac": ach / peak_gbs, "traffic": profiled_traffic(spec.nx),
             "traffic_source": "carried over from the committed ncu capture "
                               "(profiles/k_elas_strip_f32_512_traffic.md); null when the "
                               "operator source differs from the captured one",
