@@ -237,3 +237,28 @@ def test_unlimited_augmented_tangent_stalls_on_the_tensile_benchmark():
     lim = stg.load_step(g, m, st.copy(), spec.increments[10], model.S3,
                         stg.Options(tol_st=1e-7, max_stag=30, kt_floor=True), spec.reaction_dir)
     assert lim.converged
+
+
+@pytest.mark.parametrize("kind,split", [("tensile", model.VD), ("shear", model.VD),
+                                        ("tensile", model.SPECTRAL)])
+def test_reaction_times_displacement_is_twice_the_stored_energy(kind, split):
+    # Virtual work at a converged load step: the degraded energy g(d) Psi+ + Psi- is
+    # positively homogeneous of degree 2 in the strain, so sigma : eps = 2 psi (Euler), and
+    # with the free DOFs in equilibrium the internal work sum_i F_i u_i reduces to the
+    # loaded DOFs: F ubar = 2 int [g(d) Psi+ + Psi-].  An independent global check of the
+    # reaction force, the stress law, the energy split and the quadrature.
+    sp = (S.tensile(24, l=0.08, steps=6, u_max=8e-3) if kind == "tensile"
+          else S.shear(24, l=0.08, steps=6, u_max=1.2e-2))
+    g = _grid(sp)
+    m = model.material_from_E_nu(sp.E, sp.nu, sp.Gc, sp.l, sp.eta, sp.plane, split)
+    st = stg.State(g)
+    w = q1.qp_weight(g)
+    for du in sp.increments:
+        r = stg.load_step(g, m, st, du, model.ST, stg.Options(tol_st=1e-9, tol_nr=1e-11),
+                          sp.reaction_dir)
+        assert r.converged
+        exx, eyy, exy = q1.strains_qp(g, st.u)
+        dq = q1.interp_qp(g, st.d)
+        psi = model.g(dq, m.eta) * model.psi_plus(exx, eyy, exy, m) + model.psi_minus(exx, eyy, exy, m)
+        energy = w * np.sum(psi * g.elem_active[:, None])
+        assert r.reaction * st.ubar == pytest.approx(2.0 * energy, rel=1e-7)
