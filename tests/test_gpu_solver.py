@@ -285,3 +285,28 @@ def test_paper_schedule_tensile(gpu, scheme, precision):
             assert abs(r["reaction"] - r_ref.reaction) <= 1e-4 * peak
             assert _d_rms(g, d, st_ref.d) <= 1e-3
         assert abs(r["stag_iters"] - r_ref.stag_iters) <= max(2, 0.2 * r_ref.stag_iters)
+
+
+@pytest.mark.parametrize("precision", [binding.FP64, binding.FP32_IR])
+@pytest.mark.parametrize("split", [binding.SPLIT_VD, binding.SPLIT_SPECTRAL])
+def test_reaction_times_displacement_is_twice_the_stored_energy(gpu, precision, split):
+    # At a converged load step the free DOFs are in equilibrium and the degraded energy is
+    # homogeneous of degree 2 in the strain, so F ubar = 2 int [g(d) Psi+ + Psi-]: the GPU
+    # reaction against the energy of the GPU's own fields (no checker path involved).
+    spec = S.tensile(48, l=0.08, steps=5, u_max=6e-3)
+    g, m = _checker(spec)
+    m = model.material_from_E_nu(spec.E, spec.nu, spec.Gc, spec.l, spec.eta, spec.plane,
+                                 model.SPECTRAL if split == binding.SPLIT_SPECTRAL else model.VD)
+    sim = binding.Simulation(spec, precision=precision, precond=binding.PRECOND_GMG,
+                             split=split)
+    sim.set_options(tol_lin=1e-12, tol_nr=1e-10)
+    w = q1.qp_weight(g)
+    for du in spec.increments:
+        r = sim.load_step(du, 1, 1e-8)
+        assert r["converged"] == 1
+        u, d, _ = sim.fields()
+        exx, eyy, exy = q1.strains_qp(g, u)
+        dq = q1.interp_qp(g, d)
+        psi = model.g(dq, m.eta) * model.psi_plus(exx, eyy, exy, m) + model.psi_minus(exx, eyy, exy, m)
+        assert r["reaction"] * r["ubar"] == pytest.approx(2.0 * w * psi.sum(), rel=1e-6)
+    sim.close()
