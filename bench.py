@@ -245,10 +245,12 @@ def profiled_traffic(grid=512):
 
 
 def kernel_roofline(spec, sims, peak_gbs, reps=30):
-    """Time the FP32 matrix-free elasticity tangent apply (the dominant operator) on the
-    workload grid with CUDA events on the launching stream, flushing L2 before each
-    launch.  Algorithmic bytes per node: x (8) + y (8) + d (4) + DOF mask (1) + tension
-    byte (1 per element, ~1 per node) = 22."""
+    """Time the FP32 matrix-free elasticity tangent apply (the operator inside every fused
+    fine-level stage of the multigrid PCG) on the workload grid with CUDA events on the
+    launching stream, flushing L2 before each launch.  Algorithmic bytes per node: x (8) +
+    y (8) + d (4) + DOF mask (1) + tension byte (1 per element, ~1 per node) = 22.  By
+    launch-list share the single-CTA coarse cycle is the largest single kernel; every
+    kernel of the iteration is latency-bound at this size."""
     import numpy as np
     import torch
     from paper_2209_07969_gb300 import binding
@@ -290,7 +292,11 @@ def kernel_roofline(spec, sims, peak_gbs, reps=30):
                               "(profiles/k_elas_strip_f32_512_traffic.md); null when the "
                               "operator source differs from the captured one",
             "algorithmic_bytes": bytes_,
-            "launch_us": t * 1e6, "l2": "flushed before each launch"}
+            "launch_us": t * 1e6, "l2": "flushed before each launch",
+            "share_note": "launch-list shares of the whole-path bench command "
+                          "(profiles/bench_tensile128_launch_list.md): single-CTA coarse "
+                          "cycle 27%, fused fine-level stages 35%, grid-level stencil "
+                          "kernels 30%; all latency-bound"}
 
 
 def chunks(K):
