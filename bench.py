@@ -4,9 +4,9 @@
 Workload (tensile notched square, 512 x 512 Q1 elements, l = 0.0075 mm, 100 load steps to
 6e-3 mm, staggered tolerance 1e-5 with up to 20,000 passes per load step; S1 fixed-stress
 scheme, FP32 CG with FP64 refinement, geometric multigrid): a batch of B simulations of
-that specimen, advanced together through the batched executor (pf_batch_*: their FP32
-multigrid solves share kernel launches) or, with --executor streams, each on its own
-stream and host thread.
+that specimen (default 2), each on its own stream and host thread, or with --executor
+batched through the batched executor (pf_batch_*: their FP32 multigrid solves share
+kernel launches).
 
 The timed region is one WHOLE load path of every simulation: the K bench steps split the
 100 load steps into K consecutive chunks (one bench step = 100/K load steps of every
@@ -51,8 +51,8 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--batch", type=int, default=1)
-    p.add_argument("--executor", default="batched", choices=["batched", "streams"],
+    p.add_argument("--batch", type=int, default=2)
+    p.add_argument("--executor", default="streams", choices=["batched", "streams"],
                    help="batched: pf_batch (shared launches); streams: one stream per simulation")
     p.add_argument("--max-stag", type=int, default=20000)
     p.add_argument("--no-tune", action="store_true", help="skip pf_autotune")
