@@ -24,12 +24,13 @@ pytestmark = pytest.mark.gpu
 TOL_ST = 1e-5
 
 
-def _check_state(spec, steps, scheme=binding.S1, split=binding.SPLIT_VD):
+def _check_state(spec, steps, scheme=binding.S1, split=binding.SPLIT_VD, max_stag=1000):
     g = q1.Grid(spec.nx, spec.ny, spec.Lx, spec.Ly, spec.node_flags, spec.elem_active)
     m = model.material_from_E_nu(spec.E, spec.nu, spec.Gc, spec.l, spec.eta, spec.plane,
                                  split)
     sim = binding.Simulation(spec, precision=binding.FP32_IR, precond=binding.PRECOND_GMG,
                              split=split)
+    sim.set_options(max_stag=max_stag)
     ubar = 0.0
     H_prev = np.zeros((g.ne, 4))
     for k in range(steps):
@@ -88,3 +89,10 @@ def test_tensile_512_spectral_split():
                      split=binding.SPLIT_SPECTRAL)
     assert r["reaction"] > 0
 
+
+def test_tensile_256_inside_the_running_crack():
+    # 256 x 256 at the l/h of the 512 x 512 workload, through the first crack jump (step 44)
+    # into the running crack (steps 84-85: thousands of staggered passes); the checker
+    # verifies the state the GPU path returns at step 85
+    r = _check_state(S.tensile(256, l=0.015, steps=100, u_max=6e-3), 85, max_stag=20000)
+    assert r["stag_iters"] > 100
