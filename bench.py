@@ -61,7 +61,9 @@ def parse():
                    help="skip the FP64-form comparison on the 128 x 128 path")
     p.add_argument("--grid", type=int, default=512)
     p.add_argument("--scheme", default="S1")
-    p.add_argument("--full-path", action="store_true")
+    p.add_argument("--full-path", action="store_true",
+                   help="whole paths of the workload in FP32-IR and in FP64, one simulation "
+                        "per --scheme (comma list): the full-size FP64-form comparison")
     p.add_argument("--kernel", default=None, choices=["elas"],
                    help="time one operator kernel on the --grid tensile mesh and exit")
     p.add_argument("--dtype", default="f32", choices=["f32", "f64"])
