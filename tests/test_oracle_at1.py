@@ -153,3 +153,36 @@ def test_at1_free_sided_bar_both_splits(split, scheme):
         assert d_prev > 0.4                    # four damaging steps
     else:
         assert -1e-3 < d_prev < 0.0            # penalty branch just below the limit
+
+
+def test_at1_stag_residual_on_one_element_by_hand():
+    # AT1 staggered residual (Sec. 2 evolution equation, penalty irreversibility) on the
+    # unit square, one element, mu = 1, lambda = 2, G_c = l = 1 (plane strain) and
+    # u_x = x / 2: Psi+ = 1/2 at every point.  Then a = G_c/(c_w l) = 3/8,
+    # kappa = 2 G_c l / c_w = 3/4, gamma = 27 G_c / (64 l tol_ir^2) = 4218.75 (tol_ir 0.01).
+    # R_d = (M + kappa G) d + int (-2 Psi + a + gamma <d - d_{n-1}>_-) N with the Q1 mass
+    # M = m1 (x) m1 and gradient matrix G = k1 (x) m1 + m1 (x) k1 of the unit square, so
+    # M + 3/4 G has rows [11/18, -5/72, -5/72, -2/9] (and permutations); the Jacobian adds
+    # gamma M where the penalty is active.
+    g = q1.Grid(1, 1, 1.0, 1.0)
+    m = model.Material(1.0, 2.0 + 2.0 / 3.0, 1.0, 1.0, 1e-9, 1.0 / 3.0)
+    u = np.zeros(8)
+    u[0::2] = 0.5 * np.array([0.0, 1.0, 0.0, 1.0])
+    d = np.array([0.0, 0.2, 0.4, 0.6])
+    opts = stg.Options(model=model.AT1, tol_ir=0.01)
+    K = np.array([[11 / 18, -5 / 72, -5 / 72, -2 / 9],
+                  [-5 / 72, 11 / 18, -2 / 9, -5 / 72],
+                  [-5 / 72, -2 / 9, 11 / 18, -5 / 72],
+                  [-2 / 9, -5 / 72, -5 / 72, 11 / 18]])
+    # no penalty (d = d_{n-1}): source -1 + 3/8 = -5/8, integral -5/32 per node
+    R = K @ d - 5.0 / 32.0
+    assert stg.at1_stag_residual(g, m, u, d, d.copy(), opts) == pytest.approx(
+        np.max(np.abs(R / (11 / 18))), rel=1e-12)
+    assert np.max(np.abs(R / (11 / 18))) == pytest.approx(0.33125 * 18 / 11, rel=1e-12)
+    # penalty everywhere (d_{n-1} = d + 0.1): source -5/8 - 0.1 gamma, Jacobian diagonal
+    # (1 + gamma) 4/36 + 3/4 * 4/6
+    gamma = 27.0 / (64.0 * 1e-4)
+    R = K @ d + (-5.0 / 8.0 - 0.1 * gamma) / 4.0
+    Jd = (1.0 + gamma) * 4.0 / 36.0 + 0.5
+    assert stg.at1_stag_residual(g, m, u, d, d + 0.1, opts) == pytest.approx(
+        np.max(np.abs(R / Jd)), rel=1e-12)
