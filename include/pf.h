@@ -143,6 +143,9 @@ typedef struct {
 typedef struct pf_ctx pf_ctx;
 
 void pf_default_options(pf_options *opt);
+/* Environment: PF_PDL=0 launches the kernels of the Krylov iteration without programmatic
+ * dependent launch (by default each is dispatched while its predecessor drains and waits
+ * for it on the device; results are the same either way). */
 
 /* Create a simulation (Sec. 2 model with E, nu, G_c, l and residual stiffness k_res,
  * the eta of g(d) = (1-d)^2 + eta).  Allocates all device memory for the mesh; the
